@@ -1,0 +1,14 @@
+"""Seeded synthetic SCCS inputs shared by the tests, the benchmark and the oracle checks.
+
+This package only draws data (patients, eras, offsets, drug indicators, event counts).
+It holds none of the fitting method's arithmetic, and it imports neither the CUDA
+package nor the oracle.
+"""
+from .sccs_synth import (  # noqa: F401
+    SCCSData,
+    make_dataset,
+    tiny_fit_config,
+    mid_fit_config,
+    paper_scale_config,
+    CONFIGS,
+)

@@ -1,0 +1,243 @@
+"""Seeded synthetic self-controlled case series (SCCS) data.
+
+The paper's timings use licensed claims databases (Section 3) that are not available, so
+every workload here is synthetic, drawn from the model of Section 2.1:
+
+* subjects i = 1..N, each with K_i eras (constant-exposure intervals); rows of one subject
+  are contiguous and subjects appear in increasing id order;
+* l_ik: era length in days, integer, uniform on {1..365};
+* x_ikj in {0,1}: drug indicators, stored column-wise (CSC, row indices ascending);
+* y_ik ~ Poisson(l_ik exp(x_ik' beta_true) / 365), conditioned on n_i = sum_k y_ik >= 1
+  (the design keeps cases only, Eq. 1).  The conditioning is sampled exactly: n_i from a
+  zero-truncated Poisson, then y_i | n_i ~ Multinomial(n_i, rates / total rate).
+
+Column supports are drawn as Bernoulli(p_j) row processes (geometric skips), so a column's
+rows are distinct and sorted.  Column sizes are either a fixed density or a truncated
+continuous power law ("Zipf(s) from a to b") by inverse CDF, with column 0 forced to b and
+column 1 to a so both extremes exist.
+
+Nothing here evaluates the likelihood, its derivatives or any CCD step.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class SCCSData:
+    """One synthetic SCCS dataset in the layout the C ABI takes."""
+
+    K: int                      # rows (eras), including subjects later dropped for n_i = 0
+    N: int                      # subjects
+    patient_id: np.ndarray      # int64[K], non-decreasing
+    y: np.ndarray               # int32[K], event counts
+    L: np.ndarray               # float64[K], era lengths (days, integer-valued)
+    J: int                      # drug columns
+    col_ptr: np.ndarray         # int64[J+1]
+    row_idx: np.ndarray         # int32[nnz], ascending within each column
+    beta_true: np.ndarray       # float64[J], the generating coefficients
+    recipe: dict                # how it was drawn (for reports)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_ptr[-1])
+
+    def column(self, j: int) -> np.ndarray:
+        return self.row_idx[self.col_ptr[j]:self.col_ptr[j + 1]]
+
+
+# --------------------------------------------------------------------------- samplers
+
+def _bernoulli_rows(rng: np.random.Generator, K: int, p: float) -> np.ndarray:
+    """Sorted distinct rows of a Bernoulli(p) process on 0..K-1, via geometric gaps."""
+    if K <= 0 or p <= 0.0:
+        return np.empty(0, dtype=np.int64)
+    if p >= 1.0:
+        return np.arange(K, dtype=np.int64)
+    expected = K * p
+    m = int(expected + 6.0 * math.sqrt(expected) + 32)
+    gaps = rng.geometric(p, size=m)
+    pos = np.cumsum(gaps, dtype=np.int64) - 1
+    while pos[-1] < K - 1:
+        more = rng.geometric(p, size=max(m // 4, 64))
+        pos = np.concatenate([pos, pos[-1] + np.cumsum(more, dtype=np.int64)])
+    return pos[pos < K]
+
+
+def _power_law_sizes(rng: np.random.Generator, J: int, s: float, a: float, b: float) -> np.ndarray:
+    """nnz_j i.i.d. from the density proportional to n^-s on [a, b], floored; col 0 = b, col 1 = a."""
+    u = rng.random(J)
+    if abs(s - 1.0) < 1e-12:
+        x = a * np.exp(u * math.log(b / a))
+    else:
+        e = 1.0 - s
+        x = (a ** e + u * (b ** e - a ** e)) ** (1.0 / e)
+    sizes = np.floor(x).astype(np.int64)
+    if J > 0:
+        sizes[0] = int(b)
+    if J > 1:
+        sizes[1] = int(a)
+    return sizes
+
+
+def _zero_truncated_poisson(rng: np.random.Generator, mu: np.ndarray) -> np.ndarray:
+    """Exact draws of Poisson(mu) conditioned on >= 1."""
+    n = np.zeros(mu.shape[0], dtype=np.int64)
+    big = mu >= 10.0
+    ib = np.nonzero(big)[0]
+    if ib.size:
+        d = rng.poisson(mu[ib])
+        zero = d == 0
+        while zero.any():                      # P(0) < 5e-5 here: rejection is exact and cheap
+            d[zero] = rng.poisson(mu[ib][zero])
+            zero = d == 0
+        n[ib] = d
+    isml = np.nonzero(~big)[0]
+    if isml.size:
+        m = mu[isml]
+        u = rng.random(m.shape[0])
+        p0 = np.exp(-m)
+        target = p0 + u * (1.0 - p0)           # inverse CDF restricted to k >= 1
+        k = np.ones(m.shape[0], dtype=np.int64)
+        pk = m * p0
+        cdf = p0 + pk
+        done = cdf >= target
+        it = 0
+        while (~done).any() and it < 400:
+            nd = ~done
+            k[nd] += 1
+            pk[nd] *= m[nd] / k[nd]
+            cdf[nd] += pk[nd]
+            done |= cdf >= target
+            it += 1
+        n[isml] = k
+    return n
+
+
+def _events_to_rows(rng, mu_k, pat_ptr, n_i):
+    """Place n_i events of subject i on its eras with probability proportional to mu_k."""
+    K = mu_k.shape[0]
+    cum = np.cumsum(mu_k)
+    start = pat_ptr[:-1]
+    end = pat_ptr[1:]
+    base = np.where(start > 0, cum[np.maximum(start - 1, 0)], 0.0)
+    tot = cum[end - 1] - base
+    ev_pat = np.repeat(np.arange(n_i.shape[0], dtype=np.int64), n_i)
+    u = base[ev_pat] + rng.random(ev_pat.shape[0]) * tot[ev_pat]
+    r = np.searchsorted(cum, u, side="right")
+    r = np.clip(r, start[ev_pat], end[ev_pat] - 1)
+    return np.bincount(r, minlength=K).astype(np.int32)
+
+
+# --------------------------------------------------------------------------- datasets
+
+def make_dataset(*, n_patients: int, eras: tuple, J: int, columns: tuple,
+                 n_true: int, beta_sd: float, seed: int, name: str = "custom") -> SCCSData:
+    """Draw one dataset.
+
+    eras    = ("uniform", lo, hi) | ("geometric", mean) | ("fixed", k)
+    columns = ("density", p) | ("density_range", lo, hi) | ("zipf", s, a, b) | ("sizes", array)
+    """
+    rng = np.random.default_rng(seed)
+    N = int(n_patients)
+    kind = eras[0]
+    if kind == "uniform":
+        counts = rng.integers(int(eras[1]), int(eras[2]) + 1, size=N)
+    elif kind == "geometric":
+        counts = rng.geometric(1.0 / float(eras[1]), size=N)
+    elif kind == "fixed":
+        counts = np.full(N, int(eras[1]))
+    else:
+        raise ValueError(f"unknown era recipe {eras}")
+    counts = counts.astype(np.int64)
+    K = int(counts.sum())
+    pat_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(counts, out=pat_ptr[1:])
+    patient_id = np.repeat(np.arange(N, dtype=np.int64), counts)
+    L = rng.integers(1, 366, size=K).astype(np.float64)
+
+    ckind = columns[0]
+    if ckind == "density":
+        probs = np.full(J, float(columns[1]))
+    elif ckind == "density_range":
+        probs = rng.uniform(float(columns[1]), float(columns[2]), size=J)
+    elif ckind == "zipf":
+        sizes = _power_law_sizes(rng, J, float(columns[1]), float(columns[2]), float(columns[3]))
+        probs = np.minimum(1.0, sizes / max(K, 1))
+    elif ckind == "sizes":
+        sizes = np.asarray(columns[1], dtype=np.int64)
+        assert sizes.shape[0] == J
+        probs = np.minimum(1.0, sizes / max(K, 1))
+    else:
+        raise ValueError(f"unknown column recipe {columns}")
+    cols = [_bernoulli_rows(rng, K, float(p)) for p in probs]
+    col_ptr = np.zeros(J + 1, dtype=np.int64)
+    np.cumsum([c.shape[0] for c in cols], out=col_ptr[1:])
+    row_idx = (np.concatenate(cols) if cols else np.empty(0, np.int64)).astype(np.int32)
+
+    beta_true = np.zeros(J)
+    if n_true > 0 and J > 0:
+        which = rng.choice(J, size=min(n_true, J), replace=False)
+        beta_true[which] = rng.normal(0.0, beta_sd, size=which.shape[0])
+    xb = np.zeros(K)
+    for j in np.nonzero(beta_true)[0]:
+        xb[cols[j]] += beta_true[j]
+    mu_k = L * np.exp(xb) / 365.0
+    mu_i = np.add.reduceat(mu_k, pat_ptr[:-1]) if N > 0 else np.zeros(0)
+    n_i = _zero_truncated_poisson(rng, mu_i)
+    y = _events_to_rows(rng, mu_k, pat_ptr, n_i)
+    recipe = dict(name=name, seed=seed, n_patients=N, eras=list(eras), J=J,
+                  columns=[c if not isinstance(c, np.ndarray) else "explicit" for c in columns],
+                  n_true=n_true, beta_sd=beta_sd, K=K, nnz=int(col_ptr[-1]))
+    return SCCSData(K=K, N=N, patient_id=patient_id, y=y, L=L, J=J, col_ptr=col_ptr,
+                    row_idx=row_idx, beta_true=beta_true, recipe=recipe)
+
+
+def tiny_fit_config(seed: int = 1208) -> tuple[SCCSData, dict]:
+    """2,000 subjects, 1-10 eras each, 50 drugs at 2% density, 5 true effects ~ N(0, 0.3^2).
+
+    Fit: Normal prior with variance 1, FP64, stop when |delta log-posterior| < 1e-10.
+    """
+    d = make_dataset(n_patients=2000, eras=("uniform", 1, 10), J=50, columns=("density", 0.02),
+                     n_true=5, beta_sd=0.3, seed=seed, name="tiny-2k-subjects-50-drugs")
+    fit = dict(prior="normal", variance=1.0, tol_mode="abs_logpost", tol=1e-10, max_cycles=1000)
+    return d, fit
+
+
+def mid_fit_config(seed: int = 1209, scale: float = 1.0) -> tuple[SCCSData, dict]:
+    """1M subjects (~10M eras, geometric mean 10), 1,000 drugs with Zipf(1.2) sizes 10..2M.
+
+    20 true effects ~ N(0, 0.5^2); Normal prior variance 0.1; FP64.  `scale` shrinks the
+    subject count and the largest column together (for parity tests at reduced size).
+    """
+    n = max(int(round(1_000_000 * scale)), 100)
+    b = max(2_000_000 * scale, 20.0)
+    d = make_dataset(n_patients=n, eras=("geometric", 10), J=1000, columns=("zipf", 1.2, 10, b),
+                     n_true=20, beta_sd=0.5, seed=seed,
+                     name=f"mid-{n}-subjects-1000-drugs-zipf1.2")
+    fit = dict(prior="normal", variance=0.1, tol_mode="rel_logpost", tol=1e-12, max_cycles=1000)
+    return d, fit
+
+
+def paper_scale_config(seed: int = 1210, scale: float = 1.0) -> tuple[SCCSData, dict]:
+    """4M subjects (~40M eras), 5,000 drugs with Zipf(1.1) sizes 10..5M, 50 true effects.
+
+    Laplace prior variance 0.05.
+    """
+    n = max(int(round(4_000_000 * scale)), 100)
+    b = max(5_000_000 * scale, 20.0)
+    d = make_dataset(n_patients=n, eras=("geometric", 10), J=5000, columns=("zipf", 1.1, 10, b),
+                     n_true=50, beta_sd=0.5, seed=seed,
+                     name=f"paper-scale-{n}-subjects-5000-drugs-zipf1.1")
+    fit = dict(prior="laplace", variance=0.05, tol_mode="rel_logpost", tol=1e-12, max_cycles=1000)
+    return d, fit
+
+
+CONFIGS = {
+    "tiny": tiny_fit_config,
+    "mid": mid_fit_config,
+    "paper": paper_scale_config,
+}

@@ -1,0 +1,68 @@
+"""The oracle's pins are sensitive: each plausible mistake planted in a copy of the oracle
+source (a dropped term, a flipped sign, a wrong index, a wrong prior scale) makes at least
+one pin fail.  Mistakes are planted only in a temporary CPU build of the oracle."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "sccs_oracle.c")
+
+# (name, exact text in the oracle, replacement)
+MUTATIONS = [
+    ("hessian_sign_1_plus_w", "nWW += (double)p->n[i] * Wi * (1.0 - Wi);",
+     "nWW += (double)p->n[i] * Wi * (1.0 + Wi);"),
+    ("gradient_sign", "*g = (double)p->ytx[j] - nW;", "*g = (double)p->ytx[j] + nW;"),
+    ("loglik_dropped_log_term", "total += lin - (double)p->n[i] * log(den);", "total += lin - log(den);"),
+    ("laplace_scale", "double lambda = sqrt(2.0 / var);\n        if (q > 0.0)",
+     "double lambda = sqrt(1.0 / var);\n        if (q > 0.0)"),
+    ("normal_prior_curvature", "dv = (g - bj / var) / (q + 1.0 / var);", "dv = (g - bj / var) / (q + 2.0 / var);"),
+    ("denominator_update_dropped_old", "D[p->row_pat[k]] += En - E[k];", "D[p->row_pat[k]] += En;"),
+    ("off_by_one_subject", "if (cur >= 0) {\n                        double Wi = num / D[cur];",
+     "if (cur >= 0) {\n                        double Wi = num / D[cur > 0 ? cur - 1 : 0];"),
+    ("offset_ignored_in_update", "double En = p->L[k] * exp(xb[k]);", "double En = exp(xb[k]);"),
+]
+
+PIN_CASES = [
+    (pins.test_loglik_equals_conditional_multinomial, dict(seed=0)),
+    (pins.test_grad_hess_finite_differences, dict(seed=0)),
+    (pins.test_grad_hess_against_dense_softmax_form, {}),
+    (pins.test_golden_one_covariate_closed_forms, {}),
+    (pins.test_one_covariate_general_minimiser, dict(seed=0)),
+    (pins.test_ccd_matches_multivariate_newton, dict(seed=1, prior="normal")),
+    (pins.test_laplace_kkt_certificate, dict(seed=1, var=0.2)),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(oracle.compile_command(str(mutated), str(so)), check=True)
+    lib = oracle.load_variant(str(so))
+    failed = []
+    saved = pins.ORACLE_LIB
+    pins.ORACLE_LIB = lib
+    try:
+        for fn, kw in PIN_CASES:
+            try:
+                fn(**kw)
+            except (AssertionError, oracle.OracleError):
+                failed.append(fn.__name__)
+    finally:
+        pins.ORACLE_LIB = saved
+    assert failed, f"planted mistake {name} passed every pin"
+
+
+def test_unmutated_oracle_passes_the_same_pins():
+    for fn, kw in PIN_CASES:
+        fn(**kw)
