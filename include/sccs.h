@@ -1,0 +1,209 @@
+/*
+ * sccs.h -- C ABI of the GB300 (sm_103a) library for the Bayesian self-controlled case
+ * series (BSCCS) MAP fit by cyclic coordinate descent, after Suchard, Simpson, Zorych,
+ * Ryan and Madigan, "Massive parallelization of serial inference algorithms for a complex
+ * generalized linear model" (arXiv 1208.0945).
+ *
+ * Conventions for every entry point:
+ *   - Return value: int status.  0 = SCCS_OK; positive = a non-error status; negative = an
+ *     error.  On an error nothing the call was to produce is written, and
+ *     sccs_last_error() describes the cause.
+ *   - Array arguments are HOST pointers unless a comment says otherwise.  The caller keeps
+ *     ownership of every array it passes; the library copies what it needs before returning.
+ *   - A handle owns its device memory and CUDA stream work.  Calls on one handle must not
+ *     overlap (the library does not lock); distinct handles are independent.
+ *   - Indices are zero-based.  Row k is an era; subject i a patient; column j a drug.
+ *
+ * Paper notation (Section 2.1 and 2.3): y_k events, l_k era length (offset), x_kj in {0,1},
+ * n_i = sum of y over subject i's eras, X the K x J design (compressed column storage),
+ * M the N x K subject loading matrix (each subject's eras contiguous, Eq. 5).
+ */
+#ifndef SCCS_H
+#define SCCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCCS_ABI_VERSION 1
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define SCCS_OK 0
+#define SCCS_NOT_CONVERGED 1     /* sccs_fit stopped at max_cycles */
+#define SCCS_PENDING 2           /* serving: request not finished yet */
+#define SCCS_E_INVAL (-1)        /* bad argument: null pointer, size, range, non-positive offset */
+#define SCCS_E_UNSORTED (-2)     /* patient ids decrease somewhere */
+#define SCCS_E_NONBINARY (-3)    /* an explicit X value is not exactly 1 */
+#define SCCS_E_NOMEM (-4)        /* host or device allocation failed */
+#define SCCS_E_CUDA (-5)         /* a CUDA runtime call failed */
+#define SCCS_E_TIMEOUT (-6)      /* a device-side wait exceeded its bound; the handle is reset */
+#define SCCS_E_NUMERIC (-7)      /* non-finite gradient, Hessian, step or log-posterior */
+#define SCCS_E_BUSY (-8)         /* serving: queue full */
+#define SCCS_E_DUPLICATE (-9)    /* a row appears twice in one column */
+#define SCCS_E_UNSUPPORTED (-10) /* option not available in this build */
+
+/* ---- priors (Eq. 3: Normal(0, s2) or Laplace(0, s2), s2 the variance) ----------------- */
+#define SCCS_PRIOR_NONE 0
+#define SCCS_PRIOR_NORMAL 1
+#define SCCS_PRIOR_LAPLACE 2     /* lambda = sqrt(2 / s2) */
+
+/* ---- convergence tests, evaluated once per full cycle (Section 2.2) ------------------- */
+#define SCCS_TOL_ABS_LOGPOST 0   /* |P_t - P_{t-1}| < tol */
+#define SCCS_TOL_REL_LOGPOST 1   /* |P_t - P_{t-1}| / max(1, |P_t|) < tol */
+#define SCCS_TOL_GENKIN_XBETA 2  /* sum|Xb_t - Xb_{t-1}| / (1 + sum|Xb_t|) < tol (not on GPU yet) */
+
+/* ---- arithmetic ----------------------------------------------------------------------- */
+#define SCCS_PREC_FP64 0         /* every step in FP64 */
+
+typedef struct sccs_handle sccs_handle;
+
+/* Optional device allocator (for example a framework's caching allocator).  alloc returns a
+ * device pointer aligned to at least 256 bytes or NULL; free receives the same size. */
+typedef void *(*sccs_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*sccs_free_fn)(void *ptr, size_t bytes, void *ctx);
+
+typedef struct sccs_create_opts {
+    int32_t struct_size;       /* sizeof(sccs_create_opts) */
+    int32_t device;            /* CUDA device ordinal */
+    void *stream;              /* cudaStream_t for all work; NULL = a stream the handle owns */
+    int32_t num_shards;        /* subject shards = resident CTAs of the fit kernel; 0 = one per SM */
+    int32_t threads_per_block; /* 0 = 512; must be a multiple of 32 in [64, 512] */
+    sccs_alloc_fn alloc;       /* NULL = cudaMalloc */
+    sccs_free_fn free;
+    void *alloc_ctx;
+} sccs_create_opts;
+
+typedef struct sccs_data_info {
+    int64_t rows_in, rows_kept;         /* K before / after removing subjects with n_i = 0 */
+    int64_t subjects_in, subjects_kept; /* N before / after */
+    int64_t nnz_kept;                   /* nonzeros of X on kept rows */
+    int64_t segments;                   /* (subject, column) pairs with at least one nonzero */
+    int64_t max_column_nnz;
+    int64_t device_bytes;               /* device memory held by the handle */
+    int64_t upload_bytes;               /* bytes copied host -> device by sccs_create */
+    int32_t columns;                    /* J */
+    int32_t num_shards;
+    int32_t threads_per_block;
+    int32_t reserved;
+} sccs_data_info;
+
+typedef struct sccs_fit_opts {
+    int32_t struct_size;       /* sizeof(sccs_fit_opts) */
+    int32_t warm_start;        /* 1: start from the handle's current beta (the previous fit) */
+    const double *beta0;       /* host, J values; overrides warm_start; NULL and warm_start = 0
+                                  start from beta = 0 as Algorithm 1 does */
+    int32_t tol_mode;          /* SCCS_TOL_* */
+    int32_t max_cycles;        /* >= 0; 0 only evaluates P at the start point */
+    double tol;                /* < 0 runs exactly max_cycles cycles */
+    int32_t precision;         /* SCCS_PREC_FP64 */
+    int32_t reserved;
+    double *logpost_history;   /* optional host buffer of max_cycles + 1 values: P_0 .. P_cycles */
+} sccs_fit_opts;
+
+typedef struct sccs_fit_info {
+    int32_t status;            /* SCCS_OK or SCCS_NOT_CONVERGED */
+    int32_t cycles;            /* full cycles run */
+    int64_t steps;             /* coordinate steps = cycles * J */
+    int64_t nonzero_steps;     /* steps with db_j != 0 (Algorithm 1's test) */
+    double logpost;            /* P(beta) at the end, constants dropped */
+    double conv_value;         /* last convergence statistic */
+    double kernel_ms;          /* device time of the fit kernel (CUDA events) */
+    double total_ms;           /* host wall time of the call */
+    int32_t warnings;          /* bit 0: an unbounded coordinate took the trust-region bound */
+    int32_t reserved;
+} sccs_fit_info;
+
+/* Library identification: ABI version and "sm_103a" build string. */
+int sccs_version(int32_t *abi_version, const char **build);
+
+/* Thread-local description of the last error raised by a call on this thread ("" if none).
+ * The handle argument may be NULL. */
+const char *sccs_last_error(const sccs_handle *h);
+
+/*
+ * sccs_create -- validate, canonicalise and upload one SCCS dataset (Section 2.3,
+ * "Representation in Memory": X in compressed column storage, ones implicit).
+ *   K            rows (eras); >= 0
+ *   patient_id   [K] non-decreasing subject ids; a subject's eras are contiguous (Eq. 5)
+ *   y            [K] event counts >= 0
+ *   offset_L     [K] era lengths l_k > 0, finite
+ *   J            columns (drugs); >= 0
+ *   col_ptr      [J+1] column starts into row_idx; col_ptr[0] = 0, non-decreasing
+ *   row_idx      [col_ptr[J]] row of each nonzero, in [0, K); any order within a column
+ *   x_values     NULL for an indicator matrix, else [col_ptr[J]] values that must all be 1
+ *                (the Hessian form of Eq. 9 needs x_kj^2 = x_kj)
+ *   opts         NULL for defaults
+ * Subjects with n_i = 0 contribute nothing (Section 2.1) and are removed here.  Errors:
+ * SCCS_E_INVAL, SCCS_E_UNSORTED, SCCS_E_NONBINARY, SCCS_E_DUPLICATE, SCCS_E_NOMEM,
+ * SCCS_E_CUDA.  On success *out owns device memory until sccs_destroy.  The prior starts as
+ * SCCS_PRIOR_NONE and beta as 0.
+ */
+int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const int32_t *y,
+                const double *offset_L, int32_t J, const int64_t *col_ptr,
+                const int32_t *row_idx, const double *x_values, const sccs_create_opts *opts);
+
+/* Release the handle and its device memory.  NULL is accepted. */
+int sccs_destroy(sccs_handle *h);
+
+/* Dimensions and memory of a created handle. */
+int sccs_get_info(const sccs_handle *h, sccs_data_info *info);
+
+/*
+ * sccs_set_prior -- choose the prior of Eq. 3 for later fits: SCCS_PRIOR_NONE, or
+ * SCCS_PRIOR_NORMAL / SCCS_PRIOR_LAPLACE with variance s2 > 0 (Laplace scale sqrt(s2/2)).
+ * Errors: SCCS_E_INVAL.
+ */
+int sccs_set_prior(sccs_handle *h, int32_t prior_type, double variance);
+
+/*
+ * sccs_fit -- MAP estimate by cyclic coordinate descent (Algorithm 1): for j = 1..J take
+ * the prior-regularised Newton step of Eq. 4 under a Genkin trust region, built from the
+ * gradient and Hessian of Eqs. 7-9, and update L x exp(Xb) and M[L x exp(Xb)] on the rows of
+ * X_j (Section 2.3 steps 1-3); refresh M[L x exp(Xb)] and test convergence after each cycle.
+ * The whole fit runs in one persistent kernel on the handle's stream; the call returns when
+ * it is done.
+ *   opts      NULL = beta0 0, SCCS_TOL_REL_LOGPOST, tol 1e-12, max_cycles 1000, FP64
+ *   beta_out  host [J] or NULL: the final beta
+ *   info      host or NULL
+ * Returns SCCS_OK, SCCS_NOT_CONVERGED, or an error (SCCS_E_INVAL, SCCS_E_NUMERIC,
+ * SCCS_E_TIMEOUT, SCCS_E_CUDA, SCCS_E_UNSUPPORTED).  After an error the handle's beta is 0.
+ */
+int sccs_fit(sccs_handle *h, const sccs_fit_opts *opts, double *beta_out, sccs_fit_info *info);
+
+/*
+ * sccs_grad_hess -- the log-likelihood derivatives along coordinate j (Eqs. 7-9, no prior):
+ *   g_j = Y'X_j - N'W,  h_j = -N'[W x (1 - W)],  W = M[L x exp(Xb) x X_j] / M[L x exp(Xb)].
+ *   beta  host [J]: evaluate there (the handle's state is moved to beta); NULL: at the
+ *         handle's current state.
+ * Errors: SCCS_E_INVAL (j out of range), SCCS_E_TIMEOUT, SCCS_E_CUDA.
+ */
+int sccs_grad_hess(sccs_handle *h, int32_t j, const double *beta, double *g, double *hess);
+
+/*
+ * sccs_logpost -- P(b) = L(b) + log p(b) with constants dropped (Eq. 2 and Eq. 3) under the
+ * handle's prior.  beta as for sccs_grad_hess.  loglik may be NULL; it receives L(b).
+ */
+int sccs_logpost(sccs_handle *h, const double *beta, double *logpost, double *loglik);
+
+/* Copy the handle's current beta (host [J]). */
+int sccs_get_beta(const sccs_handle *h, double *beta_out);
+
+/*
+ * sccs_check_wait_timeout -- self-test of the bounded device-side waits (failure detection).
+ * Launches the gradient kernel on one CTA fewer than the all-reduce counts, so the last
+ * partial is never written and every launched CTA's wait must run out after timeout_ms
+ * (0 < timeout_ms <= 10000).  Nothing faults or hangs: the CTAs raise the abort flag and
+ * return.  Returns SCCS_E_TIMEOUT when the waits ran out as designed (the expected result),
+ * SCCS_E_INVAL otherwise.  The handle is reset to beta = 0 and stays usable.  Needs at least
+ * two shards and one column.
+ */
+int sccs_check_wait_timeout(sccs_handle *h, double timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCCS_H */

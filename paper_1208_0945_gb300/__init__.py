@@ -1,0 +1,21 @@
+"""GB300 (sm_103a) BSCCS cyclic-coordinate-descent MAP fit (arXiv 1208.0945, Section 2).
+
+The compute lives in libsccs.so (hand-written CUDA behind the C ABI of include/sccs.h);
+`sccs` is its ctypes binding.  Importing this package fails if the library is not built.
+"""
+from .sccs import (  # noqa: F401
+    EXPORTED,
+    SCCSError,
+    SCCSModel,
+    sccs_check_wait_timeout,
+    sccs_create,
+    sccs_destroy,
+    sccs_fit,
+    sccs_get_beta,
+    sccs_get_info,
+    sccs_grad_hess,
+    sccs_last_error,
+    sccs_logpost,
+    sccs_set_prior,
+    sccs_version,
+)

@@ -1,0 +1,95 @@
+// sccs_internal.h -- device layout shared by the host set-up code and the CUDA kernels.
+//
+// Layout ("subject shards"): the kept rows are cut into S contiguous shards at subject
+// boundaries; shard s is owned by CTA s of every kernel, which alone reads and writes
+// L x exp(Xb) (E) on the shard's rows and M[L x exp(Xb)] (D) on its subjects.  The
+// only data CTAs exchange is the pair of partial sums per coordinate (Eqs. 7-9 are sums
+// over subjects), so a coordinate step needs one grid-wide all-reduce and no other barrier.
+//
+// Each column X_j is split into per-shard slices.  A slice's nonzeros are grouped by subject
+// into "segments" (the paper's COO rows of M X_j, Section 2.3), ordered by length, longest
+// first, and packed 32 to a group.  A group stores its rows diagonal by diagonal (jagged
+// diagonal order): diagonal t holds the t-th row of every segment longer than t, so the
+// lanes active at step t are exactly the first c_t lanes and every step is one coalesced
+// load.  A lane then owns one whole segment and sums its numerator with no cross-lane
+// traffic.
+#pragma once
+
+#include <cstdint>
+
+#include <vector_types.h>
+
+namespace sccs {
+
+constexpr int kMaxShards = 4096;
+constexpr int kWarp = 32;
+
+struct DevLayout {
+    int32_t S;                 // shards == CTAs
+    int32_t J;                 // columns
+    int64_t K;                 // kept rows
+    int64_t N;                 // kept subjects
+    // static structure
+    const int32_t *rows;       // JDS row index per nonzero (global kept-row id)
+    const int2 *segs;          // per segment: {subject id, length}
+    const int64_t *grp_base;   // per group: index into rows[] of its first diagonal
+    const int64_t *slice_row;  // S*(J+1): first rows[] index of slice (s, j)
+    const int64_t *slice_seg;  // S*(J+1): first segment of slice (s, j)
+    const int64_t *slice_grp;  // S*(J+1): first group of slice (s, j)
+    const int64_t *shard_row;  // S+1
+    const int64_t *shard_pat;  // S+1
+    const int64_t *pat_ptr;    // N+1: rows of subject i
+    const int32_t *nev;        // N: n_i
+    const double *L;           // K: offsets l_k
+    const double *ytx;         // J: Y'X_j
+    // state
+    double *E;                 // K: L x exp(Xb)
+    double *D;                 // N: M[L x exp(Xb)]
+    double *beta_priv;         // S*J: each CTA's private copy of beta (all copies agree)
+    double *trust_priv;        // S*J: each CTA's private trust radii
+    double *stash;             // S*stash_stride*2: (num, D) per segment beyond the register path
+    int64_t stash_stride;      // segments per shard
+    // grid all-reduce slots: 2 buffers x S slots x {a, b}; sign bit carries the phase
+    unsigned long long *slots;
+    int *abort_flag;           // set by a CTA that gives up; every wait checks it (lives in FitOut)
+};
+
+struct FitParams {
+    int32_t prior;             // SCCS_PRIOR_*
+    int32_t tol_mode;
+    double variance;
+    double lambda;             // Laplace sqrt(2/variance)
+    double tol;
+    int32_t max_cycles;
+    int32_t record_history;
+    unsigned long long seq0;   // all-reduce sequence number at launch
+    long long timeout_ns;      // bound on each device-side wait (from the start of that wait)
+};
+
+struct FitOut {
+    double logpost;
+    double conv;
+    double loglik;
+    int32_t cycles;
+    int32_t status;            // 0 ok, 1 not converged, negative error
+    int64_t nonzero_steps;
+    int32_t warnings;
+    int32_t err_where;         // diagnostic: which wait timed out
+    unsigned long long seq_end;
+    double g, h;               // grad_hess output
+    int32_t abort_flag;        // nonzero if any CTA gave up a wait
+    int32_t pad;
+};
+
+// Launchers (return cudaError_t as int).  `stream` is a cudaStream_t.
+int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, void *stream);
+int launch_fit(const DevLayout &d, const FitParams &p, FitOut *out_dev, double *hist_dev,
+               int threads, void *stream);
+int launch_grad_hess(const DevLayout &d, int32_t j, const FitParams &p, FitOut *out_dev,
+                     int threads, void *stream);
+// The gradient kernel on only `ctas` of the S CTAs the all-reduce counts (a wait-bound test).
+int launch_grad_hess_partial(const DevLayout &d, int32_t j, const FitParams &p, FitOut *out_dev,
+                             int threads, int ctas, void *stream);
+int fit_kernel_max_blocks_per_sm(int threads, int *blocks);
+
+}  // namespace sccs

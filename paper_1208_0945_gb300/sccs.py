@@ -1,0 +1,256 @@
+"""ctypes binding of libsccs.so: the C ABI of include/sccs.h, one Python name per entry point.
+
+Only argument marshalling happens here; every step of the fit runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library is missing this module raises at import.
+PyTorch, when present, only supplies the CUDA stream (and optionally the allocator).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libsccs.so")
+
+OK, NOT_CONVERGED, PENDING = 0, 1, 2
+E_INVAL, E_UNSORTED, E_NONBINARY, E_NOMEM, E_CUDA = -1, -2, -3, -4, -5
+E_TIMEOUT, E_NUMERIC, E_BUSY, E_DUPLICATE, E_UNSUPPORTED = -6, -7, -8, -9, -10
+PRIOR = {"none": 0, "normal": 1, "laplace": 2}
+TOL = {"abs_logpost": 0, "rel_logpost": 1, "genkin_xbeta": 2}
+PREC = {"fp64": 0}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class sccs_create_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("num_shards", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("alloc", _alloc_fn), ("free", _free_fn), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class sccs_data_info(ctypes.Structure):
+    _fields_ = [("rows_in", ctypes.c_int64), ("rows_kept", ctypes.c_int64), ("subjects_in", ctypes.c_int64),
+                ("subjects_kept", ctypes.c_int64), ("nnz_kept", ctypes.c_int64), ("segments", ctypes.c_int64),
+                ("max_column_nnz", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("upload_bytes", ctypes.c_int64),
+                ("columns", ctypes.c_int32), ("num_shards", ctypes.c_int32),
+                ("threads_per_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class sccs_fit_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("warm_start", ctypes.c_int32),
+                ("beta0", ctypes.POINTER(ctypes.c_double)), ("tol_mode", ctypes.c_int32),
+                ("max_cycles", ctypes.c_int32), ("tol", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("logpost_history", ctypes.POINTER(ctypes.c_double))]
+
+
+class sccs_fit_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("cycles", ctypes.c_int32), ("steps", ctypes.c_int64),
+                ("nonzero_steps", ctypes.c_int64), ("logpost", ctypes.c_double), ("conv_value", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("warnings", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "sccs_version": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_char_p)]),
+    "sccs_last_error": (ctypes.c_char_p, [_P]),
+    "sccs_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int64, _P, _P, _P, ctypes.c_int32, _P, _P, _P,
+                                   ctypes.POINTER(sccs_create_opts)]),
+    "sccs_destroy": (ctypes.c_int, [_P]),
+    "sccs_get_info": (ctypes.c_int, [_P, ctypes.POINTER(sccs_data_info)]),
+    "sccs_set_prior": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double]),
+    "sccs_fit": (ctypes.c_int, [_P, ctypes.POINTER(sccs_fit_opts), _dp, ctypes.POINTER(sccs_fit_info)]),
+    "sccs_grad_hess": (ctypes.c_int, [_P, ctypes.c_int32, _dp, _dp, _dp]),
+    "sccs_logpost": (ctypes.c_int, [_P, _dp, _dp, _dp]),
+    "sccs_get_beta": (ctypes.c_int, [_P, _dp]),
+    "sccs_check_wait_timeout": (ctypes.c_int, [_P, ctypes.c_double]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class SCCSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = sccs_last_error(None)
+        super().__init__(f"{where} returned {code}: {msg}")
+        self.code = code
+
+
+def _check(code: int, where: str) -> int:
+    if code < 0:
+        raise SCCSError(code, where)
+    return code
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _dptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+# ------------------------------------------------------------------ the C ABI, name for name
+
+def sccs_version() -> tuple[int, str]:
+    v = ctypes.c_int32()
+    s = ctypes.c_char_p()
+    _lib.sccs_version(ctypes.byref(v), ctypes.byref(s))
+    return v.value, s.value.decode()
+
+
+def sccs_last_error(handle) -> str:
+    r = _lib.sccs_last_error(handle)
+    return r.decode() if r else ""
+
+
+def sccs_create(K, patient_id, y, offset_L, J, col_ptr, row_idx, x_values=None, *, device=0, stream=None,
+                num_shards=0, threads_per_block=0):
+    """Returns an opaque handle (int).  Arrays are copied by the library before it returns."""
+    pid = np.ascontiguousarray(patient_id, np.int64)
+    yy = np.ascontiguousarray(y, np.int32)
+    LL = np.ascontiguousarray(offset_L, np.float64)
+    cp = np.ascontiguousarray(col_ptr, np.int64)
+    ri = np.ascontiguousarray(row_idx, np.int32)
+    xv = None if x_values is None else np.ascontiguousarray(x_values, np.float64)
+    o = sccs_create_opts(struct_size=ctypes.sizeof(sccs_create_opts), device=int(device),
+                         stream=stream, num_shards=int(num_shards), threads_per_block=int(threads_per_block))
+    h = ctypes.c_void_p()
+    _check(_lib.sccs_create(ctypes.byref(h), int(K), _ptr(pid), _ptr(yy), _ptr(LL), int(J), _ptr(cp), _ptr(ri),
+                            _ptr(xv), ctypes.byref(o)), "sccs_create")
+    return h.value
+
+
+def sccs_destroy(handle) -> int:
+    return _lib.sccs_destroy(handle)
+
+
+def sccs_get_info(handle) -> dict:
+    info = sccs_data_info()
+    _check(_lib.sccs_get_info(handle, ctypes.byref(info)), "sccs_get_info")
+    return {name: getattr(info, name) for name, _ in sccs_data_info._fields_ if name != "reserved"}
+
+
+def sccs_set_prior(handle, prior: str | int, variance: float = 1.0) -> int:
+    pt = PRIOR[prior] if isinstance(prior, str) else int(prior)
+    return _check(_lib.sccs_set_prior(handle, pt, float(variance)), "sccs_set_prior")
+
+
+def sccs_fit(handle, J: int, *, beta0=None, warm_start=False, tol_mode="rel_logpost", tol=1e-12,
+             max_cycles=1000, precision="fp64", history=False) -> dict:
+    b0 = None if beta0 is None else np.ascontiguousarray(beta0, np.float64)
+    hist = np.full(max_cycles + 1, np.nan) if history else None
+    o = sccs_fit_opts(struct_size=ctypes.sizeof(sccs_fit_opts), warm_start=int(bool(warm_start)),
+                      beta0=_dptr(b0), tol_mode=TOL[tol_mode], max_cycles=int(max_cycles), tol=float(tol),
+                      precision=PREC[precision], logpost_history=_dptr(hist))
+    beta = np.zeros(max(J, 1))
+    info = sccs_fit_info()
+    rc = _check(_lib.sccs_fit(handle, ctypes.byref(o), _dptr(beta), ctypes.byref(info)), "sccs_fit")
+    out = {name: getattr(info, name) for name, _ in sccs_fit_info._fields_ if name != "reserved"}
+    out["rc"] = rc
+    out["beta"] = beta[:J]
+    if history:
+        out["history"] = hist[:info.cycles + 1]
+    return out
+
+
+def sccs_grad_hess(handle, j: int, beta=None) -> tuple[float, float]:
+    b = None if beta is None else np.ascontiguousarray(beta, np.float64)
+    g, h = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.sccs_grad_hess(handle, int(j), _dptr(b), ctypes.byref(g), ctypes.byref(h)), "sccs_grad_hess")
+    return g.value, h.value
+
+
+def sccs_logpost(handle, beta=None) -> tuple[float, float]:
+    b = None if beta is None else np.ascontiguousarray(beta, np.float64)
+    lp, ll = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.sccs_logpost(handle, _dptr(b), ctypes.byref(lp), ctypes.byref(ll)), "sccs_logpost")
+    return lp.value, ll.value
+
+
+def sccs_get_beta(handle, J: int) -> np.ndarray:
+    b = np.zeros(max(J, 1))
+    _check(_lib.sccs_get_beta(handle, _dptr(b)), "sccs_get_beta")
+    return b[:J]
+
+
+def sccs_check_wait_timeout(handle, timeout_ms: float) -> int:
+    """Returns the raw status; E_TIMEOUT (-6) is the expected result."""
+    return _lib.sccs_check_wait_timeout(handle, float(timeout_ms))
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return None
+
+
+class SCCSModel:
+    """One dataset resident on the GPU, fitted through the C ABI."""
+
+    def __init__(self, data=None, *, K=None, patient_id=None, y=None, L=None, J=None, col_ptr=None,
+                 row_idx=None, x_values=None, device=0, stream="torch", num_shards=0, threads_per_block=0):
+        if data is not None:
+            K, patient_id, y, L, J = data.K, data.patient_id, data.y, data.L, data.J
+            col_ptr, row_idx = data.col_ptr, data.row_idx
+        st = _torch_stream() if stream == "torch" else stream
+        self.J = int(J)
+        self.handle = sccs_create(K, patient_id, y, L, J, col_ptr, row_idx, x_values, device=device, stream=st,
+                                  num_shards=num_shards, threads_per_block=threads_per_block)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sccs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def info(self) -> dict:
+        return sccs_get_info(self.handle)
+
+    def set_prior(self, prior="normal", variance=1.0):
+        sccs_set_prior(self.handle, prior, variance)
+        return self
+
+    def fit(self, **kw) -> dict:
+        return sccs_fit(self.handle, self.J, **kw)
+
+    def grad_hess(self, j, beta=None):
+        return sccs_grad_hess(self.handle, j, beta)
+
+    def logpost(self, beta=None):
+        return sccs_logpost(self.handle, beta)
+
+    @property
+    def beta(self) -> np.ndarray:
+        return sccs_get_beta(self.handle, self.J)

@@ -1,0 +1,275 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Tolerances (FP64 path):
+  g_j, h_j                      relative 1e-12 (both sides sum the same terms in FP64; the
+                                orders differ, so a few ulps of each of ~1e3 terms)
+  fixed-cycle trajectories      |d beta| <= 1e-11, relative d P <= 1e-12 (Normal prior)
+  converged fits                |d beta| <= 1e-8, relative d P <= 1e-10 (the stated bar)
+"""
+import numpy as np
+import pytest
+
+import oracle
+from sccs_testlib import from_dense, random_tiny, to_dense
+from synth import make_dataset, mid_fit_config, paper_scale_config, tiny_fit_config
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1208_0945_gb300 as P
+    return P
+
+
+def gpu_model(P, d, **kw):
+    return P.SCCSModel(d, device=0, **kw)
+
+
+def rel(a, b):
+    return abs(a - b) / max(1.0, abs(b))
+
+
+def check_grad_hess(P, d, betas, columns=None, **kw):
+    orc = oracle.Problem.from_data(d)
+    with gpu_model(P, d, **kw) as m:
+        for beta in betas:
+            for j in (range(d.J) if columns is None else columns):
+                g, h = m.grad_hess(j, beta)
+                go, ho = orc.grad_hess(j, beta)
+                scale_g = max(1.0, abs(go))
+                assert abs(g - go) <= 1e-12 * scale_g + 1e-12 * abs(ho), (j, g, go)
+                assert abs(h - ho) <= 1e-12 * max(1.0, abs(ho)), (j, h, ho)
+
+
+def test_grad_hess_tiny_config(P):
+    d, _ = tiny_fit_config()
+    rng = np.random.default_rng(0)
+    check_grad_hess(P, d, [np.zeros(d.J), rng.normal(0, 0.3, d.J)])
+
+
+@pytest.mark.parametrize("shards,threads", [(1, 64), (7, 128), (64, 512), (0, 256)])
+def test_grad_hess_across_launch_shapes(P, shards, threads):
+    """Several tiles per slice and ragged tails: 30k subjects, columns from 0.1% to 30% density."""
+    d = make_dataset(n_patients=30000, eras=("geometric", 6), J=12, columns=("density_range", 0.001, 0.3),
+                     n_true=4, beta_sd=0.4, seed=77)
+    rng = np.random.default_rng(1)
+    check_grad_hess(P, d, [rng.normal(0, 0.4, d.J)], num_shards=shards, threads_per_block=threads)
+
+
+def test_logpost_matches_oracle(P):
+    d, _ = tiny_fit_config()
+    orc = oracle.Problem.from_data(d)
+    rng = np.random.default_rng(3)
+    with gpu_model(P, d) as m:
+        for prior, var in (("none", 1.0), ("normal", 0.5), ("laplace", 0.2)):
+            m.set_prior(prior, var)
+            for _ in range(3):
+                b = rng.normal(0, 0.5, d.J)
+                lp, ll = m.logpost(b)
+                assert rel(ll, orc.loglik(b)) <= 1e-12
+                assert rel(lp, orc.logpost(b, prior, var)) <= 1e-12
+
+
+@pytest.mark.parametrize("prior,var", [("normal", 1.0), ("normal", 0.1), ("none", 1.0)])
+def test_fixed_cycle_trajectory(P, prior, var):
+    d, _ = tiny_fit_config()
+    ref = oracle.Problem.from_data(d).fit(prior=prior, variance=var, fixed_cycles=3)
+    with gpu_model(P, d) as m:
+        m.set_prior(prior, var)
+        r = m.fit(tol=-1.0, max_cycles=3, history=True)
+    assert r["cycles"] == 3
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11, rtol=0)
+    for a, b in zip(r["history"], ref["history"]):
+        assert rel(a, b) <= 1e-12
+    assert r["nonzero_steps"] == ref["nonzero_steps"]
+
+
+def test_converged_tiny_config(P):
+    d, fit = tiny_fit_config()
+    ref = oracle.Problem.from_data(d).fit(prior=fit["prior"], variance=fit["variance"],
+                                          tol_mode=fit["tol_mode"], tol=fit["tol"])
+    with gpu_model(P, d) as m:
+        m.set_prior(fit["prior"], fit["variance"])
+        r = m.fit(tol_mode=fit["tol_mode"], tol=fit["tol"], max_cycles=fit["max_cycles"], history=True)
+    assert r["rc"] == 0
+    assert r["cycles"] == ref["cycles"]
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-8, rtol=0)
+    assert rel(r["logpost"], ref["logpost"]) <= 1e-10
+    h = r["history"]
+    assert np.all(np.diff(h) >= -1e-13 * np.abs(h[1:]) - 1e-12)  # monotone ascent
+
+
+@pytest.mark.parametrize("var", [0.05, 0.5])
+def test_converged_laplace(P, var):
+    """Laplace prior: soft-threshold decisions may flip transiently near |g| = lambda, so
+    only converged results are compared (tight stop on both sides)."""
+    d, _ = paper_scale_config(scale=0.004)  # 16k subjects, 5000 drugs, Zipf(1.1) sizes
+    ref = oracle.Problem.from_data(d).fit(prior="laplace", variance=var, tol_mode="rel_logpost", tol=1e-15,
+                                          max_cycles=300)
+    with gpu_model(P, d) as m:
+        m.set_prior("laplace", var)
+        r = m.fit(tol_mode="rel_logpost", tol=1e-15, max_cycles=300)
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-8, rtol=0)
+    assert rel(r["logpost"], ref["logpost"]) <= 1e-10
+    assert np.array_equal(r["beta"] == 0, ref["beta"] == 0)
+
+
+def test_mid_config_reduced_scale(P):
+    """The 1,000-drug Zipf(1.2) recipe at 2% of its subjects: trajectories and converged fit."""
+    d, fit = mid_fit_config(scale=0.02)
+    orc = oracle.Problem.from_data(d)
+    ref3 = orc.fit(prior="normal", variance=fit["variance"], fixed_cycles=2)
+    ref = orc.fit(prior="normal", variance=fit["variance"], tol_mode="rel_logpost", tol=1e-14, max_cycles=200)
+    with gpu_model(P, d) as m:
+        m.set_prior("normal", fit["variance"])
+        r3 = m.fit(tol=-1.0, max_cycles=2)
+        r = m.fit(tol_mode="rel_logpost", tol=1e-14, max_cycles=200)
+    np.testing.assert_allclose(r3["beta"], ref3["beta"], atol=1e-11, rtol=0)
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-8, rtol=0)
+    assert rel(r["logpost"], ref["logpost"]) <= 1e-10
+
+
+def test_full_mid_config_as_benchmarked(P):
+    """The benchmarked workload (1M subjects, ~10M eras, 1,000 drugs) in the bench's launch
+    shape: the whole fit against the oracle's, plus sampled g_j at the fitted beta."""
+    d, fit = mid_fit_config()
+    orc = oracle.Problem.from_data(d)
+    ref = orc.fit(prior="normal", variance=fit["variance"], tol_mode=fit["tol_mode"], tol=fit["tol"])
+    with gpu_model(P, d) as m:
+        m.set_prior("normal", fit["variance"])
+        r = m.fit(tol_mode=fit["tol_mode"], tol=fit["tol"], max_cycles=fit["max_cycles"])
+        assert r["cycles"] == ref["cycles"]
+        np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-8, rtol=0)
+        assert rel(r["logpost"], ref["logpost"]) <= 1e-10
+        for j in (0, 1, 2, 500, 999):
+            g, h = m.grad_hess(j, ref["beta"])
+            go, ho = orc.grad_hess(j, ref["beta"])
+            assert abs(g - go) <= 1e-10 * max(1.0, abs(ho)), j
+            assert rel(h, ho) <= 1e-11, j
+
+
+def test_repeat_fits_are_bitwise_identical(P):
+    d, _ = mid_fit_config(scale=0.01)
+    with gpu_model(P, d) as m:
+        m.set_prior("normal", 0.1)
+        a = m.fit(tol=1e-13)
+        b = m.fit(tol=1e-13)
+    assert np.array_equal(a["beta"], b["beta"]) and a["logpost"] == b["logpost"]
+
+
+def test_results_do_not_depend_on_launch_shape(P):
+    d = make_dataset(n_patients=20000, eras=("geometric", 8), J=30, columns=("density_range", 0.005, 0.1),
+                     n_true=5, beta_sd=0.5, seed=5)
+    outs = []
+    for shards, threads in ((0, 512), (13, 96), (1, 64)):
+        with gpu_model(P, d, num_shards=shards, threads_per_block=threads) as m:
+            m.set_prior("normal", 0.3)
+            outs.append(m.fit(tol=1e-14, max_cycles=300))
+    for o in outs[1:]:
+        np.testing.assert_allclose(o["beta"], outs[0]["beta"], atol=1e-10, rtol=0)
+
+
+def test_warm_start_and_beta0(P):
+    d, _ = tiny_fit_config()
+    orc = oracle.Problem.from_data(d)
+    b0 = np.random.default_rng(9).normal(0, 0.2, d.J)
+    ref = orc.fit(prior="normal", variance=0.4, beta0=b0, fixed_cycles=2)
+    with gpu_model(P, d) as m:
+        m.set_prior("normal", 0.4)
+        r = m.fit(beta0=b0, tol=-1.0, max_cycles=2)
+        np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11, rtol=0)
+        # warm start continues from the previous fit
+        ref2 = orc.fit(prior="normal", variance=0.4, beta0=ref["beta"], fixed_cycles=1)
+        r2 = m.fit(warm_start=True, tol=-1.0, max_cycles=1)
+        np.testing.assert_allclose(r2["beta"], ref2["beta"], atol=1e-11, rtol=0)
+        np.testing.assert_allclose(m.beta, r2["beta"], atol=0, rtol=0)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_edge_empty_columns_and_zero_event_subjects(P):
+    d0 = random_tiny(2, n_patients=40, J=5, density=0.3, with_zero_subjects=True, beta_scale=0.4)
+    X = to_dense(d0)
+    X[:, 2] = 0.0                                  # an empty column
+    d = from_dense(d0.patient_id, d0.y, d0.L, X)
+    ref = oracle.Problem.from_data(d).fit(prior="normal", variance=0.7, tol=1e-14, max_cycles=500)
+    with gpu_model(P, d) as m:
+        info = m.info
+        assert info["subjects_in"] - info["subjects_kept"] > 0
+        m.set_prior("normal", 0.7)
+        r = m.fit(tol_mode="abs_logpost", tol=1e-14, max_cycles=500)
+    assert r["beta"][2] == 0.0
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-8, rtol=0)
+
+
+def test_edge_column_covering_whole_subjects(P):
+    """W_i = 1 for every touched subject: h_j = 0 and g_j = 0 (flat direction)."""
+    pid = np.repeat(np.arange(6), 3)
+    X = np.zeros((18, 2))
+    X[0:3, 0] = 1.0      # all eras of subject 0
+    X[6:9, 0] = 1.0      # all eras of subject 2
+    X[1::3, 1] = 1.0
+    y = np.tile([1, 0, 2], 6)
+    d = from_dense(pid, y, np.arange(1, 19, dtype=float), X)
+    orc = oracle.Problem.from_data(d)
+    with gpu_model(P, d) as m:
+        g, h = m.grad_hess(0, np.array([0.3, -0.2]))
+        go, ho = orc.grad_hess(0, np.array([0.3, -0.2]))
+        assert abs(h) <= 1e-14 and abs(g) <= 1e-12
+        assert abs(g - go) <= 1e-12 and abs(h - ho) <= 1e-12
+        m.set_prior("laplace", 0.5)
+        r = m.fit(tol_mode="abs_logpost", tol=1e-14, max_cycles=200)
+    ref = orc.fit(prior="laplace", variance=0.5, tol_mode="abs_logpost", tol=1e-14, max_cycles=200)
+    assert r["beta"][0] == 0.0
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-8)
+
+
+def test_edge_single_subject_and_single_column(P):
+    pid = np.zeros(4, np.int64)
+    X = np.array([[1.0], [0.0], [1.0], [0.0]])
+    d = from_dense(pid, [2, 1, 0, 1], [10.0, 20.0, 30.0, 40.0], X)
+    ref = oracle.Problem.from_data(d).fit(prior="none", tol=1e-15, max_cycles=300)
+    with gpu_model(P, d) as m:
+        r = m.fit(tol_mode="abs_logpost", tol=1e-15, max_cycles=300)
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-9)
+    # closed form: A = 2 exposed events of n = 4, exposed time 40 vs unexposed 60
+    assert r["beta"][0] == pytest.approx(np.log(2 / 2) - np.log(40 / 60), abs=1e-9)
+
+
+def test_edge_duplicate_rows_rejected(P):
+    pid = np.array([0, 0, 1], np.int64)
+    with pytest.raises(P.SCCSError) as ei:
+        P.sccs_create(3, pid, np.array([1, 0, 1], np.int32), np.ones(3), 1, np.array([0, 2], np.int64),
+                      np.array([1, 1], np.int32))
+    assert ei.value.code == -9
+
+
+def test_edge_no_columns_and_max_cycles_zero(P):
+    d, _ = tiny_fit_config()
+    orc = oracle.Problem.from_data(d)
+    with gpu_model(P, d) as m:
+        m.set_prior("normal", 1.0)
+        r = m.fit(max_cycles=0)
+        assert r["cycles"] == 0 and r["rc"] == 1
+        assert rel(r["logpost"], orc.logpost(np.zeros(d.J), "normal", 1.0)) <= 1e-12
+    d0 = from_dense(d.patient_id, d.y, d.L, np.zeros((d.K, 0)))
+    with gpu_model(P, d0) as m:
+        r = m.fit(max_cycles=3, tol=-1.0)
+        assert r["cycles"] == 3
+        assert rel(r["logpost"], oracle.Problem.from_data(d0).loglik(np.zeros(0))) <= 1e-12
+
+
+# ------------------------------------------------------------------ failure detection
+
+def test_bounded_wait_times_out_and_handle_recovers(P):
+    """One CTA fewer than the all-reduce counts: every wait must run out (~0.2 s), report
+    SCCS_E_TIMEOUT, and leave a usable handle."""
+    d, fit = tiny_fit_config()
+    ref = oracle.Problem.from_data(d).fit(prior="normal", variance=1.0, fixed_cycles=2)
+    with gpu_model(P, d) as m:
+        rc = P.sccs_check_wait_timeout(m.handle, 200.0)
+        assert rc == -6
+        m.set_prior("normal", 1.0)
+        r = m.fit(tol=-1.0, max_cycles=2)
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11)
