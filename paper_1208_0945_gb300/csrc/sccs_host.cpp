@@ -127,10 +127,16 @@ int set_device(const sccs_handle *h) {
     return SCCS_OK;
 }
 
+// Copy `count` elements to a new device array; `pad` zeroed bytes follow them (arrays read
+// by bulk copies rounded out to 16-byte boundaries).
 template <class T>
-int upload(sccs_handle *h, T **dst, const T *src, size_t count) {
-    *dst = static_cast<T *>(h->arena.get(count * sizeof(T)));
+int upload(sccs_handle *h, T **dst, const T *src, size_t count, size_t pad = 0) {
+    *dst = static_cast<T *>(h->arena.get(count * sizeof(T) + pad));
     if (!*dst) return fail(SCCS_E_NOMEM, "device allocation failed");
+    if (pad) {
+        cudaError_t e = cudaMemsetAsync(reinterpret_cast<char *>(*dst) + count * sizeof(T), 0, pad, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
     if (count) {
         cudaError_t e = cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
@@ -442,6 +448,7 @@ sccs::FitParams base_params(const sccs_handle *h) {
     sccs::FitParams p{};
     p.prior = h->prior;
     p.variance = h->variance;
+    p.inv_var = 1.0 / h->variance;
     p.lambda = h->prior == SCCS_PRIOR_LAPLACE ? std::sqrt(2.0 / h->variance) : 0.0;
     p.tol_mode = SCCS_TOL_REL_LOGPOST;
     p.tol = 1e-12;
@@ -543,9 +550,9 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     int64_t *grp_base, *slice_row, *slice_seg, *slice_grp, *shard_row, *shard_pat, *pat_ptr;
     int32_t *nev;
     double *L, *ytx;
-    if ((rc = upload(h, &rows, hl.rows.data(), hl.rows.size())) ||
-        (rc = upload(h, &segs, hl.segs.data(), hl.segs.size())) ||
-        (rc = upload(h, &grp_base, hl.grp_base.data(), hl.grp_base.size())) ||
+    if ((rc = upload(h, &rows, hl.rows.data(), hl.rows.size(), sccs::kCopyPad)) ||
+        (rc = upload(h, &segs, hl.segs.data(), hl.segs.size(), sccs::kCopyPad)) ||
+        (rc = upload(h, &grp_base, hl.grp_base.data(), hl.grp_base.size(), sccs::kCopyPad)) ||
         (rc = upload(h, &slice_row, hl.slice_row.data(), hl.slice_row.size())) ||
         (rc = upload(h, &slice_seg, hl.slice_seg.data(), hl.slice_seg.size())) ||
         (rc = upload(h, &slice_grp, hl.slice_grp.data(), hl.slice_grp.size())) ||

@@ -15,6 +15,7 @@
 // traffic.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 
 #include <vector_types.h>
@@ -23,6 +24,14 @@ namespace sccs {
 
 constexpr int kMaxShards = 4096;
 constexpr int kWarp = 32;
+
+// Slices up to these sizes are staged in shared memory by bulk copies one column ahead.
+constexpr int kSegCap = 2048;              // segments per staged slice
+constexpr int kRowCap = 4096;              // nonzeros per staged slice
+constexpr int kGrpCap = kSegCap / 32;      // groups per staged slice
+// Global arrays read by bulk copies are padded by this many bytes past their end, so a copy
+// rounded out to 16-byte boundaries stays inside the allocation.
+constexpr int kCopyPad = 32;
 
 struct DevLayout {
     int32_t S;                 // shards == CTAs
@@ -47,7 +56,7 @@ struct DevLayout {
     double *D;                 // N: M[L x exp(Xb)]
     double *beta_priv;         // S*J: each CTA's private copy of beta (all copies agree)
     double *trust_priv;        // S*J: each CTA's private trust radii
-    double *stash;             // S*stash_stride*2: (num, D) per segment beyond the register path
+    double *stash;             // S*stash_stride*2: (num, D) per segment of slices too big to stage
     int64_t stash_stride;      // segments per shard
     // grid all-reduce slots: 2 buffers x S slots x {a, b}; sign bit carries the phase
     unsigned long long *slots;
@@ -58,6 +67,7 @@ struct FitParams {
     int32_t prior;             // SCCS_PRIOR_*
     int32_t tol_mode;
     double variance;
+    double inv_var;            // 1 / variance
     double lambda;             // Laplace sqrt(2/variance)
     double tol;
     int32_t max_cycles;
@@ -80,6 +90,9 @@ struct FitOut {
     int32_t abort_flag;        // nonzero if any CTA gave up a wait
     int32_t pad;
 };
+
+// Dynamic shared memory the fit kernel needs.
+size_t fit_kernel_smem_bytes();
 
 // Launchers (return cudaError_t as int).  `stream` is a cudaStream_t.
 int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, void *stream);

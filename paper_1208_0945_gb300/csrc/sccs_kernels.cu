@@ -7,18 +7,30 @@
 //      M[L x exp(Xb) x X_j] of Eq. 8, restricted to the touched subjects), forms
 //      W_i = num_i / D_i and the partial sums  sum n_i W_i  and  sum n_i W_i (1 - W_i)
 //      (the fused transformation and reduction of Section 2.4, with W never stored);
-//   -  joins one grid all-reduce of the two partials (fixed summation order, so all CTAs
-//      hold bit-identical totals), then computes g_j, h_j (Eqs. 7, 9) and the step db_j
-//      (Eq. 4 with the prior of Eq. 3 and a Genkin trust region) redundantly;
+//   -  joins one grid all-reduce of the two partials, then one lane computes g_j, h_j
+//      (Eqs. 7, 9) and the step db_j (Eq. 4 with the prior of Eq. 3 and a Genkin trust
+//      region) and broadcasts db_j, e^{db_j} and e^{db_j} - 1;
 //   C  if db_j != 0, updates its own rows and subjects (Section 2.3 steps 1-3):
-//      E_k <- E_k e^{db}  (= l_k exp(Xb_k + db), one exp per coordinate instead of one per
+//      E_k <- E_k e^{db}  (= l_k exp(Xb_k + db): one exp per coordinate instead of one per
 //      nonzero), and D_i <- D_i + (e^{db} - 1) num_i (= D_i + sum_k (E_k,new - E_k,old)).
-// Because no CTA ever touches another shard's rows, phase C needs no grid barrier: the only
-// cross-CTA traffic is the 16-byte partial per CTA per coordinate.  At the end of a cycle
-// each CTA recomputes D from E on its subjects, and the log-posterior is all-reduced.
+// No CTA ever touches another shard's rows, so phase C needs no grid barrier: the only
+// cross-CTA traffic is 16 bytes per CTA per coordinate.  At the end of a cycle each CTA
+// recomputes D from E on its subjects and the log-posterior is all-reduced.
+//
+// GB300 specifics:
+//   * The static part of a column's slice (segments, rows, group offsets) is staged into
+//     shared memory by bulk asynchronous copies (cp.async.bulk + mbarrier) one column ahead,
+//     so only the gathers of the state E and D remain on the critical path.
+//   * FP64 issues at one warp-instruction per 64 cycles per SM sub-partition, whatever the
+//     number of active lanes, so every reduction (lane -> warp -> CTA -> grid) is done in
+//     exact 192-bit fixed point with integer instructions.  Exact sums are independent of
+//     order: all CTAs obtain bit-identical totals, and results do not depend on the launch
+//     shape.  FP64 is kept for the per-subject arithmetic and the scalar step, which one
+//     lane computes once per coordinate.
 //
 // Every wait is bounded by a deadline on %globaltimer; a CTA that gives up raises the abort
-// flag and returns, and the others see the flag and return too.
+// flag, waits (bounded) for its own bulk copies in flight and returns; the others see the
+// flag and return too.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -30,8 +42,9 @@ namespace sccs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kUnroll = 4;       // diagonals of a warp's first group held in registers
+constexpr int kBatch = 8;        // diagonals gathered per batch
 constexpr int kMaxWarps = 32;
+constexpr int kFrac = 128;       // fraction bits of the fixed-point sums (value = V * 2^-128)
 
 // status values written to FitOut
 constexpr int kStOk = 0;
@@ -39,20 +52,21 @@ constexpr int kStNotConverged = 1;
 constexpr int kStTimeout = -6;
 constexpr int kStNumeric = -7;
 
+// ------------------------------------------------------------------ timers, memory order
+
 __device__ __forceinline__ long long now_ns() {
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
 
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
+__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long *p, unsigned long long &a,
+                                              unsigned long long &b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed_v2(unsigned long long *p, unsigned long long a, unsigned long long b) {
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
 
 __device__ __forceinline__ int ld_relaxed_i32(const int *p) {
@@ -61,45 +75,257 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p) {
     return v;
 }
 
-// A non-negative double with its sign bit replaced by the phase bit.
-__device__ __forceinline__ unsigned long long enc(double v, unsigned long long phase) {
-    unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(fabs(v)));
-    return (b & 0x7fffffffffffffffull) | (phase << 63);
+// ------------------------------------------------------------------ bulk copies, mbarriers
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ double dec(unsigned long long b) {
-    return __longlong_as_double(static_cast<long long>(b & 0x7fffffffffffffffull));
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
+
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of a bulk-copy barrier.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long deadline = now_ns() + timeout_ns;
+    for (int it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31) == 31 && now_ns() > deadline) return false;
+    }
+}
+
+// ------------------------------------------------------------------ exact fixed-point sums
+
+// A non-negative value V * 2^-128 held in three 64-bit limbs (w0 least significant).
+struct Fx {
+    unsigned long long w0, w1, w2;
+};
+
+__device__ __forceinline__ Fx fx_zero() { return Fx{0ull, 0ull, 0ull}; }
+
+__device__ __forceinline__ Fx fx_add(const Fx &a, const Fx &b) {
+    Fx r;
+    r.w0 = a.w0 + b.w0;
+    const unsigned long long c0 = r.w0 < a.w0;
+    const unsigned long long t1 = a.w1 + b.w1;
+    const unsigned long long c1a = t1 < a.w1;
+    r.w1 = t1 + c0;
+    const unsigned long long c1b = r.w1 < t1;
+    r.w2 = a.w2 + b.w2 + c1a + c1b;
+    return r;
+}
+
+// Exact conversion of a finite non-negative double below 2^60; bits below 2^-128 are
+// dropped.  Anything else (negative, NaN, inf, huge) sets `bad`.
+__device__ __forceinline__ Fx fx_from_double(double v, bool &bad) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+    const int e = static_cast<int>((b >> 52) & 0x7ff);
+    Fx r = fx_zero();
+    if ((b >> 63) && b != 0x8000000000000000ull) {  // negative (minus zero is zero)
+        bad = true;
+        return r;
+    }
+    if (e == 0) return r;                        // zero or subnormal
+    if (e >= 1023 + 60) {                        // >= 2^60, inf or NaN
+        bad = true;
+        return r;
+    }
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = e - 1075 + kFrac;             // v = m * 2^(e - 1075)
+    if (sh < 0) {
+        if (sh > -64) r.w0 = m >> (-sh);
+        return r;
+    }
+    const int q = sh >> 6, rm = sh & 63;
+    const unsigned long long lo = m << rm;
+    const unsigned long long hi = rm ? (m >> (64 - rm)) : 0ull;
+    if (q == 0) {
+        r.w0 = lo;
+        r.w1 = hi;
+    } else if (q == 1) {
+        r.w1 = lo;
+        r.w2 = hi;
+    } else {
+        r.w2 = lo;
+    }
+    return r;
+}
+
+// Round-to-nearest-even conversion back to double.
+__device__ __forceinline__ double fx_to_double(const Fx &v) {
+    int p;
+    if (v.w2) p = 128 + 63 - __clzll(static_cast<long long>(v.w2));
+    else if (v.w1) p = 64 + 63 - __clzll(static_cast<long long>(v.w1));
+    else if (v.w0) p = 63 - __clzll(static_cast<long long>(v.w0));
+    else return 0.0;
+    // W = bits [p-63, p] of V; sticky = any bit below p-63
+    unsigned long long W;
+    bool sticky = false;
+    if (p < 63) {
+        W = v.w0 << (63 - p);
+    } else {
+        const int s = p - 63;
+        const int q = s >> 6, r = s & 63;
+        const unsigned long long L0 = q == 0 ? v.w0 : (q == 1 ? v.w1 : v.w2);
+        const unsigned long long L1 = q == 0 ? v.w1 : (q == 1 ? v.w2 : 0ull);
+        W = r ? ((L0 >> r) | (L1 << (64 - r))) : L0;
+        const unsigned long long below = r ? (L0 & ((1ull << r) - 1)) : 0ull;
+        sticky = below != 0 || (q >= 1 && v.w0 != 0) || (q >= 2 && v.w1 != 0);
+    }
+    unsigned long long m = W >> 11;
+    const unsigned long long rb = (W >> 10) & 1ull;
+    sticky = sticky || (W & 0x3ffull) != 0;
+    long long biased = static_cast<long long>(p) - kFrac + 1023;
+    if (rb && (sticky || (m & 1ull))) {
+        m += 1;
+        if (m == (1ull << 53)) {
+            m >>= 1;
+            biased += 1;
+        }
+    }
+    const unsigned long long bits = (static_cast<unsigned long long>(biased) << 52) | (m & 0xfffffffffffffull);
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
+__device__ __forceinline__ Fx fx_shfl_down(const Fx &v, int o) {
+    Fx r;
+    r.w0 = __shfl_down_sync(kFull, v.w0, o);
+    r.w1 = __shfl_down_sync(kFull, v.w1, o);
+    r.w2 = __shfl_down_sync(kFull, v.w2, o);
+    return r;
+}
+
+// Exact warp sum; the total is in lane 0.
+__device__ __forceinline__ Fx fx_warp_sum(Fx v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fx_add(v, fx_shfl_down(v, o));
+    return v;
+}
+
+// ------------------------------------------------------------------ shared state
+
+struct StageBuf {
+    int2 segs[kSegCap + 2];          // 16,400 B
+    int32_t rows[kRowCap + 8];       // 16,416 B
+    long long grp[kGrpCap + 2];      //    528 B
+};
+
+struct ColDesc {
+    long long seg0, row0, grp0;
+    int nseg, nnz, ngrp, staged;
+    int seg_off, row_off, grp_off, pad;
+};
+
+struct SharedState {
+    Fx wa[kMaxWarps];
+    Fx wb[kMaxWarps];
+    int wbad[kMaxWarps];
+    double db, r, em1;
+    double G, H;
+    int ok;
+    int stop;
+    ColDesc desc[2];
+    uint64_t bar[2];
+};
+
+struct SmemLayout {
+    StageBuf stage[2];
+    double est[kRowCap];             // E gathered in phase A, per row position
+    double2 seg_stash[kSegCap];      // (num, D) per segment
+};
+
+// ------------------------------------------------------------------ grid all-reduce
 
 // Grid all-reduce of two non-negative partials, run by one full warp of every CTA.
 // Slot buffer (seq & 1) holds this round; the sign bit of each value equals the round's
 // phase ((seq >> 1) & 1) ^ 1, which differs from what the buffer held two rounds earlier,
-// so a reader can tell a fresh value from a stale one without any separate flag.  A CTA can
+// so a reader can tell a fresh value from a stale one without a separate flag.  A CTA can
 // not run two rounds ahead of a reader, because the round after next needs the reader's
-// own contribution.  Totals are summed in the same order by every CTA (lane-strided, then a
-// fixed tree read from lane 0), so all CTAs hold identical results.
-__device__ bool grid_allreduce2(const DevLayout &d, unsigned long long seq, double a, double b,
-                                double &A, double &B, long long timeout_ns) {
+// own contribution.  The totals are exact fixed-point sums rounded once, so every CTA
+// holds the same bits.
+__device__ bool grid_allreduce2(const DevLayout &d, unsigned long long seq, double a, double b, double &A,
+                                double &B, long long timeout_ns) {
     const int lane = threadIdx.x & 31;
-    const long long deadline = now_ns() + timeout_ns;
     const unsigned long long phase = ((seq >> 1) & 1ull) ^ 1ull;
     unsigned long long *buf = d.slots + (seq & 1ull) * 2ull * static_cast<unsigned long long>(d.S);
     if (lane == 0) {
-        st_relaxed_u64(buf + 2 * blockIdx.x, enc(a, phase));
-        st_relaxed_u64(buf + 2 * blockIdx.x + 1, enc(b, phase));
+        const unsigned long long ea = (static_cast<unsigned long long>(__double_as_longlong(a)) &
+                                       0x7fffffffffffffffull) | (phase << 63);
+        const unsigned long long eb = (static_cast<unsigned long long>(__double_as_longlong(b)) &
+                                       0x7fffffffffffffffull) | (phase << 63);
+        st_relaxed_v2(buf + 2 * blockIdx.x, ea, eb);
     }
-    double sa, sb;
+    const long long deadline = now_ns() + timeout_ns;
+    Fx sa = fx_zero(), sb = fx_zero();
+    bool bad = false;
     for (int it = 0;; ++it) {
         bool ready = true;
-        sa = 0.0;
-        sb = 0.0;
-        for (int s = lane; s < d.S; s += 32) {
-            unsigned long long va = ld_relaxed_u64(buf + 2 * s);
-            unsigned long long vb = ld_relaxed_u64(buf + 2 * s + 1);
-            ready &= ((va >> 63) == phase) && ((vb >> 63) == phase);
-            sa += dec(va);
-            sb += dec(vb);
+        unsigned long long va[5], vb[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int s = lane + 32 * q;
+            va[q] = vb[q] = 0ull;
+            if (s < d.S) ld_relaxed_v2(buf + 2 * s, va[q], vb[q]);
         }
-        if (__all_sync(kFull, ready)) break;
+        for (int s = lane + 160; s < d.S; s += 32) {   // more than 160 shards
+            unsigned long long x, y;
+            ld_relaxed_v2(buf + 2 * s, x, y);
+            ready &= ((x >> 63) == phase) && ((y >> 63) == phase);
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            if (lane + 32 * q < d.S) ready &= ((va[q] >> 63) == phase) && ((vb[q] >> 63) == phase);
+        if (__all_sync(kFull, ready)) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (lane + 32 * q < d.S) {
+                    sa = fx_add(sa, fx_from_double(__longlong_as_double(static_cast<long long>(va[q] & 0x7fffffffffffffffull)), bad));
+                    sb = fx_add(sb, fx_from_double(__longlong_as_double(static_cast<long long>(vb[q] & 0x7fffffffffffffffull)), bad));
+                }
+            }
+            for (int s = lane + 160; s < d.S; s += 32) {
+                unsigned long long x, y;
+                ld_relaxed_v2(buf + 2 * s, x, y);
+                sa = fx_add(sa, fx_from_double(__longlong_as_double(static_cast<long long>(x & 0x7fffffffffffffffull)), bad));
+                sb = fx_add(sb, fx_from_double(__longlong_as_double(static_cast<long long>(y & 0x7fffffffffffffffull)), bad));
+            }
+            break;
+        }
         int give_up = 0;
         if (lane == 0 && (it & 15) == 15)
             give_up = (ld_relaxed_i32(d.abort_flag) != 0) || (now_ns() > deadline);
@@ -108,38 +334,71 @@ __device__ bool grid_allreduce2(const DevLayout &d, unsigned long long seq, doub
             return false;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sa += __shfl_down_sync(kFull, sa, o);
-        sb += __shfl_down_sync(kFull, sb, o);
-    }
-    A = __shfl_sync(kFull, sa, 0);
-    B = __shfl_sync(kFull, sb, 0);
+    sa = fx_warp_sum(sa);
+    sb = fx_warp_sum(sb);
+    const bool any_bad = __any_sync(kFull, bad);
+    double ta = fx_to_double(sa), tb = fx_to_double(sb);
+    if (any_bad) ta = tb = __longlong_as_double(0x7ff8000000000000ll);
+    A = __shfl_sync(kFull, ta, 0);
+    B = __shfl_sync(kFull, tb, 0);
     return true;
 }
 
-// Warp sum with a fixed association; the result is read from lane 0.
-__device__ __forceinline__ double warp_sum_lane0(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return v;
+// Block reduction of two per-thread partials (exact), then the grid all-reduce by warp 0.
+// On return (all threads) sh.G, sh.H hold the grid totals; returns false on abort.
+__device__ bool block_grid_reduce(const DevLayout &d, unsigned long long seq, long long timeout_ns,
+                                  SharedState &sh, double a, double b, bool bad) {
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    Fx fa = fx_from_double(a, bad), fb = fx_from_double(b, bad);
+    fa = fx_warp_sum(fa);
+    fb = fx_warp_sum(fb);
+    const int wbad = __any_sync(kFull, bad);
+    if (lane == 0) {
+        sh.wa[warp] = fa;
+        sh.wb[warp] = fb;
+        sh.wbad[warp] = wbad;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        Fx ta = lane < nwarps ? sh.wa[lane] : fx_zero();
+        Fx tb = lane < nwarps ? sh.wb[lane] : fx_zero();
+        const bool cb = __any_sync(kFull, lane < nwarps ? sh.wbad[lane] != 0 : false);
+        ta = fx_warp_sum(ta);
+        tb = fx_warp_sum(tb);
+        double ca = fx_to_double(ta), cbv = fx_to_double(tb);
+        if (cb) ca = cbv = __longlong_as_double(0x7ff8000000000000ll);
+        ca = __shfl_sync(kFull, ca, 0);
+        cbv = __shfl_sync(kFull, cbv, 0);
+        double At = 0.0, Bt = 0.0;
+        const bool ok = grid_allreduce2(d, seq, ca, cbv, At, Bt, timeout_ns);
+        if (lane == 0) {
+            sh.ok = ok;
+            sh.G = At;
+            sh.H = Bt;
+        }
+    }
+    __syncthreads();
+    return sh.ok != 0;
 }
 
-// Coordinate step: Newton step of Eq. 4 under the prior of Eq. 3, then the Genkin trust
-// region.  q = -h >= 0.  Laplace: soft threshold at 0, and a step that would change the
-// sign of a nonzero b stops at 0.  q = 0 with no finite minimiser takes the trust bound
-// and raises warning bit 0.
-__device__ double newton_step(double g, double h, double b, int prior, double var, double lambda,
-                              double &trust, int &warn) {
-    const double q = -h;
+// ------------------------------------------------------------------ the coordinate step
+
+// Newton step of Eq. 4 under the prior of Eq. 3, clamped to the Genkin trust region (one
+// lane).  q = -h >= 0.  Laplace: soft threshold at 0, and a step that would change the sign
+// of a nonzero b stops at 0.  q = 0 with no finite minimiser takes the trust bound and
+// raises warning bit 0.  The trust radius itself is updated by the caller.
+__device__ double newton_step(double g, double q, double b, const FitParams &p, double trust, int &warn) {
     double dv;
-    if (prior == 1) {
-        dv = (g - b / var) / (q + 1.0 / var);
-    } else if (prior == 2) {
+    if (p.prior == 1) {
+        dv = fma(-b, p.inv_var, g) / (q + p.inv_var);
+    } else if (p.prior == 2) {
+        const double lambda = p.lambda;
         if (q > 0.0) {
             if (b == 0.0) {
-                const double up = (g - lambda) / q, dn = (g + lambda) / q;
-                dv = up > 0.0 ? up : (dn < 0.0 ? dn : 0.0);
+                const double gu = g - lambda, gd = g + lambda;
+                dv = gu > 0.0 ? gu / q : (gd < 0.0 ? gd / q : 0.0);
             } else {
                 const double s = b > 0.0 ? 1.0 : -1.0;
                 dv = (g - lambda * s) / q;
@@ -151,7 +410,7 @@ __device__ double newton_step(double g, double h, double b, int prior, double va
             if (fabs(g) <= lambda) {
                 dv = 0.0;
             } else {
-                dv = (g > 0.0 ? 1.0 : -1.0) * trust;
+                dv = g > 0.0 ? trust : -trust;
                 warn |= 1;
             }
         } else {
@@ -160,7 +419,7 @@ __device__ double newton_step(double g, double h, double b, int prior, double va
                 dv = -b;
             } else {
                 const double dd = g - lambda * s;
-                dv = (dd > 0.0 ? 1.0 : (dd < 0.0 ? -1.0 : 0.0)) * trust;
+                dv = dd > 0.0 ? trust : (dd < 0.0 ? -trust : 0.0);
                 const double nb = b + dv;
                 const double ns = nb > 0.0 ? 1.0 : (nb < 0.0 ? -1.0 : 0.0);
                 if (ns != s) dv = -b;
@@ -171,348 +430,446 @@ __device__ double newton_step(double g, double h, double b, int prior, double va
         if (q > 0.0) {
             dv = g / q;
         } else if (g != 0.0) {
-            dv = (g > 0.0 ? 1.0 : -1.0) * trust;
+            dv = g > 0.0 ? trust : -trust;
             warn |= 1;
         } else {
             dv = 0.0;
         }
     }
-    const double db = fmin(fmax(dv, -trust), trust);
-    trust = fmax(2.0 * fabs(db), 0.5 * trust);
-    return db;
+    return fmin(fmax(dv, -trust), trust);
 }
 
-// What a lane keeps between phases A and C for its warp's first group of the slice.
-struct LaneCache {
-    int32_t row[kUnroll];
-    double e[kUnroll];
-    int32_t pid;
-    int32_t len;
-    double Dv;
-    double num;
-    int64_t tail_base;   // rows[] index of diagonal kUnroll of the group
-};
-
-// Phase A for one group of 32 segments.  Adds this lane's n_i W_i and n_i W_i (1 - W_i)
-// to G and H.  Keeps the lane's data in `lc` (first group of the warp) or in `stash`.
-__device__ __forceinline__ void group_phase_a(const DevLayout &d, int64_t si, int64_t seg_end,
-                                              int64_t base, double &G, double &H, LaneCache *lc,
-                                              double *stash_slot) {
-    const int lane = threadIdx.x & 31;
-    const bool valid = si < seg_end;
-    const int2 sg = valid ? d.segs[si] : make_int2(0, 0);
-    const double Dv = valid ? d.D[sg.x] : 1.0;
-    const int nv = valid ? d.nev[sg.x] : 0;
-    const int maxlen = __shfl_sync(kFull, sg.y, 0);  // segments are sorted longest first
-    double num = 0.0;
-    int64_t b = base;
-    int32_t rr[kUnroll];
-    double ee[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-        const bool act = sg.y > u;
-        const unsigned m = __ballot_sync(kFull, act);
-        rr[u] = act ? d.rows[b + lane] : -1;
-        b += __popc(m);
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) ee[u] = rr[u] >= 0 ? d.E[rr[u]] : 0.0;
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) num += ee[u];
-    const int64_t tail_base = b;
-    for (int t = kUnroll; t < maxlen; t += kUnroll) {
-        int32_t r2[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const bool act = sg.y > t + u;
-            const unsigned m = __ballot_sync(kFull, act);
-            r2[u] = act ? d.rows[b + lane] : -1;
-            b += __popc(m);
-        }
-        double e2[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) e2[u] = r2[u] >= 0 ? d.E[r2[u]] : 0.0;
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) num += e2[u];
-    }
-    // W_i is a share of D_i; rounding in the incremental D can push it an ulp past 1.
-    double w = valid ? num / Dv : 0.0;
-    w = fmin(fmax(w, 0.0), 1.0);
-    const double nw = static_cast<double>(nv) * w;
-    G += nw;
-    H += nw * (1.0 - w);
-    if (lc) {
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            lc->row[u] = rr[u];
-            lc->e[u] = ee[u];
-        }
-        lc->pid = valid ? sg.x : -1;
-        lc->len = sg.y;
-        lc->Dv = Dv;
-        lc->num = num;
-        lc->tail_base = tail_base;
-    } else if (valid) {
-        stash_slot[0] = num;
-        stash_slot[1] = Dv;
-    }
+// W_i from one segment, with the partials of Eqs. 7 and 9.  W_i is a share of D_i; rounding
+// in the incremental D can push it an ulp past 1, so it is clamped (by its bit pattern).
+__device__ __forceinline__ void segment_terms(double num, double Dv, int nv, double &gl, double &hl, bool &bad) {
+    const unsigned long long bd = static_cast<unsigned long long>(__double_as_longlong(Dv));
+    const unsigned long long bn = static_cast<unsigned long long>(__double_as_longlong(num));
+    if (bd == 0ull || bd >= 0x7ff0000000000000ull || bn >= 0x7ff0000000000000ull) bad = true;
+    double w = num / Dv;
+    if (static_cast<unsigned long long>(__double_as_longlong(w)) > 0x3ff0000000000000ull) w = 1.0;
+    gl = static_cast<double>(nv) * w;
+    hl = gl * (1.0 - w);
 }
 
-// Phase C for the tail diagonals (t >= from) of a group: E_k <- E_k * r.
-__device__ __forceinline__ void group_tail_update(const DevLayout &d, int len, int maxlen, int from,
-                                                  int64_t b, double r) {
-    const int lane = threadIdx.x & 31;
-    for (int t = from; t < maxlen; ++t) {
-        const bool act = len > t;
-        const unsigned m = __ballot_sync(kFull, act);
-        if (act) {
-            const int32_t k = d.rows[b + lane];
-            d.E[k] *= r;
-        }
-        b += __popc(m);
-    }
-}
+// ------------------------------------------------------------------ column phases
 
-struct SharedState {
-    double wa[kMaxWarps];
-    double wb[kMaxWarps];
-    double db;
-    double G, H;
-    int ok;
-};
-
-// Phase A + all-reduce for column j on this CTA's slice.  Returns false on abort.
-// On return (all threads) sh.G, sh.H hold the grid totals.
-__device__ bool column_reduce(const DevLayout &d, int j, unsigned long long seq, long long timeout_ns,
-                              SharedState &sh, LaneCache &lc, bool &have_lc) {
-    const int s = blockIdx.x;
+// Phase A over a staged slice (everything static already in shared memory).
+__device__ void phase_a_staged(const DevLayout &d, const ColDesc &cd, const StageBuf &sb, SmemLayout &sm,
+                               double &G, double &H, bool &bad) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const int64_t so = static_cast<int64_t>(s) * (d.J + 1) + j;
-    const int64_t seg0 = d.slice_seg[so], seg1 = d.slice_seg[so + 1];
-    const int64_t grp0 = d.slice_grp[so];
-    const int ngrp = static_cast<int>((seg1 - seg0 + 31) >> 5);
-    double G = 0.0, H = 0.0;
-    have_lc = false;
-    double *stash = d.stash + 2 * static_cast<int64_t>(s) * d.stash_stride;
-    for (int g = warp; g < ngrp; g += nwarps) {
-        const int64_t si = seg0 + 32 * static_cast<int64_t>(g) + lane;
-        const int64_t base = d.grp_base[grp0 + g];
-        if (g == warp) {
-            group_phase_a(d, si, seg1, base, G, H, &lc, nullptr);
-            have_lc = true;
+    const int2 *sseg = sb.segs + cd.seg_off;
+    const int32_t *srow = sb.rows + cd.row_off;
+    const long long *sgrp = sb.grp + cd.grp_off;
+    bool first = true;
+    for (int g = warp; g < cd.ngrp; g += nwarps) {
+        const int si = 32 * g + lane;
+        const bool valid = si < cd.nseg;
+        const int2 sg = valid ? sseg[si] : make_int2(0, 0);
+        const double Dv = valid ? d.D[sg.x] : 1.0;
+        const int nv = valid ? d.nev[sg.x] : 0;
+        int base = static_cast<int>(sgrp[g] - cd.row0);
+        const int maxlen = __shfl_sync(kFull, sg.y, 0);  // segments are sorted longest first
+        double num = 0.0;
+        for (int t0 = 0; t0 < maxlen; t0 += kBatch) {
+            int pos[kBatch];
+            int32_t k[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const bool act = sg.y > t0 + u;
+                const unsigned m = __ballot_sync(kFull, act);
+                pos[u] = act ? base + lane : -1;
+                k[u] = act ? srow[base + lane] : -1;
+                base += __popc(m);
+            }
+            double e[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? d.E[k[u]] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                if (t0 + u < maxlen) {       // warp-uniform: skip the FP64 add on empty diagonals
+                    if (k[u] >= 0) {
+                        num += e[u];
+                        sm.est[pos[u]] = e[u];
+                    }
+                }
+            }
+        }
+        double gl = 0.0, hl = 0.0;
+        if (valid) {
+            segment_terms(num, Dv, nv, gl, hl, bad);
+            sm.seg_stash[si] = make_double2(num, Dv);
+        }
+        if (first) {
+            G = gl;
+            H = hl;
+            first = false;
         } else {
-            group_phase_a(d, si, seg1, base, G, H, nullptr, stash + 2 * (si - seg0));
+            G += gl;
+            H += hl;
         }
     }
-    G = warp_sum_lane0(G);
-    H = warp_sum_lane0(H);
-    if (lane == 0) {
-        sh.wa[warp] = G;
-        sh.wb[warp] = H;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        double a = lane < nwarps ? sh.wa[lane] : 0.0;
-        double b = lane < nwarps ? sh.wb[lane] : 0.0;
-        a = __shfl_sync(kFull, warp_sum_lane0(a), 0);
-        b = __shfl_sync(kFull, warp_sum_lane0(b), 0);
-        double At, Bt;
-        const bool ok = grid_allreduce2(d, seq, a, b, At, Bt, timeout_ns);
-        if (lane == 0) {
-            sh.ok = ok;
-            sh.G = At;
-            sh.H = Bt;
-        }
-    }
-    __syncthreads();
-    return sh.ok != 0;
 }
 
-// Phase C for column j with ratio r = e^{db} and em1 = e^{db} - 1.
-__device__ void column_update(const DevLayout &d, int j, double r, double em1, const LaneCache &lc,
-                              bool have_lc) {
-    const int s = blockIdx.x;
+// Phase A over a slice read straight from global memory (slices too big to stage).
+__device__ void phase_a_global(const DevLayout &d, int s, int j, double &G, double &H, bool &bad) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const int64_t so = static_cast<int64_t>(s) * (d.J + 1) + j;
-    const int64_t seg0 = d.slice_seg[so], seg1 = d.slice_seg[so + 1];
-    const int64_t grp0 = d.slice_grp[so];
-    const int ngrp = static_cast<int>((seg1 - seg0 + 31) >> 5);
-    const double *stash = d.stash + 2 * static_cast<int64_t>(s) * d.stash_stride;
-    if (have_lc) {
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            if (lc.row[u] >= 0) d.E[lc.row[u]] = lc.e[u] * r;
-        if (lc.pid >= 0) d.D[lc.pid] = lc.Dv + em1 * lc.num;
-        const int maxlen = __shfl_sync(kFull, lc.len, 0);
-        if (maxlen > kUnroll) group_tail_update(d, lc.len, maxlen, kUnroll, lc.tail_base, r);
-    }
-    for (int g = warp + nwarps; g < ngrp; g += nwarps) {
-        const int64_t si = seg0 + 32 * static_cast<int64_t>(g) + lane;
+    const long long so = static_cast<long long>(s) * (d.J + 1) + j;
+    const long long seg0 = d.slice_seg[so], seg1 = d.slice_seg[so + 1];
+    const long long grp0 = d.slice_grp[so];
+    const int ngrp = static_cast<int>(d.slice_grp[so + 1] - grp0);
+    double *stash = d.stash + 2 * static_cast<long long>(s) * d.stash_stride;
+    bool first = true;
+    for (int g = warp; g < ngrp; g += nwarps) {
+        const long long si = seg0 + 32 * static_cast<long long>(g) + lane;
         const bool valid = si < seg1;
         const int2 sg = valid ? d.segs[si] : make_int2(0, 0);
+        const double Dv = valid ? d.D[sg.x] : 1.0;
+        const int nv = valid ? d.nev[sg.x] : 0;
+        long long base = d.grp_base[grp0 + g];
         const int maxlen = __shfl_sync(kFull, sg.y, 0);
-        group_tail_update(d, sg.y, maxlen, 0, d.grp_base[grp0 + g], r);
+        double num = 0.0;
+        for (int t0 = 0; t0 < maxlen; t0 += kBatch) {
+            int32_t k[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const bool act = sg.y > t0 + u;
+                const unsigned m = __ballot_sync(kFull, act);
+                k[u] = act ? d.rows[base + lane] : -1;
+                base += __popc(m);
+            }
+            double e[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? d.E[k[u]] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (t0 + u < maxlen && k[u] >= 0) num += e[u];
+        }
+        double gl = 0.0, hl = 0.0;
         if (valid) {
-            const double num = stash[2 * (si - seg0)];
-            const double Dv = stash[2 * (si - seg0) + 1];
-            d.D[sg.x] = Dv + em1 * num;
+            segment_terms(num, Dv, nv, gl, hl, bad);
+            stash[2 * (si - seg0)] = num;
+            stash[2 * (si - seg0) + 1] = Dv;
+        }
+        if (first) {
+            G = gl;
+            H = hl;
+            first = false;
+        } else {
+            G += gl;
+            H += hl;
         }
     }
 }
 
-// Recompute D_i = sum_{k in i} E_k on this CTA's subjects and return (in sh.G, sh.H after
-// the all-reduce) the totals of the positive and negative parts of sum_i n_i log D_i.
+// Phase C over a staged slice: stores only.
+__device__ void phase_c_staged(const DevLayout &d, const ColDesc &cd, const StageBuf &sb, const SmemLayout &sm,
+                               double r, double em1) {
+    const int2 *sseg = sb.segs + cd.seg_off;
+    const int32_t *srow = sb.rows + cd.row_off;
+    for (int p = threadIdx.x; p < cd.nnz; p += blockDim.x) d.E[srow[p]] = sm.est[p] * r;
+    for (int si = threadIdx.x; si < cd.nseg; si += blockDim.x) {
+        const double2 st = sm.seg_stash[si];
+        d.D[sseg[si].x] = fma(em1, st.x, st.y);
+    }
+}
+
+// Phase C over a global slice.
+__device__ void phase_c_global(const DevLayout &d, int s, int j, double r, double em1) {
+    const long long so = static_cast<long long>(s) * (d.J + 1) + j;
+    const long long row0 = d.slice_row[so], row1 = d.slice_row[so + 1];
+    const long long seg0 = d.slice_seg[so], seg1 = d.slice_seg[so + 1];
+    const double *stash = d.stash + 2 * static_cast<long long>(s) * d.stash_stride;
+    const long long T = blockDim.x;
+    long long p = row0 + threadIdx.x;
+    for (; p + 3 * T < row1; p += 4 * T) {
+        int32_t k[4];
+        double e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k[u] = d.rows[p + u * T];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = d.E[k[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d.E[k[u]] = e[u] * r;
+    }
+    for (; p < row1; p += T) {
+        const int32_t k = d.rows[p];
+        d.E[k] *= r;
+    }
+    for (long long si = seg0 + threadIdx.x; si < seg1; si += T) {
+        const double num = stash[2 * (si - seg0)], Dv = stash[2 * (si - seg0) + 1];
+        d.D[d.segs[si].x] = fma(em1, num, Dv);
+    }
+}
+
+// ------------------------------------------------------------------ staging
+
+struct SliceBounds {
+    long long seg0, seg1, row0, row1, grp0, grp1;
+};
+
+__device__ __forceinline__ SliceBounds load_bounds(const DevLayout &d, int s, int j) {
+    const long long so = static_cast<long long>(s) * (d.J + 1) + j;
+    SliceBounds b;
+    b.seg0 = d.slice_seg[so];
+    b.seg1 = d.slice_seg[so + 1];
+    b.row0 = d.slice_row[so];
+    b.row1 = d.slice_row[so + 1];
+    b.grp0 = d.slice_grp[so];
+    b.grp1 = d.slice_grp[so + 1];
+    return b;
+}
+
+// Thread 0: describe slice `b` in desc[buf] and, if it fits, start its bulk copies.
+// Returns whether an mbarrier arrival (with its copies) was issued.
+__device__ bool issue_stage(const DevLayout &d, const SliceBounds &b, SmemLayout &sm, SharedState &sh, int buf) {
+    ColDesc &cd = sh.desc[buf];
+    cd.seg0 = b.seg0;
+    cd.row0 = b.row0;
+    cd.grp0 = b.grp0;
+    cd.nseg = static_cast<int>(b.seg1 - b.seg0);
+    cd.nnz = static_cast<int>(b.row1 - b.row0);
+    cd.ngrp = static_cast<int>(b.grp1 - b.grp0);
+    cd.staged = (cd.nseg <= kSegCap && cd.nnz <= kRowCap) ? 1 : 0;
+    cd.seg_off = cd.row_off = cd.grp_off = 0;
+    if (!cd.staged) return false;
+    StageBuf &st = sm.stage[buf];
+    uint32_t total = 0;
+    const char *gs = nullptr, *gr = nullptr, *gg = nullptr;
+    uint32_t ns = 0, nr = 0, ng = 0;
+    if (cd.nseg > 0) {
+        const long long a0 = (8 * b.seg0) & ~15ll, a1 = (8 * b.seg1 + 15) & ~15ll;
+        gs = reinterpret_cast<const char *>(d.segs) + a0;
+        ns = static_cast<uint32_t>(a1 - a0);
+        cd.seg_off = static_cast<int>((8 * b.seg0 - a0) / 8);
+        const long long r0 = (4 * b.row0) & ~15ll, r1 = (4 * b.row1 + 15) & ~15ll;
+        gr = reinterpret_cast<const char *>(d.rows) + r0;
+        nr = static_cast<uint32_t>(r1 - r0);
+        cd.row_off = static_cast<int>((4 * b.row0 - r0) / 4);
+        const long long g0 = (8 * b.grp0) & ~15ll, g1 = (8 * b.grp1 + 15) & ~15ll;
+        gg = reinterpret_cast<const char *>(d.grp_base) + g0;
+        ng = static_cast<uint32_t>(g1 - g0);
+        cd.grp_off = static_cast<int>((8 * b.grp0 - g0) / 8);
+        total = ns + nr + ng;
+    }
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&sh.bar[buf], total);
+    if (ns) bulk_g2s(st.segs, gs, ns, &sh.bar[buf]);
+    if (nr) bulk_g2s(st.rows, gr, nr, &sh.bar[buf]);
+    if (ng) bulk_g2s(st.grp, gg, ng, &sh.bar[buf]);
+    return true;
+}
+
+// ------------------------------------------------------------------ end of cycle
+
+// Recompute D_i = sum_{k in i} E_k on this CTA's subjects and all-reduce the positive and
+// negative parts of sum_i n_i log D_i (into sh.G, sh.H).
 __device__ bool refresh_and_reduce(const DevLayout &d, unsigned long long seq, long long timeout_ns,
-                                   SharedState &sh, bool refresh) {
+                                   SharedState &sh) {
     const int s = blockIdx.x;
-    const int warp = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    const int64_t p0 = d.shard_pat[s], p1 = d.shard_pat[s + 1];
+    const long long p0 = d.shard_pat[s], p1 = d.shard_pat[s + 1];
     double pos = 0.0, neg = 0.0;
-    for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
-        double Di;
-        if (refresh) {
-            Di = 0.0;
-#pragma unroll 4
-            for (int64_t k = d.pat_ptr[i]; k < d.pat_ptr[i + 1]; ++k) Di += d.E[k];
-            d.D[i] = Di;
-        } else {
-            Di = d.D[i];
+    bool bad = false;
+    for (long long i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+        double Di = 0.0;
+        const long long k0 = d.pat_ptr[i], k1 = d.pat_ptr[i + 1];
+        long long k = k0;
+        for (; k + 3 < k1; k += 4) {
+            const double e0 = d.E[k], e1 = d.E[k + 1], e2 = d.E[k + 2], e3 = d.E[k + 3];
+            Di += e0;
+            Di += e1;
+            Di += e2;
+            Di += e3;
         }
+        for (; k < k1; ++k) Di += d.E[k];
+        d.D[i] = Di;
         const double t = static_cast<double>(d.nev[i]) * log(Di);
-        if (t >= 0.0) pos += t; else neg -= t;  // a NaN lands in neg and stays visible
+        if (t >= 0.0) pos += t;
+        else if (t < 0.0) neg -= t;
+        else bad = true;  // NaN
     }
-    pos = warp_sum_lane0(pos);
-    neg = warp_sum_lane0(neg);
-    if (lane == 0) {
-        sh.wa[warp] = pos;
-        sh.wb[warp] = neg;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        double a = lane < nwarps ? sh.wa[lane] : 0.0;
-        double b = lane < nwarps ? sh.wb[lane] : 0.0;
-        a = __shfl_sync(kFull, warp_sum_lane0(a), 0);
-        b = __shfl_sync(kFull, warp_sum_lane0(b), 0);
-        double At, Bt;
-        const bool ok = grid_allreduce2(d, seq, a, b, At, Bt, timeout_ns);
-        if (lane == 0) {
-            sh.ok = ok;
-            sh.G = At;
-            sh.H = Bt;
-        }
-    }
-    __syncthreads();
-    return sh.ok != 0;
+    return block_grid_reduce(d, seq, timeout_ns, sh, pos, neg, bad);
 }
 
 // sum_j b_j Y'X_j (= Y'Xb) and the prior term, from this CTA's private beta, in j order.
 __device__ void beta_terms(const DevLayout &d, const FitParams &p, double &lin, double &logprior) {
-    const double *beta = d.beta_priv + static_cast<int64_t>(blockIdx.x) * d.J;
+    const double *beta = d.beta_priv + static_cast<long long>(blockIdx.x) * d.J;
     double l = 0.0, sq = 0.0, ab = 0.0;
     for (int j = 0; j < d.J; ++j) {
         const double b = beta[j];
-        l += b * d.ytx[j];
-        sq += b * b;
+        l = fma(b, d.ytx[j], l);
+        sq = fma(b, b, sq);
         ab += fabs(b);
     }
     lin = l;
-    logprior = p.prior == 1 ? -sq / (2.0 * p.variance) : (p.prior == 2 ? -p.lambda * ab : 0.0);
+    logprior = p.prior == 1 ? -0.5 * sq * p.inv_var : (p.prior == 2 ? -p.lambda * ab : 0.0);
 }
 
+// Thread 0: wait (bounded) for any bulk copy still in flight into this CTA's shared memory.
+__device__ void drain_stages(SharedState &sh, unsigned pending, unsigned phase_bits, long long timeout_ns) {
+    if (threadIdx.x != 0) return;
+    for (int b = 0; b < 2; ++b)
+        if ((pending >> b) & 1u) (void)mbar_wait(&sh.bar[b], (phase_bits >> b) & 1u, timeout_ns);
+}
+
+// ------------------------------------------------------------------ kernels
+
 __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, FitOut *out, double *hist) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemLayout &sm = *reinterpret_cast<SmemLayout *>(smem_raw);
     __shared__ SharedState sh;
-    __shared__ int sh_stop;
     const int s = blockIdx.x;
     const bool leader = (s == 0) && (threadIdx.x == 0);
     const long long timeout = p.timeout_ns;
     unsigned long long seq = p.seq0;
-    double *beta = d.beta_priv + static_cast<int64_t>(s) * d.J;
-    double *trust = d.trust_priv + static_cast<int64_t>(s) * d.J;
+    double *beta = d.beta_priv + static_cast<long long>(s) * d.J;
+    double *trust = d.trust_priv + static_cast<long long>(s) * d.J;
+    const int J = d.J;
+
+    // staging state: pending and nb live in thread 0; phase_bits is tracked by every thread
+    unsigned pending = 0u;      // buffers with an arrival issued and not yet waited for
+    unsigned phase_bits = 0u;   // expected parity per buffer
+    SliceBounds nb{};           // bounds of the column after the staged one
+    int status = kStNotConverged, warn = 0, cycles = 0;
+    long long nonzero = 0;
+    double P_prev = 0.0, P = 0.0, conv = 0.0, loglik = 0.0;
+    long long col = 0;          // columns processed: stage buffer = col & 1
+
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.bar[0], 1);
+        mbar_init(&sh.bar[1], 1);
+        mbar_init_fence();
+        sh.desc[0].staged = 0;
+        sh.desc[1].staged = 0;
+        if (J > 0 && p.max_cycles > 0) {
+            const SliceBounds b0 = load_bounds(d, s, 0);
+            if (issue_stage(d, b0, sm, sh, 0)) pending |= 1u;
+            nb = load_bounds(d, s, J > 1 ? 1 : 0);
+        }
+    }
+    __syncthreads();
 
     // P at the start point.
-    if (!refresh_and_reduce(d, seq++, timeout, sh, true)) goto aborted;
+    if (!refresh_and_reduce(d, seq++, timeout, sh)) goto aborted;
     {
         double lin = 0.0, lp = 0.0;
         if (threadIdx.x == 0) beta_terms(d, p, lin, lp);
-        double P_prev = lin - (sh.G - sh.H) + lp;
+        loglik = lin - (sh.G - sh.H);
+        P_prev = loglik + lp;
+        P = P_prev;
         if (leader && p.record_history) hist[0] = P_prev;
-        int status = kStNotConverged, warn = 0, cycles = 0;
-        long long nonzero = 0;
-        double conv = 0.0, P = P_prev, loglik = lin - (sh.G - sh.H);
-        if (!(P_prev == P_prev) || isinf(P_prev)) status = kStNumeric;
-        for (int c = 1; c <= p.max_cycles && status == kStNotConverged; ++c) {
-            double lin_c = 0.0, sq_c = 0.0, ab_c = 0.0;
-            for (int j = 0; j < d.J; ++j) {
-                LaneCache lc;
-                bool have_lc;
-                if (!column_reduce(d, j, seq++, timeout, sh, lc, have_lc)) goto aborted;
-                if (threadIdx.x == 0) {
-                    const double g = d.ytx[j] - sh.G;
-                    const double h = -sh.H;
-                    const double bj = beta[j];
-                    double tr = trust[j];
-                    double db = newton_step(g, h, bj, p.prior, p.variance, p.lambda, tr, warn);
-                    if (!(db == db) || isinf(db)) {
-                        db = 0.0;
-                        status = kStNumeric;
-                    }
-                    const double nb = bj + db;
-                    beta[j] = nb;
-                    trust[j] = tr;
-                    lin_c += nb * d.ytx[j];
-                    sq_c += nb * nb;
-                    ab_c += fabs(nb);
-                    if (db != 0.0) ++nonzero;
-                    sh.db = db;
-                }
-                __syncthreads();
-                const double db = sh.db;
-                if (db != 0.0) column_update(d, j, exp(db), expm1(db), lc, have_lc);
-                __syncthreads();
-            }
-            if (!refresh_and_reduce(d, seq++, timeout, sh, true)) goto aborted;
+        if (threadIdx.x == 0) sh.stop = (!(P_prev == P_prev) || isinf(P_prev)) ? kStNumeric : kStNotConverged;
+        __syncthreads();
+        status = sh.stop;
+    }
+    for (int c = 1; c <= p.max_cycles && status == kStNotConverged; ++c) {
+        double lin_c = 0.0, sq_c = 0.0, ab_c = 0.0;
+        for (int j = 0; j < J; ++j, ++col) {
+            const int buf = static_cast<int>(col & 1);
+            // thread 0: stage the next column into the other buffer; prefetch this column's scalars
+            double bj = 0.0, tj = 0.0, yj = 0.0;
             if (threadIdx.x == 0) {
-                const double lp = p.prior == 1 ? -sq_c / (2.0 * p.variance)
-                                               : (p.prior == 2 ? -p.lambda * ab_c : 0.0);
-                loglik = lin_c - (sh.G - sh.H);
-                P = loglik + lp;
-                if (leader && p.record_history) hist[c] = P;
-                conv = fabs(P - P_prev);
-                if (p.tol_mode == 1) conv /= fmax(1.0, fabs(P));
-                cycles = c;
-                if (!(P == P) || isinf(P)) status = kStNumeric;
-                else if (status == kStNotConverged && p.tol >= 0.0 && conv < p.tol) status = kStOk;
-                P_prev = P;
-                sh_stop = status;
+                if (issue_stage(d, nb, sm, sh, buf ^ 1)) pending |= 1u << (buf ^ 1);
+                const int jn = j + 1 < J ? j + 1 : 0;
+                const int jnn = jn + 1 < J ? jn + 1 : 0;
+                nb = load_bounds(d, s, jnn);
+                bj = beta[j];
+                tj = trust[j];
+                yj = d.ytx[j];
+            }
+            // desc[buf] was written a column ago and is stable; wait for its copies
+            const ColDesc cd = sh.desc[buf];
+            bool staged_ok = true;
+            if (cd.staged) {
+                staged_ok = mbar_wait(&sh.bar[buf], (phase_bits >> buf) & 1u, timeout);
+                phase_bits ^= 1u << buf;
+                if (threadIdx.x == 0) pending &= ~(1u << buf);
+            }
+            // one barrier: desc[buf ^ 1] published, and a CTA-wide verdict on the copies
+            staged_ok = __syncthreads_and(staged_ok) != 0;
+            double G = 0.0, H = 0.0;
+            bool bad = false;
+            if (cd.staged) {
+                if (staged_ok) {
+                    phase_a_staged(d, cd, sm.stage[buf], sm, G, H, bad);
+                } else {                           // never read a stage that did not arrive
+                    bad = true;
+                    if (threadIdx.x == 0) atomicExch(d.abort_flag, 1);
+                }
+            } else {
+                phase_a_global(d, s, j, G, H, bad);
+            }
+            if (!block_grid_reduce(d, seq++, timeout, sh, G, H, bad)) goto aborted;
+            if (threadIdx.x == 0) {
+                const double g = yj - sh.G;
+                const double q = sh.H;
+                double db = newton_step(g, q, bj, p, tj, warn);
+                double em1 = 0.0;
+                if (!(db == db) || isinf(db) || !(g == g) || !(q == q)) {
+                    db = 0.0;
+                    status = kStNumeric;
+                } else if (db != 0.0) {
+                    em1 = expm1(db);
+                }
+                sh.db = db;
+                sh.em1 = em1;
+                sh.r = 1.0 + em1;
             }
             __syncthreads();
-            status = sh_stop;
+            const double db = sh.db;
+            if (db != 0.0) {
+                if (cd.staged) phase_c_staged(d, cd, sm.stage[buf], sm, sh.r, sh.em1);
+                else phase_c_global(d, s, j, sh.r, sh.em1);
+            }
+            if (threadIdx.x == 0) {
+                const double nbj = bj + db;
+                beta[j] = nbj;
+                trust[j] = fmax(2.0 * fabs(db), 0.5 * tj);
+                lin_c = fma(nbj, yj, lin_c);
+                sq_c = fma(nbj, nbj, sq_c);
+                ab_c += fabs(nbj);
+                if (db != 0.0) ++nonzero;
+            }
+            __syncthreads();   // E and D writes visible to the next column's reads
         }
-        if (leader) {
-            out->logpost = P;
-            out->loglik = loglik;
-            out->conv = conv;
-            out->cycles = cycles;
-            out->status = status;
-            out->nonzero_steps = nonzero;
-            out->warnings = warn;
-            out->seq_end = seq;
-            out->err_where = 0;
+        if (!refresh_and_reduce(d, seq++, timeout, sh)) goto aborted;
+        if (threadIdx.x == 0) {
+            const double lp = p.prior == 1 ? -0.5 * sq_c * p.inv_var : (p.prior == 2 ? -p.lambda * ab_c : 0.0);
+            loglik = lin_c - (sh.G - sh.H);
+            P = loglik + lp;
+            if (leader && p.record_history) hist[c] = P;
+            conv = fabs(P - P_prev);
+            if (p.tol_mode == 1) conv /= fmax(1.0, fabs(P));
+            cycles = c;
+            if (!(P == P) || isinf(P)) status = kStNumeric;
+            else if (status == kStNotConverged && p.tol >= 0.0 && conv < p.tol) status = kStOk;
+            P_prev = P;
+            sh.stop = status;
         }
-        return;
+        __syncthreads();
+        status = sh.stop;
     }
+    drain_stages(sh, pending, phase_bits, timeout);
+    if (leader) {
+        out->logpost = P;
+        out->loglik = loglik;
+        out->conv = conv;
+        out->cycles = cycles;
+        out->status = status;
+        out->nonzero_steps = nonzero;
+        out->warnings = warn;
+        out->seq_end = seq;
+        out->err_where = 0;
+    }
+    return;
 aborted:
-    if (threadIdx.x == 0) {
-        if (s == 0) {
-            out->status = kStTimeout;
-            out->err_where = 1;
-        }
+    drain_stages(sh, pending, phase_bits, timeout);
+    if (leader) {
+        out->status = kStTimeout;
+        out->err_where = 1;
     }
 }
 
@@ -520,11 +877,12 @@ __global__ void __launch_bounds__(512, 1) grad_hess_kernel(DevLayout d, int j, F
     __shared__ SharedState sh;
     const long long timeout = p.timeout_ns;
     unsigned long long seq = p.seq0;
-    if (!refresh_and_reduce(d, seq++, timeout, sh, true)) goto aborted;
+    if (!refresh_and_reduce(d, seq++, timeout, sh)) goto aborted;
     {
-        LaneCache lc;
-        bool have_lc;
-        if (!column_reduce(d, j, seq++, timeout, sh, lc, have_lc)) goto aborted;
+        double G = 0.0, H = 0.0;
+        bool bad = false;
+        phase_a_global(d, blockIdx.x, j, G, H, bad);
+        if (!block_grid_reduce(d, seq++, timeout, sh, G, H, bad)) goto aborted;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             out->g = d.ytx[j] - sh.G;
             out->h = -sh.H;
@@ -544,31 +902,39 @@ aborted:
 // private beta copies and trust radii (= 1) are (re)set.
 __global__ void __launch_bounds__(512, 1) init_state_kernel(DevLayout d, const double *beta0) {
     const int s = blockIdx.x;
-    const int64_t r0 = d.shard_row[s], r1 = d.shard_row[s + 1];
-    double *beta = d.beta_priv + static_cast<int64_t>(s) * d.J;
-    double *trust = d.trust_priv + static_cast<int64_t>(s) * d.J;
+    const long long r0 = d.shard_row[s], r1 = d.shard_row[s + 1];
+    double *beta = d.beta_priv + static_cast<long long>(s) * d.J;
+    double *trust = d.trust_priv + static_cast<long long>(s) * d.J;
     for (int j = threadIdx.x; j < d.J; j += blockDim.x) {
         beta[j] = beta0 ? beta0[j] : 0.0;
         trust[j] = 1.0;
     }
     if (!beta0) {
-        for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k];
+        for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k];
         return;
     }
-    for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = 0.0;
+    for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = 0.0;
     __syncthreads();
     for (int j = 0; j < d.J; ++j) {
         const double bj = beta0[j];
         if (bj == 0.0) continue;
-        const int64_t so = static_cast<int64_t>(s) * (d.J + 1) + j;
-        for (int64_t q = d.slice_row[so] + threadIdx.x; q < d.slice_row[so + 1]; q += blockDim.x)
+        const long long so = static_cast<long long>(s) * (d.J + 1) + j;
+        for (long long q = d.slice_row[so] + threadIdx.x; q < d.slice_row[so + 1]; q += blockDim.x)
             d.E[d.rows[q]] += bj;
         __syncthreads();
     }
-    for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k] * exp(d.E[k]);
+    for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k] * exp(d.E[k]);
+}
+
+int ensure_smem_attr() {
+    const cudaError_t e = cudaFuncSetAttribute(fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(sizeof(SmemLayout)));
+    return static_cast<int>(e);
 }
 
 }  // namespace
+
+size_t fit_kernel_smem_bytes() { return sizeof(SmemLayout); }
 
 int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, void *stream) {
     init_state_kernel<<<d.S, threads, 0, static_cast<cudaStream_t>(stream)>>>(d, beta0_dev);
@@ -577,23 +943,19 @@ int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, 
 
 int launch_fit(const DevLayout &d, const FitParams &p, FitOut *out_dev, double *hist_dev, int threads,
                void *stream) {
+    int e = ensure_smem_attr();
+    if (e) return e;
     DevLayout dd = d;
     FitParams pp = p;
     void *args[] = {&dd, &pp, &out_dev, &hist_dev};
     return static_cast<int>(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(fit_kernel), dim3(d.S),
-                                                         dim3(threads), args, 0,
+                                                         dim3(threads), args, sizeof(SmemLayout),
                                                          static_cast<cudaStream_t>(stream)));
 }
 
 int launch_grad_hess(const DevLayout &d, int32_t j, const FitParams &p, FitOut *out_dev, int threads,
                      void *stream) {
-    DevLayout dd = d;
-    FitParams pp = p;
-    int jj = j;
-    void *args[] = {&dd, &jj, &pp, &out_dev};
-    return static_cast<int>(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(grad_hess_kernel),
-                                                         dim3(d.S), dim3(threads), args, 0,
-                                                         static_cast<cudaStream_t>(stream)));
+    return launch_grad_hess_partial(d, j, p, out_dev, threads, d.S, stream);
 }
 
 int launch_grad_hess_partial(const DevLayout &d, int32_t j, const FitParams &p, FitOut *out_dev,
@@ -608,11 +970,13 @@ int launch_grad_hess_partial(const DevLayout &d, int32_t j, const FitParams &p, 
 }
 
 int fit_kernel_max_blocks_per_sm(int threads, int *blocks) {
+    int e = ensure_smem_attr();
+    if (e) return e;
     int a = 0, b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fit_kernel, threads, 0);
-    if (e != cudaSuccess) return static_cast<int>(e);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grad_hess_kernel, threads, 0);
-    if (e != cudaSuccess) return static_cast<int>(e);
+    cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fit_kernel, threads, sizeof(SmemLayout));
+    if (ce != cudaSuccess) return static_cast<int>(ce);
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grad_hess_kernel, threads, 0);
+    if (ce != cudaSuccess) return static_cast<int>(ce);
     *blocks = a < b ? a : b;
     return 0;
 }
