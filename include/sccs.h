@@ -202,6 +202,40 @@ int sccs_get_beta(const sccs_handle *h, double *beta_out);
  */
 int sccs_check_wait_timeout(sccs_handle *h, double timeout_ms);
 
+/*
+ * sccs_grad_hess_noalloc -- g_j and h_j of one column (the same quantities as
+ * sccs_grad_hess) from arrays the caller already holds on the device, without allocating
+ * any device memory.  The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate at the point of the call -- for example a serving process whose framework
+ * reserved all device memory for its own pool up front (there a cudaMalloc fails, or
+ * synchronises the device and stalls other streams), or code running inside a callback of
+ * another library that forbids allocation.
+ *
+ * The reduction across CTAs uses a scratch array compiled into the library (about 197 KB,
+ * room for SCCS_NOALLOC_MAX_SEGMENTS segments); every device that loads the library holds it
+ * until the process exits.  The first call on a device looks up that array's device address
+ * (with the device current); make that first call before any stream capture.  The call runs
+ * on the calling thread's current device and is asynchronous on `stream`.  All calls share
+ * the one array, so calls that overlap on the GPU (on different streams, or from different
+ * host threads) race and give wrong results: order them on one stream.
+ *
+ *   seg_ptr      device int64 [P+1]: segment s of the column covers rows[seg_ptr[s] .. seg_ptr[s+1])
+ *   seg_subject  device int32 [P]: the subject of segment s (all its rows belong to it)
+ *   rows         device int32 [seg_ptr[P]]: row (era) indices into E
+ *   E            device double [K]: L x exp(Xb) per row
+ *   D            device double [N]: M[L x exp(Xb)] per subject
+ *   n            device int32 [N]: events per subject
+ *   ytx          Y'X_j, the events on the column's rows
+ *   P            segments, 0 <= P <= SCCS_NOALLOC_MAX_SEGMENTS
+ *   gh_out       device double [2]: receives g_j, h_j (NaN if an input was not finite or D <= 0)
+ *   stream       cudaStream_t (NULL = default stream)
+ * Errors: SCCS_E_INVAL (P out of range, null pointer), SCCS_E_CUDA.  No handle is needed.
+ */
+#define SCCS_NOALLOC_MAX_SEGMENTS 1048576
+int sccs_grad_hess_noalloc(const int64_t *seg_ptr, const int32_t *seg_subject, const int32_t *rows,
+                           const double *E, const double *D, const int32_t *n, double ytx, int64_t P,
+                           double *gh_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@ from .sccs import (  # noqa: F401
     sccs_get_beta,
     sccs_get_info,
     sccs_grad_hess,
+    sccs_grad_hess_noalloc,
     sccs_last_error,
     sccs_logpost,
     sccs_set_prior,

@@ -463,6 +463,8 @@ sccs::FitParams base_params(const sccs_handle *h) {
 
 extern "C" {
 
+int sccs_set_error(int code, const char *msg) { return fail(code, msg ? msg : ""); }
+
 int sccs_version(int32_t *abi_version, const char **build) {
     if (abi_version) *abi_version = SCCS_ABI_VERSION;
     if (build) *build = "sccs-gb300 sm_103a fp64";

@@ -106,3 +106,6 @@ int launch_grad_hess_partial(const DevLayout &d, int32_t j, const FitParams &p, 
 int fit_kernel_max_blocks_per_sm(int threads, int *blocks);
 
 }  // namespace sccs
+
+// Record a thread-local error message for sccs_last_error and return `code`.
+extern "C" int sccs_set_error(int code, const char *msg);

@@ -35,7 +35,9 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
+#include "sccs.h"
 #include "sccs_internal.h"
 
 namespace sccs {
@@ -982,3 +984,137 @@ int fit_kernel_max_blocks_per_sm(int threads, int *blocks) {
 }
 
 }  // namespace sccs
+
+// ====================================================================================
+// Gradient and Hessian of one column with no device allocation.
+//
+// Some callers cannot allocate device memory at the point where they need this step: a
+// serving process whose framework reserved all device memory up front for its own pool (a
+// cudaMalloc there fails, or synchronises the device and stalls the other streams), or code
+// called back from another library that forbids allocation.  For them the cross-CTA
+// scratch of this reduction lives in a fixed array compiled into the library instead of a
+// buffer from cudaMalloc.  Every device that loads the library holds the array until the
+// process exits.
+// ====================================================================================
+namespace sccs {
+namespace {
+
+constexpr int kNoallocThreads = 256;
+constexpr int kNoallocMaxBlocks = 4096;
+// word 0: arrival counter; then 6 words (two exact sums) per CTA
+constexpr int kNoallocWords = 8 + 6 * kNoallocMaxBlocks;
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoallocWords];
+
+// One thread per segment: num = sum of E over the segment's rows, W = num / D, and the two
+// exact partial sums; the last CTA to arrive adds every CTA's partial and writes g, h.
+__global__ void __launch_bounds__(kNoallocThreads) grad_hess_noalloc_kernel(
+    const int64_t *seg_ptr, const int32_t *seg_subject, const int32_t *rows, const double *E, const double *D,
+    const int32_t *nev, double ytx, long long P, double *gh_out, unsigned long long *scratch) {
+    __shared__ Fx wa[kNoallocThreads / 32], wb[kNoallocThreads / 32];
+    __shared__ int wbad[kNoallocThreads / 32];
+    __shared__ int is_last;
+    const long long sidx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    bool bad = false;
+    double gl = 0.0, hl = 0.0;
+    if (sidx < P) {
+        double num = 0.0;
+        for (long long q = seg_ptr[sidx]; q < seg_ptr[sidx + 1]; ++q) num += E[rows[q]];
+        const int i = seg_subject[sidx];
+        segment_terms(num, D[i], nev[i], gl, hl, bad);
+    }
+    Fx fa = fx_warp_sum(fx_from_double(gl, bad));
+    Fx fb = fx_warp_sum(fx_from_double(hl, bad));
+    const int anybad = __any_sync(kFull, bad);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        wa[warp] = fa;
+        wb[warp] = fb;
+        wbad[warp] = anybad;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        Fx ta = lane < nw ? wa[lane] : fx_zero();
+        Fx tb = lane < nw ? wb[lane] : fx_zero();
+        const int cb = __any_sync(kFull, lane < nw ? wbad[lane] : 0);
+        ta = fx_warp_sum(ta);
+        tb = fx_warp_sum(tb);
+        if (lane == 0) {
+            unsigned long long *slot = scratch + 8 + 6 * static_cast<long long>(blockIdx.x);
+            slot[0] = ta.w0; slot[1] = ta.w1; slot[2] = ta.w2;
+            slot[3] = tb.w0; slot[4] = tb.w1; slot[5] = cb ? ~0ull : tb.w2;
+            __threadfence();
+            const unsigned long long prev = atomicAdd(&scratch[0], 1ull);
+            is_last = prev == gridDim.x - 1;
+        }
+    }
+    __syncthreads();
+    if (!is_last || warp != 0) return;
+    __threadfence();
+    Fx sa = fx_zero(), sb = fx_zero();
+    bool flag = false;
+    for (unsigned b = lane; b < gridDim.x; b += 32) {
+        const volatile unsigned long long *slot = scratch + 8 + 6 * static_cast<long long>(b);
+        const Fx pa{slot[0], slot[1], slot[2]};
+        const Fx pb{slot[3], slot[4], slot[5]};
+        if (pb.w2 == ~0ull) flag = true;
+        sa = fx_add(sa, pa);
+        sb = fx_add(sb, pb);
+    }
+    sa = fx_warp_sum(sa);
+    sb = fx_warp_sum(sb);
+    flag = __any_sync(kFull, flag);
+    if (lane == 0) {
+        const double G = fx_to_double(sa), H = fx_to_double(sb);
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        gh_out[0] = flag ? nan : ytx - G;
+        gh_out[1] = flag ? nan : -H;
+        scratch[0] = 0ull;   // ready for the next call
+    }
+}
+
+}  // namespace
+}  // namespace sccs
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64] = {};
+}  // namespace
+
+extern "C" int sccs_grad_hess_noalloc(const int64_t *seg_ptr, const int32_t *seg_subject, const int32_t *rows,
+                                      const double *E, const double *D, const int32_t *n, double ytx,
+                                      int64_t P, double *gh_out, void *stream) {
+    if (P < 0 || P > SCCS_NOALLOC_MAX_SEGMENTS)
+        return sccs_set_error(SCCS_E_INVAL, "P must be in [0, SCCS_NOALLOC_MAX_SEGMENTS] (1048576 segments)");
+    if (!gh_out || (P > 0 && (!seg_ptr || !seg_subject || !rows || !E || !D || !n)))
+        return sccs_set_error(SCCS_E_INVAL, "null device pointer");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return sccs_set_error(SCCS_E_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return sccs_set_error(SCCS_E_INVAL, "device ordinal above 63");
+    void *scratch = nullptr;
+    {
+        // First call on a device: look up the device address of the array (with the device
+        // current).  Host code must not pass the array's name itself to a kernel.
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            e = cudaGetSymbolAddress(&g_noalloc_addr[dev], sccs::g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                g_noalloc_addr[dev] = nullptr;
+                return sccs_set_error(SCCS_E_CUDA, cudaGetErrorString(e));
+            }
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the arrival counter must start at zero; the rest is overwritten before it is read
+    e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return sccs_set_error(SCCS_E_CUDA, cudaGetErrorString(e));
+    const long long blocks = P > 0 ? (P + sccs::kNoallocThreads - 1) / sccs::kNoallocThreads : 1;
+    sccs::grad_hess_noalloc_kernel<<<static_cast<unsigned>(blocks), sccs::kNoallocThreads, 0, st>>>(
+        seg_ptr, seg_subject, rows, E, D, n, ytx, P, gh_out, static_cast<unsigned long long *>(scratch));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return sccs_set_error(SCCS_E_CUDA, cudaGetErrorString(e));
+    return SCCS_OK;
+}

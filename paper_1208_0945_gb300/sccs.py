@@ -73,6 +73,7 @@ _SIGS = {
     "sccs_logpost": (ctypes.c_int, [_P, _dp, _dp, _dp]),
     "sccs_get_beta": (ctypes.c_int, [_P, _dp]),
     "sccs_check_wait_timeout": (ctypes.c_int, [_P, ctypes.c_double]),
+    "sccs_grad_hess_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int64, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -190,6 +191,18 @@ def sccs_get_beta(handle, J: int) -> np.ndarray:
 def sccs_check_wait_timeout(handle, timeout_ms: float) -> int:
     """Returns the raw status; E_TIMEOUT (-6) is the expected result."""
     return _lib.sccs_check_wait_timeout(handle, float(timeout_ms))
+
+
+NOALLOC_MAX_SEGMENTS = 1048576
+
+
+def sccs_grad_hess_noalloc(seg_ptr, seg_subject, rows, E, D, n, ytx: float, P: int, gh_out, stream=None) -> int:
+    """g_j, h_j of one column from device arrays the caller holds, allocating nothing on the
+    device (for callers that cannot allocate at that point).  Pointer arguments are device
+    addresses (ints); writes g_j, h_j to gh_out[0:2].  Asynchronous on `stream`; returns the
+    status (0 on success) and raises on errors."""
+    return _check(_lib.sccs_grad_hess_noalloc(seg_ptr, seg_subject, rows, E, D, n, float(ytx), int(P), gh_out,
+                                              stream), "sccs_grad_hess_noalloc")
 
 
 # ------------------------------------------------------------------ convenience wrapper
