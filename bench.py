@@ -41,6 +41,22 @@ def workload_config(d, fit):
     }
 
 
+def recorded_traffic():
+    """DRAM bytes per fit-kernel launch from the committed ncu record, if it was taken on the
+    kernel source that is built now (else None: the counters are stale)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "fit_kernel_traffic_mid_1M_subjects.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, rec["kernel_source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if sha != rec["kernel_source_sha256"]:
+            return None
+        return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+    except Exception:
+        return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -271,7 +287,8 @@ def run_ours(args, rank, world, local):
                     "shards": info["num_shards"], "threads_per_block": info["threads_per_block"],
                     "wall_s": wall},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": recorded_traffic() if args.scale == 1.0 else None,
                          "kernel": "fit_kernel (one persistent launch per fit)",
                          "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_kind},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
