@@ -77,6 +77,15 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p) {
     return v;
 }
 
+// Barrier 1 among warps 1..n-1 (warp 0 is busy with the all-reduce).
+__device__ __forceinline__ void named_barrier_all_but_warp0() {
+    asm volatile("bar.sync 1, %0;" ::"r"(static_cast<int>(blockDim.x) - 32) : "memory");
+}
+
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // ------------------------------------------------------------------ bulk copies, mbarriers
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -259,6 +268,8 @@ struct SharedState {
     int wbad[kMaxWarps];
     double db, r, em1;
     double G, H;
+    double lin, sq, ab;     // cycle sums of b_j Y'X_j, b_j^2, |b_j| (from the bookkeeping thread)
+    long long nonzero;
     int ok;
     int stop;
     ColDesc desc[2];
@@ -525,13 +536,27 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, double &G, doub
     const int ngrp = static_cast<int>(d.slice_grp[so + 1] - grp0);
     double *stash = d.stash + 2 * static_cast<long long>(s) * d.stash_stride;
     bool first = true;
+    // the next group's descriptors are loaded one group ahead
+    int2 sg_next = make_int2(0, 0);
+    long long base_next = 0;
+    if (warp < ngrp) {
+        const long long si = seg0 + 32 * static_cast<long long>(warp) + lane;
+        sg_next = si < seg1 ? d.segs[si] : make_int2(0, 0);
+        base_next = d.grp_base[grp0 + warp];
+    }
     for (int g = warp; g < ngrp; g += nwarps) {
         const long long si = seg0 + 32 * static_cast<long long>(g) + lane;
         const bool valid = si < seg1;
-        const int2 sg = valid ? d.segs[si] : make_int2(0, 0);
+        const int2 sg = sg_next;
+        long long base = base_next;
+        const int gn = g + nwarps;
+        if (gn < ngrp) {
+            const long long sn = seg0 + 32 * static_cast<long long>(gn) + lane;
+            sg_next = sn < seg1 ? d.segs[sn] : make_int2(0, 0);
+            base_next = d.grp_base[grp0 + gn];
+        }
         const double Dv = valid ? d.D[sg.x] : 1.0;
         const int nv = valid ? d.nev[sg.x] : 0;
-        long long base = d.grp_base[grp0 + g];
         const int maxlen = __shfl_sync(kFull, sg.y, 0);
         double num = 0.0;
         for (int t0 = 0; t0 < maxlen; t0 += kBatch) {
@@ -665,6 +690,23 @@ __device__ bool issue_stage(const DevLayout &d, const SliceBounds &b, SmemLayout
     return true;
 }
 
+// Warps other than warp 0, while warp 0 runs the grid all-reduce: once the next column's
+// static slice has landed, pull the E, D and n_i lines it will gather into L1.  Only caches
+// are touched, so stale data is impossible; the copy wait is short and its failure harmless.
+__device__ void prefetch_staged_state(const DevLayout &d, const ColDesc &nd, const StageBuf &sb, uint64_t *bar,
+                                      uint32_t parity) {
+    if (!mbar_wait(bar, parity, 20000)) return;
+    const int t = threadIdx.x - 32, T = blockDim.x - 32;
+    const int32_t *srow = sb.rows + nd.row_off;
+    const int2 *sseg = sb.segs + nd.seg_off;
+    for (int p = t; p < nd.nnz; p += T) prefetch_l1(d.E + srow[p]);
+    for (int si = t; si < nd.nseg; si += T) {
+        const int i = sseg[si].x;
+        prefetch_l1(d.D + i);
+        prefetch_l1(d.nev + i);
+    }
+}
+
 // ------------------------------------------------------------------ end of cycle
 
 // Recompute D_i = sum_{k in i} E_k on this CTA's subjects and all-reduce the positive and
@@ -710,11 +752,25 @@ __device__ void beta_terms(const DevLayout &d, const FitParams &p, double &lin, 
     logprior = p.prior == 1 ? -0.5 * sq * p.inv_var : (p.prior == 2 ? -p.lambda * ab : 0.0);
 }
 
-// Thread 0: wait (bounded) for any bulk copy still in flight into this CTA's shared memory.
+// The staging thread (last warp, lane 0): wait (bounded) for any bulk copy still in flight
+// into this CTA's shared memory.
 __device__ void drain_stages(SharedState &sh, unsigned pending, unsigned phase_bits, long long timeout_ns) {
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != static_cast<int>(blockDim.x) - 32) return;
     for (int b = 0; b < 2; ++b)
         if ((pending >> b) & 1u) (void)mbar_wait(&sh.bar[b], (phase_bits >> b) & 1u, timeout_ns);
+}
+
+// beta_j <- beta_j + db, the trust-region update T_j <- max(2|db|, T_j / 2), and the cycle's sums
+// for the log-posterior's linear and prior terms (in column order).
+__device__ __forceinline__ void bookkeep(double *beta, double *trust, int j, double b, double t, double y, double db,
+                                         double &lin, double &sq, double &ab, long long &nonzero) {
+    const double nbj = b + db;
+    beta[j] = nbj;
+    trust[j] = fmax(2.0 * fabs(db), 0.5 * t);
+    lin = fma(nbj, y, lin);
+    sq = fma(nbj, nbj, sq);
+    ab += fabs(nbj);
+    if (db != 0.0) ++nonzero;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -731,7 +787,7 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
     double *trust = d.trust_priv + static_cast<long long>(s) * d.J;
     const int J = d.J;
 
-    // staging state: pending and nb live in thread 0; phase_bits is tracked by every thread
+    // staging state: pending and nb live in the last warp's lane 0; phase_bits in every thread
     unsigned pending = 0u;      // buffers with an arrival issued and not yet waited for
     unsigned phase_bits = 0u;   // expected parity per buffer
     SliceBounds nb{};           // bounds of the column after the staged one
@@ -746,11 +802,14 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
         mbar_init_fence();
         sh.desc[0].staged = 0;
         sh.desc[1].staged = 0;
-        if (J > 0 && p.max_cycles > 0) {
-            const SliceBounds b0 = load_bounds(d, s, 0);
-            if (issue_stage(d, b0, sm, sh, 0)) pending |= 1u;
-            nb = load_bounds(d, s, J > 1 ? 1 : 0);
-        }
+        sh.nonzero = 0;
+    }
+    __syncthreads();
+    // staging (copies, pending set, next bounds) belongs to the last warp's lane 0
+    if (threadIdx.x == static_cast<int>(blockDim.x) - 32 && J > 0 && p.max_cycles > 0) {
+        const SliceBounds b0 = load_bounds(d, s, 0);
+        if (issue_stage(d, b0, sm, sh, 0)) pending |= 1u;
+        nb = load_bounds(d, s, J > 1 ? 1 : 0);
     }
     __syncthreads();
 
@@ -767,92 +826,164 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
         __syncthreads();
         status = sh.stop;
     }
-    for (int c = 1; c <= p.max_cycles && status == kStNotConverged; ++c) {
+    {
+        // Bookkeeping of a finished column (beta, trust radius, the cycle's sums) is done by
+        // thread tb at the start of the next column, off the critical path.
+        const int tb = blockDim.x - 32;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+        int pend_j = -1;
+        double pend_b = 0.0, pend_t = 0.0, pend_y = 0.0, pend_db = 0.0;
         double lin_c = 0.0, sq_c = 0.0, ab_c = 0.0;
-        for (int j = 0; j < J; ++j, ++col) {
-            const int buf = static_cast<int>(col & 1);
-            // thread 0: stage the next column into the other buffer; prefetch this column's scalars
-            double bj = 0.0, tj = 0.0, yj = 0.0;
-            if (threadIdx.x == 0) {
-                if (issue_stage(d, nb, sm, sh, buf ^ 1)) pending |= 1u << (buf ^ 1);
-                const int jn = j + 1 < J ? j + 1 : 0;
-                const int jnn = jn + 1 < J ? jn + 1 : 0;
-                nb = load_bounds(d, s, jnn);
-                bj = beta[j];
-                tj = trust[j];
-                yj = d.ytx[j];
-            }
-            // desc[buf] was written a column ago and is stable; wait for its copies
-            const ColDesc cd = sh.desc[buf];
-            bool staged_ok = true;
-            if (cd.staged) {
-                staged_ok = mbar_wait(&sh.bar[buf], (phase_bits >> buf) & 1u, timeout);
-                phase_bits ^= 1u << buf;
-                if (threadIdx.x == 0) pending &= ~(1u << buf);
-            }
-            // one barrier: desc[buf ^ 1] published, and a CTA-wide verdict on the copies
-            staged_ok = __syncthreads_and(staged_ok) != 0;
-            double G = 0.0, H = 0.0;
-            bool bad = false;
-            if (cd.staged) {
-                if (staged_ok) {
-                    phase_a_staged(d, cd, sm.stage[buf], sm, G, H, bad);
-                } else {                           // never read a stage that did not arrive
-                    bad = true;
-                    if (threadIdx.x == 0) atomicExch(d.abort_flag, 1);
+        long long nonzero_tb = 0;
+        for (int c = 1; c <= p.max_cycles && status == kStNotConverged; ++c) {
+            lin_c = sq_c = ab_c = 0.0;
+            for (int j = 0; j < J; ++j, ++col) {
+                const int buf = static_cast<int>(col & 1);
+                double bj = 0.0, tj = 0.0, yj = 0.0;
+                if (threadIdx.x == 0 || threadIdx.x == tb) {
+                    bj = beta[j];
+                    tj = trust[j];
+                    yj = d.ytx[j];
                 }
-            } else {
-                phase_a_global(d, s, j, G, H, bad);
-            }
-            if (!block_grid_reduce(d, seq++, timeout, sh, G, H, bad)) goto aborted;
-            if (threadIdx.x == 0) {
-                const double g = yj - sh.G;
-                const double q = sh.H;
-                double db = newton_step(g, q, bj, p, tj, warn);
-                double em1 = 0.0;
-                if (!(db == db) || isinf(db) || !(g == g) || !(q == q)) {
-                    db = 0.0;
-                    status = kStNumeric;
-                } else if (db != 0.0) {
-                    em1 = expm1(db);
+                // desc[buf] was written a column ago and is stable; wait for its copies
+                const ColDesc cd = sh.desc[buf];
+                bool staged_ok = true;
+                if (cd.staged) {
+                    staged_ok = mbar_wait(&sh.bar[buf], (phase_bits >> buf) & 1u, timeout);
+                    phase_bits ^= 1u << buf;
+                    if (threadIdx.x == tb) pending &= ~(1u << buf);
                 }
-                sh.db = db;
-                sh.em1 = em1;
-                sh.r = 1.0 + em1;
+                // a CTA-wide verdict on the copies (buffer buf ^ 1 is free from here on)
+                staged_ok = __syncthreads_and(staged_ok) != 0;
+                if (threadIdx.x == tb) {
+                    // stage the next column, then the deferred bookkeeping of the previous one
+                    if (issue_stage(d, nb, sm, sh, buf ^ 1)) pending |= 1u << (buf ^ 1);
+                    const int jn = j + 1 < J ? j + 1 : 0;
+                    const int jnn = jn + 1 < J ? jn + 1 : 0;
+                    nb = load_bounds(d, s, jnn);
+                    if (pend_j >= 0) {
+                        bookkeep(beta, trust, pend_j, pend_b, pend_t, pend_y, pend_db, lin_c, sq_c, ab_c, nonzero_tb);
+                        pend_j = -1;
+                    }
+                }
+                double G = 0.0, H = 0.0;
+                bool bad = false;
+                if (cd.staged) {
+                    if (staged_ok) {
+                        phase_a_staged(d, cd, sm.stage[buf], sm, G, H, bad);
+                    } else {                           // never read a stage that did not arrive
+                        bad = true;
+                        if (threadIdx.x == 0) atomicExch(d.abort_flag, 1);
+                    }
+                } else {
+                    phase_a_global(d, s, j, G, H, bad);
+                }
+                // A slice of at most one group lives in warp 0 alone: its warp sum is the CTA's.
+                const bool one_warp = cd.staged && cd.ngrp <= 1;
+                if (!one_warp) {
+                    const Fx fa = fx_warp_sum(fx_from_double(G, bad));
+                    const Fx fb = fx_warp_sum(fx_from_double(H, bad));
+                    const int wbad = __any_sync(kFull, bad);
+                    if (lane == 0) {
+                        sh.wa[warp] = fa;
+                        sh.wb[warp] = fb;
+                        sh.wbad[warp] = wbad;
+                    }
+                    __syncthreads();
+                }
+                if (warp == 0) {
+                    Fx ta, tbx;
+                    bool cbad;
+                    if (one_warp) {
+                        ta = fx_warp_sum(fx_from_double(G, bad));
+                        tbx = fx_warp_sum(fx_from_double(H, bad));
+                        cbad = __any_sync(kFull, bad);
+                    } else {
+                        ta = lane < nwarps ? sh.wa[lane] : fx_zero();
+                        tbx = lane < nwarps ? sh.wb[lane] : fx_zero();
+                        cbad = __any_sync(kFull, lane < nwarps ? sh.wbad[lane] != 0 : false);
+                        ta = fx_warp_sum(ta);
+                        tbx = fx_warp_sum(tbx);
+                    }
+                    double ca = fx_to_double(ta), cb = fx_to_double(tbx);
+                    if (cbad) ca = cb = __longlong_as_double(0x7ff8000000000000ll);
+                    ca = __shfl_sync(kFull, ca, 0);
+                    cb = __shfl_sync(kFull, cb, 0);
+                    // grid all-reduce, then the step in lane 0 (no extra barrier)
+                    double At = 0.0, Bt = 0.0;
+                    const bool ok = grid_allreduce2(d, seq, ca, cb, At, Bt, timeout);
+                    if (lane == 0) {
+                        double db = 0.0, r = 1.0, em1 = 0.0;
+                        if (ok) {
+                            const double g = yj - At, q = Bt;
+                            db = newton_step(g, q, bj, p, tj, warn);
+                            if (!(db == db) || isinf(db) || !(g == g) || !(q == q)) {
+                                db = 0.0;
+                                status = kStNumeric;
+                            } else if (db != 0.0) {
+                                // e^db - 1 only scales the D update, whose rounding dominates
+                                r = exp(db);
+                                em1 = r - 1.0;
+                            }
+                        }
+                        sh.ok = ok;
+                        sh.db = db;
+                        sh.r = r;
+                        sh.em1 = em1;
+                    }
+                } else {
+                    // warps 1..: desc[buf ^ 1] (written by thread tb) is visible after this barrier
+                    if (one_warp) named_barrier_all_but_warp0();
+                    const ColDesc &nd = sh.desc[buf ^ 1];
+                    if (nd.staged)
+                        prefetch_staged_state(d, nd, sm.stage[buf ^ 1], &sh.bar[buf ^ 1], (phase_bits >> (buf ^ 1)) & 1u);
+                }
+                ++seq;
+                __syncthreads();
+                if (!sh.ok) goto aborted;
+                const double db = sh.db;
+                if (db != 0.0) {
+                    if (cd.staged) phase_c_staged(d, cd, sm.stage[buf], sm, sh.r, sh.em1);
+                    else phase_c_global(d, s, j, sh.r, sh.em1);
+                }
+                if (threadIdx.x == tb) {
+                    pend_j = j;
+                    pend_b = bj;
+                    pend_t = tj;
+                    pend_y = yj;
+                    pend_db = db;
+                }
+                __syncthreads();   // E and D writes visible to the next column's reads
+            }
+            if (threadIdx.x == tb) {
+                if (pend_j >= 0) {
+                    bookkeep(beta, trust, pend_j, pend_b, pend_t, pend_y, pend_db, lin_c, sq_c, ab_c, nonzero_tb);
+                    pend_j = -1;
+                }
+                sh.lin = lin_c;
+                sh.sq = sq_c;
+                sh.ab = ab_c;
+                sh.nonzero = nonzero_tb;
             }
             __syncthreads();
-            const double db = sh.db;
-            if (db != 0.0) {
-                if (cd.staged) phase_c_staged(d, cd, sm.stage[buf], sm, sh.r, sh.em1);
-                else phase_c_global(d, s, j, sh.r, sh.em1);
-            }
+            if (!refresh_and_reduce(d, seq++, timeout, sh)) goto aborted;
             if (threadIdx.x == 0) {
-                const double nbj = bj + db;
-                beta[j] = nbj;
-                trust[j] = fmax(2.0 * fabs(db), 0.5 * tj);
-                lin_c = fma(nbj, yj, lin_c);
-                sq_c = fma(nbj, nbj, sq_c);
-                ab_c += fabs(nbj);
-                if (db != 0.0) ++nonzero;
+                const double lp = p.prior == 1 ? -0.5 * sh.sq * p.inv_var : (p.prior == 2 ? -p.lambda * sh.ab : 0.0);
+                loglik = sh.lin - (sh.G - sh.H);
+                P = loglik + lp;
+                if (leader && p.record_history) hist[c] = P;
+                conv = fabs(P - P_prev);
+                if (p.tol_mode == 1) conv /= fmax(1.0, fabs(P));
+                cycles = c;
+                if (!(P == P) || isinf(P)) status = kStNumeric;
+                else if (status == kStNotConverged && p.tol >= 0.0 && conv < p.tol) status = kStOk;
+                P_prev = P;
+                sh.stop = status;
             }
-            __syncthreads();   // E and D writes visible to the next column's reads
+            __syncthreads();
+            status = sh.stop;
         }
-        if (!refresh_and_reduce(d, seq++, timeout, sh)) goto aborted;
-        if (threadIdx.x == 0) {
-            const double lp = p.prior == 1 ? -0.5 * sq_c * p.inv_var : (p.prior == 2 ? -p.lambda * ab_c : 0.0);
-            loglik = lin_c - (sh.G - sh.H);
-            P = loglik + lp;
-            if (leader && p.record_history) hist[c] = P;
-            conv = fabs(P - P_prev);
-            if (p.tol_mode == 1) conv /= fmax(1.0, fabs(P));
-            cycles = c;
-            if (!(P == P) || isinf(P)) status = kStNumeric;
-            else if (status == kStNotConverged && p.tol >= 0.0 && conv < p.tol) status = kStOk;
-            P_prev = P;
-            sh.stop = status;
-        }
-        __syncthreads();
-        status = sh.stop;
+        nonzero = sh.nonzero;
     }
     drain_stages(sh, pending, phase_bits, timeout);
     if (leader) {
