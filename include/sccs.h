@@ -57,6 +57,11 @@ extern "C" {
 
 /* ---- arithmetic ----------------------------------------------------------------------- */
 #define SCCS_PREC_FP64 0         /* every step in FP64 */
+#define SCCS_PREC_FP32_POLISH 1  /* FP32 phase (FP32 E, compensated per-subject sums, exact
+                                    cross-subject sums, FP64 step) to a relative change of
+                                    1e-6, then FP64 cycles from that point to the requested tol
+                                    (tol < 0: exactly max_cycles FP64 cycles) */
+#define SCCS_PREC_FP32 2         /* the FP32 phase alone, to the requested tol (no polish) */
 
 typedef struct sccs_handle sccs_handle;
 
@@ -98,9 +103,10 @@ typedef struct sccs_fit_opts {
     int32_t tol_mode;          /* SCCS_TOL_* */
     int32_t max_cycles;        /* >= 0; 0 only evaluates P at the start point */
     double tol;                /* < 0 runs exactly max_cycles cycles */
-    int32_t precision;         /* SCCS_PREC_FP64 */
+    int32_t precision;         /* SCCS_PREC_FP64, SCCS_PREC_FP32_POLISH or SCCS_PREC_FP32 */
     int32_t reserved;
-    double *logpost_history;   /* optional host buffer of max_cycles + 1 values: P_0 .. P_cycles */
+    double *logpost_history;   /* optional host buffer of max_cycles + 1 values: P_0 .. P_c of the
+                                  last phase run (the FP64 polish in SCCS_PREC_FP32_POLISH) */
 } sccs_fit_opts;
 
 typedef struct sccs_fit_info {
@@ -113,7 +119,7 @@ typedef struct sccs_fit_info {
     double kernel_ms;          /* device time of the fit kernel (CUDA events) */
     double total_ms;           /* host wall time of the call */
     int32_t warnings;          /* bit 0: an unbounded coordinate took the trust-region bound */
-    int32_t reserved;
+    int32_t fp32_cycles;       /* cycles of the FP32 phase (FP32 modes), included in `cycles` */
 } sccs_fit_info;
 
 /* Library identification: ABI version and "sm_103a" build string. */
@@ -172,6 +178,22 @@ int sccs_set_prior(sccs_handle *h, int32_t prior_type, double variance);
  * SCCS_E_TIMEOUT, SCCS_E_CUDA, SCCS_E_UNSUPPORTED).  After an error the handle's beta is 0.
  */
 int sccs_fit(sccs_handle *h, const sccs_fit_opts *opts, double *beta_out, sccs_fit_info *info);
+
+/*
+ * sccs_fit_batch -- independent MAP fits (Algorithm 1 on each handle's dataset and prior) in
+ * one persistent cooperative launch.  Handle k's num_shards CTAs form team k; a team exchanges
+ * partial sums only with itself, so teams never wait on one another and each fit gives bit for
+ * bit what sccs_fit gives on the same handle.  Teams that do not fit on the device together run
+ * in successive launches.  Handles must share the device and threads_per_block; the work runs
+ * on handles[0]'s stream.
+ *   opts      shared by all fits (NULL = sccs_fit's defaults); beta0 must be NULL (warm_start
+ *             applies to every handle)
+ *   beta_out  NULL, or n host pointers (each NULL or [J_k])
+ *   infos     NULL, or n entries; infos[k].kernel_ms is the time of the whole batch
+ * Returns SCCS_OK, or the first failing fit's error (every infos[k].status is filled).
+ */
+int sccs_fit_batch(sccs_handle *const *handles, int32_t n, const sccs_fit_opts *opts, double *const *beta_out,
+                   sccs_fit_info *infos);
 
 /*
  * sccs_grad_hess -- the log-likelihood derivatives along coordinate j (Eqs. 7-9, no prior):

@@ -11,6 +11,7 @@ from .sccs import (  # noqa: F401
     sccs_create,
     sccs_destroy,
     sccs_fit,
+    sccs_fit_batch,
     sccs_get_beta,
     sccs_get_info,
     sccs_grad_hess,

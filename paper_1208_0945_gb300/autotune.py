@@ -1,0 +1,104 @@
+"""Team-size autotuner for batched fits.
+
+A fit run by a team of S CTAs costs, per CCD cycle, about
+
+    t(S) = J * lat(S) + nnz * c / S
+
+where lat(S) is the per-coordinate latency of a team of S CTAs (phase A on a tiny slice, the
+team's all-reduce, the FP64 step, phase C) and c the device time per nonzero on one CTA.  Both
+are measured on the device with probe fits through the library (`measure`).  `assign` then
+gives every fit of a batch a team size by greedy makespan minimisation: start from one CTA per
+fit and repeatedly grow the team of the currently slowest fit while that shortens it and the
+teams still fit on the device together.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import sccs as _s
+
+
+@dataclasses.dataclass
+class CostModel:
+    lat_us: dict          # team size -> microseconds per coordinate step
+    c_us_per_nnz: float   # microseconds per nonzero on one CTA
+    capacity: int         # CTAs the device holds at once
+
+    def latency(self, S: int) -> float:
+        ks = sorted(self.lat_us)
+        if S <= ks[0]:
+            return self.lat_us[ks[0]]
+        if S >= ks[-1]:
+            return self.lat_us[ks[-1]]
+        hi = next(k for k in ks if k >= S)
+        lo = max(k for k in ks if k <= S)
+        if hi == lo:
+            return self.lat_us[lo]
+        w = (np.log(S) - np.log(lo)) / (np.log(hi) - np.log(lo))
+        return (1 - w) * self.lat_us[lo] + w * self.lat_us[hi]
+
+    def cycle_us(self, J: int, nnz: int, S: int) -> float:
+        return J * self.latency(S) + nnz * self.c_us_per_nnz / S
+
+
+def _probe(data, S, device, cycles):
+    with _s.SCCSModel(data, device=device, num_shards=S) as m:
+        m.set_prior("normal", 1.0)
+        m.fit(tol=-1.0, max_cycles=1)                       # warm-up
+        r = m.fit(tol=-1.0, max_cycles=cycles)
+        return r["kernel_ms"] * 1e3 / cycles, m.info
+
+
+def measure(device: int = 0, team_sizes=(1, 2, 4, 8, 16, 32, 64, 128), cycles: int = 3) -> CostModel:
+    from synth import make_dataset
+    import ctypes
+
+    # latency: many tiny columns (one or two nonzeros per shard)
+    tiny = make_dataset(n_patients=3000, eras=("uniform", 1, 4), J=64, columns=("density", 0.01), n_true=0,
+                        beta_sd=0.0, seed=5150)
+    # throughput: a few dense columns
+    dense = make_dataset(n_patients=150_000, eras=("geometric", 8), J=4, columns=("density", 0.3), n_true=0,
+                         beta_sd=0.0, seed=5151)
+    cap = _capacity(device)
+    lat = {}
+    for S in team_sizes:
+        if S > cap:
+            continue
+        us, _ = _probe(tiny, S, device, cycles)
+        lat[S] = us / tiny.J
+    S_big = max(k for k in lat)
+    us, info = _probe(dense, S_big, device, cycles)
+    c = max(us - dense.J * lat[S_big], 1e-3) * S_big / max(info["nnz_kept"], 1)
+    return CostModel(lat_us=lat, c_us_per_nnz=c, capacity=cap)
+
+
+def _capacity(device: int) -> int:
+    import torch
+
+    props = torch.cuda.get_device_properties(device)
+    return int(props.multi_processor_count)   # one CTA per SM (512 threads, ~134 KB shared memory)
+
+
+def assign(fits, model: CostModel, capacity: int | None = None) -> list:
+    """fits: [(J, nnz per cycle)], returns a team size per fit (sum <= capacity when possible)."""
+    cap = capacity or model.capacity
+    S = [1] * len(fits)
+    t = [model.cycle_us(J, nnz, 1) for J, nnz in fits]
+    used = len(fits)
+    frozen = set()
+    while used < cap:
+        cand = [f for f in range(len(fits)) if f not in frozen]
+        if not cand:
+            break
+        f = max(cand, key=lambda k: t[k])
+        J, nnz = fits[f]
+        t_new = model.cycle_us(J, nnz, S[f] + 1)
+        if t_new >= t[f]:
+            frozen.add(f)
+            continue
+        S[f] += 1
+        t[f] = t_new
+        used += 1
+    return S

@@ -36,6 +36,9 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 constexpr long long kDefaultWaitNs = 2000000000LL;  // 2 s per device-side wait
+// SCCS_PREC_FP32_POLISH: the FP32 phase stops at this relative change of the log-posterior
+// (about what FP32 arithmetic can still resolve); the FP64 polish takes it from there.
+constexpr double kFp32PhaseRelTol = 1e-6;
 
 // Run f(t) for t in [0, n) on up to hardware_concurrency threads.
 template <class F>
@@ -459,6 +462,32 @@ sccs::FitParams base_params(const sccs_handle *h) {
     return p;
 }
 
+// One launch of the fit kernel (FP64 or FP32 body) with its result checks; `ms` gets the
+// kernel's event time.
+int run_fit_phase(sccs_handle *h, const sccs::FitParams &p, bool fp32, sccs::FitOut &r, float &ms) {
+    sccs::FitParams pp = p;
+    pp.seq0 = h->seq;
+    cudaEventRecord(h->ev0, h->stream);
+    int le = sccs::launch_fit(h->d, pp, h->out_dev, h->hist_dev, h->threads, h->stream, fp32);
+    if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "fit kernel launch");
+    cudaEventRecord(h->ev1, h->stream);
+    int rc = sync_out(h);
+    if (rc) return rc;
+    r = *h->out_host;
+    if (r.status == -6 || r.abort_flag) {
+        reset_after_abort(h);
+        return fail(SCCS_E_TIMEOUT, "a device-side wait exceeded its bound; the handle was reset to beta = 0");
+    }
+    h->seq = r.seq_end;
+    if (r.status == -7) {
+        run_init_state(h, nullptr);
+        cudaStreamSynchronize(h->stream);
+        return fail(SCCS_E_NUMERIC, "non-finite gradient, step or log-posterior; the handle was reset to beta = 0");
+    }
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    return SCCS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -580,6 +609,8 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     d.stash_stride = hl.stash_stride;
     if ((rc = alloc_zero(h, &d.E, static_cast<size_t>(hl.K))) ||
         (rc = alloc_zero(h, &d.D, static_cast<size_t>(hl.N))) ||
+        (rc = alloc_zero(h, &d.E32, static_cast<size_t>(hl.K))) ||
+        (rc = alloc_zero(h, &d.D32, static_cast<size_t>(hl.N))) ||
         (rc = alloc_zero(h, &d.beta_priv, static_cast<size_t>(S) * std::max<int32_t>(J, 1))) ||
         (rc = alloc_zero(h, &d.trust_priv, static_cast<size_t>(S) * std::max<int32_t>(J, 1))) ||
         (rc = alloc_zero(h, &d.stash, static_cast<size_t>(S) * 2 * static_cast<size_t>(hl.stash_stride))) ||
@@ -650,7 +681,8 @@ int sccs_fit(sccs_handle *h, const sccs_fit_opts *opts, double *beta_out, sccs_f
         return fail(SCCS_E_UNSUPPORTED, "the Genkin X-beta convergence test is not in this build");
     if (o.tol_mode != SCCS_TOL_ABS_LOGPOST && o.tol_mode != SCCS_TOL_REL_LOGPOST)
         return fail(SCCS_E_INVAL, "unknown tol_mode");
-    if (o.precision != SCCS_PREC_FP64) return fail(SCCS_E_UNSUPPORTED, "only SCCS_PREC_FP64 in this build");
+    if (o.precision != SCCS_PREC_FP64 && o.precision != SCCS_PREC_FP32_POLISH && o.precision != SCCS_PREC_FP32)
+        return fail(SCCS_E_INVAL, "unknown precision");
     int rc = set_device(h);
     if (rc) return rc;
 
@@ -683,24 +715,42 @@ int sccs_fit(sccs_handle *h, const sccs_fit_opts *opts, double *beta_out, sccs_f
     p.tol = o.tol;
     p.max_cycles = o.max_cycles;
     p.record_history = 1;
-    cudaEventRecord(h->ev0, h->stream);
-    int le = sccs::launch_fit(h->d, p, h->out_dev, h->hist_dev, h->threads, h->stream);
-    if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "fit kernel launch");
-    cudaEventRecord(h->ev1, h->stream);
-    if ((rc = sync_out(h))) return rc;
-    const sccs::FitOut r = *h->out_host;
-    if (r.status == -6 || r.abort_flag) {
-        reset_after_abort(h);
-        return fail(SCCS_E_TIMEOUT, "a device-side wait exceeded its bound; the handle was reset to beta = 0");
+
+    sccs::FitOut r{};
+    float ms = 0.f, ms32 = 0.f;
+    int32_t fp32_cycles = 0;
+    int64_t nonzero = 0;
+    int32_t warnings = 0;
+    if (o.precision != SCCS_PREC_FP64) {
+        int le = sccs::launch_e_to_f32(h->d, h->threads, h->stream);
+        if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "E conversion launch");
+        sccs::FitParams p32 = p;
+        if (o.precision == SCCS_PREC_FP32_POLISH) {
+            // the FP32 phase always stops at its own switch point; the caller's tol (including
+            // tol < 0, a fixed number of cycles) applies to the FP64 polish
+            p32.tol_mode = SCCS_TOL_REL_LOGPOST;
+            p32.tol = kFp32PhaseRelTol;
+        }
+        if ((rc = run_fit_phase(h, p32, true, r, ms32))) return rc;
+        fp32_cycles = r.cycles;
+        nonzero += r.nonzero_steps;
+        warnings |= r.warnings;
+        if (o.precision == SCCS_PREC_FP32_POLISH) {
+            // FP64 polish from the FP32 point: E and D rebuilt in FP64 from beta, trust radii kept
+            cudaError_t e = cudaMemcpyAsync(h->beta_dev, h->d.beta_priv, sizeof(double) * std::max<int32_t>(h->d.J, 1),
+                                            cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync polish start");
+            le = sccs::launch_init_state(h->d, h->beta_dev, h->threads, h->stream, true);
+            if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "init_state launch");
+            if ((rc = run_fit_phase(h, p, false, r, ms))) return rc;
+            nonzero += r.nonzero_steps;
+            warnings |= r.warnings;
+        }
+    } else {
+        if ((rc = run_fit_phase(h, p, false, r, ms))) return rc;
+        nonzero = r.nonzero_steps;
+        warnings = r.warnings;
     }
-    h->seq = r.seq_end;
-    if (r.status == -7) {
-        run_init_state(h, nullptr);
-        cudaStreamSynchronize(h->stream);
-        return fail(SCCS_E_NUMERIC, "non-finite gradient, step or log-posterior; the handle was reset to beta = 0");
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     if (beta_out && h->d.J > 0) {
         cudaError_t e = cudaMemcpy(beta_out, h->d.beta_priv, sizeof(double) * h->d.J, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "copy beta");
@@ -710,19 +760,221 @@ int sccs_fit(sccs_handle *h, const sccs_fit_opts *opts, double *beta_out, sccs_f
                                    cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "copy history");
     }
+    const int32_t total_cycles = o.precision == SCCS_PREC_FP32_POLISH ? fp32_cycles + r.cycles : r.cycles;
     if (info) {
         info->status = r.status;
-        info->cycles = r.cycles;
-        info->steps = static_cast<int64_t>(r.cycles) * h->d.J;
-        info->nonzero_steps = r.nonzero_steps;
+        info->cycles = total_cycles;
+        info->steps = static_cast<int64_t>(total_cycles) * h->d.J;
+        info->nonzero_steps = nonzero;
         info->logpost = r.logpost;
         info->conv_value = r.conv;
-        info->kernel_ms = ms;
+        info->kernel_ms = ms + ms32;
         info->total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-        info->warnings = r.warnings;
-        info->reserved = 0;
+        info->warnings = warnings;
+        info->fp32_cycles = fp32_cycles;
     }
     return r.status == 0 ? SCCS_OK : SCCS_NOT_CONVERGED;
+}
+
+int sccs_fit_batch(sccs_handle *const *handles, int32_t n, const sccs_fit_opts *opts, double *const *beta_out,
+                   sccs_fit_info *infos) {
+    const auto t_start = std::chrono::steady_clock::now();
+    if (n < 1 || !handles) return fail(SCCS_E_INVAL, "need at least one handle");
+    sccs_fit_opts o{};
+    o.struct_size = sizeof(sccs_fit_opts);
+    o.tol_mode = SCCS_TOL_REL_LOGPOST;
+    o.tol = 1e-12;
+    o.max_cycles = 1000;
+    o.precision = SCCS_PREC_FP64;
+    if (opts) {
+        if (opts->struct_size != static_cast<int32_t>(sizeof(sccs_fit_opts)))
+            return fail(SCCS_E_INVAL, "sccs_fit_opts.struct_size mismatch");
+        o = *opts;
+    }
+    if (o.beta0) return fail(SCCS_E_INVAL, "sccs_fit_batch takes no beta0 (use warm_start)");
+    if (o.max_cycles < 0) return fail(SCCS_E_INVAL, "max_cycles must be >= 0");
+    if (o.tol_mode != SCCS_TOL_ABS_LOGPOST && o.tol_mode != SCCS_TOL_REL_LOGPOST)
+        return fail(o.tol_mode == SCCS_TOL_GENKIN_XBETA ? SCCS_E_UNSUPPORTED : SCCS_E_INVAL, "unsupported tol_mode");
+    if (o.precision != SCCS_PREC_FP64 && o.precision != SCCS_PREC_FP32_POLISH && o.precision != SCCS_PREC_FP32)
+        return fail(SCCS_E_INVAL, "unknown precision");
+    for (int32_t k = 0; k < n; ++k) {
+        if (!handles[k]) return fail(SCCS_E_INVAL, "null handle in batch");
+        if (handles[k]->device != handles[0]->device) return fail(SCCS_E_INVAL, "handles on different devices");
+        if (handles[k]->threads != handles[0]->threads) return fail(SCCS_E_INVAL, "handles with different threads_per_block");
+        for (int32_t q = 0; q < k; ++q)
+            if (handles[q] == handles[k]) return fail(SCCS_E_INVAL, "a handle appears twice in the batch");
+    }
+    sccs_handle *h0 = handles[0];
+    int rc = set_device(h0);
+    if (rc) return rc;
+    const int threads = h0->threads;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h0->device);
+    if ((rc = sccs::fit_kernel_max_blocks_per_sm(threads, &per_sm))) return cuda_fail(static_cast<cudaError_t>(rc), "occupancy");
+    const int capacity = sms * per_sm;
+    cudaStream_t st = h0->stream;
+    for (int32_t k = 0; k < n; ++k) {
+        sccs_handle *h = handles[k];
+        if (h->stream != st) cudaStreamSynchronize(h->stream);   // no work of the handle in flight elsewhere
+        if (o.warm_start) {
+            cudaMemcpyAsync(h->beta_dev, h->d.beta_priv, sizeof(double) * std::max<int32_t>(h->d.J, 1),
+                            cudaMemcpyDeviceToDevice, st);
+            if ((rc = sccs::launch_init_state(h->d, h->beta_dev, threads, st))) return cuda_fail(static_cast<cudaError_t>(rc), "init");
+        } else if ((rc = sccs::launch_init_state(h->d, nullptr, threads, st))) {
+            return cuda_fail(static_cast<cudaError_t>(rc), "init");
+        }
+        const int32_t need = o.max_cycles + 1;
+        if (need > h->hist_cap) {
+            if (h->hist_dev) cudaFree(h->hist_dev);
+            if (h->hist_host) cudaFreeHost(h->hist_host);
+            h->hist_dev = nullptr;
+            h->hist_host = nullptr;
+            h->hist_cap = 0;
+            if (cudaMalloc(&h->hist_dev, sizeof(double) * need) != cudaSuccess ||
+                cudaMallocHost(&h->hist_host, sizeof(double) * need) != cudaSuccess)
+                return fail(SCCS_E_NOMEM, "history buffer");
+            h->hist_cap = need;
+        }
+        if (h->d.S > capacity) return fail(SCCS_E_INVAL, "a handle has more shards than the device holds at once");
+    }
+    // waves of fits whose shard counts fit on the device together
+    std::vector<std::vector<int32_t>> waves;
+    {
+        std::vector<int32_t> cur;
+        int used = 0;
+        for (int32_t k = 0; k < n; ++k) {
+            if (used + handles[k]->d.S > capacity) {
+                waves.push_back(cur);
+                cur.clear();
+                used = 0;
+            }
+            cur.push_back(k);
+            used += handles[k]->d.S;
+        }
+        if (!cur.empty()) waves.push_back(cur);
+    }
+    sccs::BatchEntry *ent_dev = nullptr;
+    int2 *map_dev = nullptr;
+    if (cudaMalloc(&ent_dev, sizeof(sccs::BatchEntry) * n) != cudaSuccess ||
+        cudaMalloc(&map_dev, sizeof(int2) * capacity) != cudaSuccess) {
+        cudaFree(ent_dev);
+        return fail(SCCS_E_NOMEM, "batch descriptors");
+    }
+    std::vector<sccs::BatchEntry> ent(n);
+    std::vector<int2> map;
+    std::vector<int> status(n, SCCS_OK);
+    std::vector<sccs::FitOut> res(n);
+    std::vector<int32_t> fp32_cycles(n, 0);
+    std::vector<int64_t> nonzero(n, 0);
+    std::vector<int32_t> warnings(n, 0);
+    double kernel_ms = 0.0;
+    auto run_phase = [&](bool fp32, bool polish_phase) -> int {
+        for (int32_t k = 0; k < n; ++k) {
+            sccs_handle *h = handles[k];
+            sccs::FitParams p = base_params(h);
+            p.tol_mode = o.tol_mode;
+            p.tol = o.tol;
+            p.max_cycles = o.max_cycles;
+            p.record_history = 1;
+            if (fp32 && o.precision == SCCS_PREC_FP32_POLISH) {
+                p.tol_mode = SCCS_TOL_REL_LOGPOST;
+                p.tol = kFp32PhaseRelTol;
+            }
+            ent[k] = sccs::BatchEntry{h->d, p, h->out_dev, h->hist_dev};
+        }
+        cudaMemcpyAsync(ent_dev, ent.data(), sizeof(sccs::BatchEntry) * n, cudaMemcpyHostToDevice, st);
+        for (const auto &w : waves) {
+            map.clear();
+            for (int32_t k : w)
+                for (int sidx = 0; sidx < handles[k]->d.S; ++sidx) map.push_back(make_int2(k, sidx));
+            cudaMemcpyAsync(map_dev, map.data(), sizeof(int2) * map.size(), cudaMemcpyHostToDevice, st);
+            cudaEventRecord(h0->ev0, st);
+            int le = sccs::launch_fit_batch(ent_dev, map_dev, static_cast<int>(map.size()), threads, st, fp32);
+            if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "batch kernel launch");
+            cudaEventRecord(h0->ev1, st);
+            cudaError_t e = cudaEventSynchronize(h0->ev1);
+            if (e != cudaSuccess) return cuda_fail(e, "batch kernel");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, h0->ev0, h0->ev1);
+            kernel_ms += ms;
+        }
+        for (int32_t k = 0; k < n; ++k)
+            cudaMemcpyAsync(handles[k]->out_host, handles[k]->out_dev, sizeof(sccs::FitOut), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch results");
+        for (int32_t k = 0; k < n; ++k) {
+            sccs_handle *h = handles[k];
+            if (status[k] != SCCS_OK) continue;
+            const sccs::FitOut r = *h->out_host;
+            if (r.status == -6 || r.abort_flag) {
+                reset_after_abort(h);
+                status[k] = SCCS_E_TIMEOUT;
+                continue;
+            }
+            h->seq = r.seq_end;
+            if (r.status == -7) {
+                run_init_state(h, nullptr);
+                status[k] = SCCS_E_NUMERIC;
+                continue;
+            }
+            res[k] = r;
+            nonzero[k] += r.nonzero_steps;
+            warnings[k] |= r.warnings;
+            if (fp32) fp32_cycles[k] = r.cycles;
+        }
+        (void)polish_phase;
+        return SCCS_OK;
+    };
+    auto done = [&](int code) {
+        cudaFree(ent_dev);
+        cudaFree(map_dev);
+        return code;
+    };
+    if (o.precision != SCCS_PREC_FP64) {
+        for (int32_t k = 0; k < n; ++k) {
+            int le = sccs::launch_e_to_f32(handles[k]->d, threads, st);
+            if (le != 0) return done(cuda_fail(static_cast<cudaError_t>(le), "E conversion launch"));
+        }
+        if ((rc = run_phase(true, false))) return done(rc);
+        if (o.precision == SCCS_PREC_FP32_POLISH) {
+            for (int32_t k = 0; k < n; ++k) {
+                sccs_handle *h = handles[k];
+                cudaMemcpyAsync(h->beta_dev, h->d.beta_priv, sizeof(double) * std::max<int32_t>(h->d.J, 1),
+                                cudaMemcpyDeviceToDevice, st);
+                int le = sccs::launch_init_state(h->d, h->beta_dev, threads, st, true);
+                if (le != 0) return done(cuda_fail(static_cast<cudaError_t>(le), "init_state launch"));
+            }
+            if ((rc = run_phase(false, true))) return done(rc);
+        }
+    } else if ((rc = run_phase(false, false))) {
+        return done(rc);
+    }
+    int first_err = SCCS_OK;
+    for (int32_t k = 0; k < n; ++k) {
+        sccs_handle *h = handles[k];
+        const sccs::FitOut &r = res[k];
+        if (status[k] == SCCS_OK && beta_out && beta_out[k] && h->d.J > 0) {
+            cudaError_t e = cudaMemcpy(beta_out[k], h->d.beta_priv, sizeof(double) * h->d.J, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) status[k] = SCCS_E_CUDA;
+        }
+        if (infos) {
+            sccs_fit_info &fi = infos[k];
+            const int32_t cyc = o.precision == SCCS_PREC_FP32_POLISH ? fp32_cycles[k] + r.cycles : r.cycles;
+            fi.status = status[k] != SCCS_OK ? status[k] : r.status;
+            fi.cycles = cyc;
+            fi.steps = static_cast<int64_t>(cyc) * h->d.J;
+            fi.nonzero_steps = nonzero[k];
+            fi.logpost = r.logpost;
+            fi.conv_value = r.conv;
+            fi.kernel_ms = kernel_ms;
+            fi.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+            fi.warnings = warnings[k];
+            fi.fp32_cycles = fp32_cycles[k];
+        }
+        if (status[k] != SCCS_OK && first_err == SCCS_OK) first_err = status[k];
+    }
+    if (first_err != SCCS_OK) return done(fail(first_err, "at least one fit of the batch failed (see infos[k].status)"));
+    return done(SCCS_OK);
 }
 
 int sccs_grad_hess(sccs_handle *h, int32_t j, const double *beta, double *g, double *hess) {

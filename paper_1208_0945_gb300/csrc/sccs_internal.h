@@ -54,6 +54,8 @@ struct DevLayout {
     // state
     double *E;                 // K: L x exp(Xb)
     double *D;                 // N: M[L x exp(Xb)]
+    float *E32;                // K: L x exp(Xb) in the FP32 mode
+    float2 *D32;               // N: M[L x exp(Xb)] as an FP32 (hi, lo) pair in the FP32 mode
     double *beta_priv;         // S*J: each CTA's private copy of beta (all copies agree)
     double *trust_priv;        // S*J: each CTA's private trust radii
     double *stash;             // S*stash_stride*2: (num, D) per segment of slices too big to stage
@@ -91,19 +93,36 @@ struct FitOut {
     int32_t pad;
 };
 
+// One fit of a batched launch: its layout and state, parameters and outputs.
+struct BatchEntry {
+    DevLayout d;
+    FitParams p;
+    FitOut *out;
+    double *hist;
+};
+
 // Dynamic shared memory the fit kernel needs.
 size_t fit_kernel_smem_bytes();
 
 // Launchers (return cudaError_t as int).  `stream` is a cudaStream_t.
-int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, void *stream);
+// E = L x exp(X beta0) (beta0 = nullptr: E = L), private beta copies = beta0; trust radii
+// reset to 1 unless keep_trust.
+int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, void *stream,
+                      bool keep_trust = false);
+// E32 = (float) E on every shard.
+int launch_e_to_f32(const DevLayout &d, int threads, void *stream);
 int launch_fit(const DevLayout &d, const FitParams &p, FitOut *out_dev, double *hist_dev,
-               int threads, void *stream);
+               int threads, void *stream, bool fp32 = false);
 int launch_grad_hess(const DevLayout &d, int32_t j, const FitParams &p, FitOut *out_dev,
                      int threads, void *stream);
 // The gradient kernel on only `ctas` of the S CTAs the all-reduce counts (a wait-bound test).
 int launch_grad_hess_partial(const DevLayout &d, int32_t j, const FitParams &p, FitOut *out_dev,
                              int threads, int ctas, void *stream);
 int fit_kernel_max_blocks_per_sm(int threads, int *blocks);
+// Independent fits in one cooperative launch: CTA b runs shard map[b].y of fit map[b].x
+// (entries and map in device memory; every fit's CTAs form its own all-reduce team).
+int launch_fit_batch(const BatchEntry *entries_dev, const int2 *map_dev, int ctas, int threads, void *stream,
+                     bool fp32);
 
 }  // namespace sccs
 

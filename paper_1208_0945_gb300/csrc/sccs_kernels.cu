@@ -291,7 +291,7 @@ struct SmemLayout {
 // not run two rounds ahead of a reader, because the round after next needs the reader's
 // own contribution.  The totals are exact fixed-point sums rounded once, so every CTA
 // holds the same bits.
-__device__ bool grid_allreduce2(const DevLayout &d, unsigned long long seq, double a, double b, double &A,
+__device__ bool grid_allreduce2(const DevLayout &d, int me, unsigned long long seq, double a, double b, double &A,
                                 double &B, long long timeout_ns) {
     const int lane = threadIdx.x & 31;
     const unsigned long long phase = ((seq >> 1) & 1ull) ^ 1ull;
@@ -301,7 +301,7 @@ __device__ bool grid_allreduce2(const DevLayout &d, unsigned long long seq, doub
                                        0x7fffffffffffffffull) | (phase << 63);
         const unsigned long long eb = (static_cast<unsigned long long>(__double_as_longlong(b)) &
                                        0x7fffffffffffffffull) | (phase << 63);
-        st_relaxed_v2(buf + 2 * blockIdx.x, ea, eb);
+        st_relaxed_v2(buf + 2 * me, ea, eb);
     }
     const long long deadline = now_ns() + timeout_ns;
     Fx sa = fx_zero(), sb = fx_zero();
@@ -359,12 +359,11 @@ __device__ bool grid_allreduce2(const DevLayout &d, unsigned long long seq, doub
 
 // Block reduction of two per-thread partials (exact), then the grid all-reduce by warp 0.
 // On return (all threads) sh.G, sh.H hold the grid totals; returns false on abort.
-__device__ bool block_grid_reduce(const DevLayout &d, unsigned long long seq, long long timeout_ns,
-                                  SharedState &sh, double a, double b, bool bad) {
+__device__ bool block_grid_reduce(const DevLayout &d, int me, unsigned long long seq, long long timeout_ns,
+                                  SharedState &sh, Fx fa, Fx fb, bool bad) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    Fx fa = fx_from_double(a, bad), fb = fx_from_double(b, bad);
     fa = fx_warp_sum(fa);
     fb = fx_warp_sum(fb);
     const int wbad = __any_sync(kFull, bad);
@@ -385,7 +384,7 @@ __device__ bool block_grid_reduce(const DevLayout &d, unsigned long long seq, lo
         ca = __shfl_sync(kFull, ca, 0);
         cbv = __shfl_sync(kFull, cbv, 0);
         double At = 0.0, Bt = 0.0;
-        const bool ok = grid_allreduce2(d, seq, ca, cbv, At, Bt, timeout_ns);
+        const bool ok = grid_allreduce2(d, me, seq, ca, cbv, At, Bt, timeout_ns);
         if (lane == 0) {
             sh.ok = ok;
             sh.G = At;
@@ -632,6 +631,256 @@ __device__ void phase_c_global(const DevLayout &d, int s, int j, double r, doubl
     }
 }
 
+// ------------------------------------------------------------------ FP32 column phases
+//
+// FP32 mode (spec precision variant): E in FP32, each segment's numerator a Kahan
+// (compensated) FP32 sum, D_i an FP32 (hi, lo) pair updated with an error-free two-sum, W_i and
+// its two terms in FP32; the per-subject terms then enter the same exact fixed-point sums, so
+// the cross-subject reductions stay exact.  The scalar step stays in FP64.
+
+// Exact conversion of a finite non-negative float below 2^60 (see fx_from_double).
+__device__ __forceinline__ Fx fx_from_float(float v, bool &bad) {
+    const unsigned b = __float_as_uint(v);
+    const int e = static_cast<int>((b >> 23) & 0xff);
+    Fx r = fx_zero();
+    if ((b >> 31) && b != 0x80000000u) {
+        bad = true;
+        return r;
+    }
+    if (e == 0) return r;
+    if (e >= 127 + 60) {
+        bad = true;
+        return r;
+    }
+    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
+    const int sh = e - 150 + kFrac;              // v = m * 2^(e - 150)
+    if (sh < 0) {
+        if (sh > -64) r.w0 = m >> (-sh);
+        return r;
+    }
+    const int q = sh >> 6, rm = sh & 63;
+    const unsigned long long lo = m << rm;
+    const unsigned long long hi = rm ? (m >> (64 - rm)) : 0ull;
+    if (q == 0) {
+        r.w0 = lo;
+        r.w1 = hi;
+    } else if (q == 1) {
+        r.w1 = lo;
+        r.w2 = hi;
+    } else {
+        r.w2 = lo;
+    }
+    return r;
+}
+
+// Compensated (Kahan) accumulation of one FP32 term.
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// (hi, lo) + x with an error-free two-sum, renormalised.
+__device__ __forceinline__ float2 pair_add(float2 d, float x) {
+    const float s = d.x + x;
+    const float bp = s - d.x;
+    const float err = (d.x - (s - bp)) + (x - bp);
+    const float lo = d.y + err;
+    const float hi = s + lo;
+    return make_float2(hi, lo - (hi - s));
+}
+
+__device__ __forceinline__ void segment_terms32(float num, float Dhi, int nv, Fx &ga, Fx &ha, bool &bad) {
+    const unsigned bd = __float_as_uint(Dhi), bn = __float_as_uint(num);
+    if (bd == 0u || bd >= 0x7f800000u || bn >= 0x7f800000u) bad = true;
+    float w = num / Dhi;
+    if (__float_as_uint(w) > 0x3f800000u) w = 1.0f;
+    const float gl = static_cast<float>(nv) * w;
+    const float hl = gl * (1.0f - w);
+    ga = fx_add(ga, fx_from_float(gl, bad));
+    ha = fx_add(ha, fx_from_float(hl, bad));
+}
+
+__device__ void phase_a_staged32(const DevLayout &d, const ColDesc &cd, const StageBuf &sb, SmemLayout &sm,
+                                 Fx &ga, Fx &ha, bool &bad) {
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int2 *sseg = sb.segs + cd.seg_off;
+    const int32_t *srow = sb.rows + cd.row_off;
+    const long long *sgrp = sb.grp + cd.grp_off;
+    float *est = reinterpret_cast<float *>(sm.est);
+    float4 *stash = reinterpret_cast<float4 *>(sm.seg_stash);
+    for (int g = warp; g < cd.ngrp; g += nwarps) {
+        const int si = 32 * g + lane;
+        const bool valid = si < cd.nseg;
+        const int2 sg = valid ? sseg[si] : make_int2(0, 0);
+        const float2 Dv = valid ? d.D32[sg.x] : make_float2(1.0f, 0.0f);
+        const int nv = valid ? d.nev[sg.x] : 0;
+        int base = static_cast<int>(sgrp[g] - cd.row0);
+        const int maxlen = __shfl_sync(kFull, sg.y, 0);
+        float sum = 0.0f, comp = 0.0f;
+        for (int t0 = 0; t0 < maxlen; t0 += kBatch) {
+            int pos[kBatch];
+            int32_t k[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const bool act = sg.y > t0 + u;
+                const unsigned m = __ballot_sync(kFull, act);
+                pos[u] = act ? base + lane : -1;
+                k[u] = act ? srow[base + lane] : -1;
+                base += __popc(m);
+            }
+            float e[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? d.E32[k[u]] : 0.0f;
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                if (k[u] >= 0) {
+                    kahan_add(sum, comp, e[u]);
+                    est[pos[u]] = e[u];
+                }
+            }
+        }
+        if (valid) {
+            const float num = sum - comp;
+            segment_terms32(num, Dv.x, nv, ga, ha, bad);
+            stash[si] = make_float4(num, Dv.x, Dv.y, 0.0f);
+        }
+    }
+}
+
+__device__ void phase_a_global32(const DevLayout &d, int s, int j, Fx &ga, Fx &ha, bool &bad) {
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const long long so = static_cast<long long>(s) * (d.J + 1) + j;
+    const long long seg0 = d.slice_seg[so], seg1 = d.slice_seg[so + 1];
+    const long long grp0 = d.slice_grp[so];
+    const int ngrp = static_cast<int>(d.slice_grp[so + 1] - grp0);
+    float4 *stash = reinterpret_cast<float4 *>(d.stash + 2 * static_cast<long long>(s) * d.stash_stride);
+    int2 sg_next = make_int2(0, 0);
+    long long base_next = 0;
+    if (warp < ngrp) {
+        const long long si = seg0 + 32 * static_cast<long long>(warp) + lane;
+        sg_next = si < seg1 ? d.segs[si] : make_int2(0, 0);
+        base_next = d.grp_base[grp0 + warp];
+    }
+    for (int g = warp; g < ngrp; g += nwarps) {
+        const long long si = seg0 + 32 * static_cast<long long>(g) + lane;
+        const bool valid = si < seg1;
+        const int2 sg = sg_next;
+        long long base = base_next;
+        const int gn = g + nwarps;
+        if (gn < ngrp) {
+            const long long sn = seg0 + 32 * static_cast<long long>(gn) + lane;
+            sg_next = sn < seg1 ? d.segs[sn] : make_int2(0, 0);
+            base_next = d.grp_base[grp0 + gn];
+        }
+        const float2 Dv = valid ? d.D32[sg.x] : make_float2(1.0f, 0.0f);
+        const int nv = valid ? d.nev[sg.x] : 0;
+        const int maxlen = __shfl_sync(kFull, sg.y, 0);
+        float sum = 0.0f, comp = 0.0f;
+        for (int t0 = 0; t0 < maxlen; t0 += kBatch) {
+            int32_t k[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const bool act = sg.y > t0 + u;
+                const unsigned m = __ballot_sync(kFull, act);
+                k[u] = act ? d.rows[base + lane] : -1;
+                base += __popc(m);
+            }
+            float e[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? d.E32[k[u]] : 0.0f;
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (k[u] >= 0) kahan_add(sum, comp, e[u]);
+        }
+        if (valid) {
+            const float num = sum - comp;
+            segment_terms32(num, Dv.x, nv, ga, ha, bad);
+            stash[si - seg0] = make_float4(num, Dv.x, Dv.y, 0.0f);
+        }
+    }
+}
+
+__device__ void phase_c_staged32(const DevLayout &d, const ColDesc &cd, const StageBuf &sb, const SmemLayout &sm,
+                                 float r, float em1) {
+    const int2 *sseg = sb.segs + cd.seg_off;
+    const int32_t *srow = sb.rows + cd.row_off;
+    const float *est = reinterpret_cast<const float *>(sm.est);
+    const float4 *stash = reinterpret_cast<const float4 *>(sm.seg_stash);
+    for (int p = threadIdx.x; p < cd.nnz; p += blockDim.x) d.E32[srow[p]] = est[p] * r;
+    for (int si = threadIdx.x; si < cd.nseg; si += blockDim.x) {
+        const float4 st = stash[si];
+        d.D32[sseg[si].x] = pair_add(make_float2(st.y, st.z), em1 * st.x);
+    }
+}
+
+__device__ void phase_c_global32(const DevLayout &d, int s, int j, float r, float em1) {
+    const long long so = static_cast<long long>(s) * (d.J + 1) + j;
+    const long long row0 = d.slice_row[so], row1 = d.slice_row[so + 1];
+    const long long seg0 = d.slice_seg[so], seg1 = d.slice_seg[so + 1];
+    const float4 *stash = reinterpret_cast<const float4 *>(d.stash + 2 * static_cast<long long>(s) * d.stash_stride);
+    const long long T = blockDim.x;
+    long long p = row0 + threadIdx.x;
+    for (; p + 3 * T < row1; p += 4 * T) {
+        int32_t k[4];
+        float e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k[u] = d.rows[p + u * T];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = d.E32[k[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d.E32[k[u]] = e[u] * r;
+    }
+    for (; p < row1; p += T) {
+        const int32_t k = d.rows[p];
+        d.E32[k] *= r;
+    }
+    for (long long si = seg0 + threadIdx.x; si < seg1; si += T) {
+        const float4 st = stash[si - seg0];
+        d.D32[d.segs[si].x] = pair_add(make_float2(st.y, st.z), em1 * st.x);
+    }
+}
+
+__device__ void prefetch_staged_state32(const DevLayout &d, const ColDesc &nd, const StageBuf &sb, uint64_t *bar,
+                                        uint32_t parity) {
+    if (!mbar_wait(bar, parity, 20000)) return;
+    const int t = threadIdx.x - 32, T = blockDim.x - 32;
+    const int32_t *srow = sb.rows + nd.row_off;
+    const int2 *sseg = sb.segs + nd.seg_off;
+    for (int p = t; p < nd.nnz; p += T) prefetch_l1(d.E32 + srow[p]);
+    for (int si = t; si < nd.nseg; si += T) {
+        const int i = sseg[si].x;
+        prefetch_l1(d.D32 + i);
+        prefetch_l1(d.nev + i);
+    }
+}
+
+// D_i from E in FP32 with compensation, and the exact sums of the positive and negative parts
+// of n_i log D_i (FP32 log: the FP32 phase only needs the log-posterior to stop on).
+__device__ bool refresh_and_reduce32(const DevLayout &d, int s, unsigned long long seq, long long timeout_ns,
+                                     SharedState &sh) {
+    const long long p0 = d.shard_pat[s], p1 = d.shard_pat[s + 1];
+    Fx fp = fx_zero(), fn = fx_zero();
+    bool bad = false;
+    for (long long i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+        float sum = 0.0f, comp = 0.0f;
+        for (long long k = d.pat_ptr[i]; k < d.pat_ptr[i + 1]; ++k) kahan_add(sum, comp, d.E32[k]);
+        const float hi = sum - comp;
+        const float lo = -comp - (hi - sum);
+        d.D32[i] = make_float2(hi, lo);
+        const float t = static_cast<float>(d.nev[i]) * logf(hi);
+        if (t >= 0.0f) fp = fx_add(fp, fx_from_float(t, bad));
+        else if (t < 0.0f) fn = fx_add(fn, fx_from_float(-t, bad));
+        else bad = true;
+    }
+    return block_grid_reduce(d, s, seq, timeout_ns, sh, fp, fn, bad);
+}
+
 // ------------------------------------------------------------------ staging
 
 struct SliceBounds {
@@ -711,9 +960,8 @@ __device__ void prefetch_staged_state(const DevLayout &d, const ColDesc &nd, con
 
 // Recompute D_i = sum_{k in i} E_k on this CTA's subjects and all-reduce the positive and
 // negative parts of sum_i n_i log D_i (into sh.G, sh.H).
-__device__ bool refresh_and_reduce(const DevLayout &d, unsigned long long seq, long long timeout_ns,
+__device__ bool refresh_and_reduce(const DevLayout &d, int s, unsigned long long seq, long long timeout_ns,
                                    SharedState &sh) {
-    const int s = blockIdx.x;
     const long long p0 = d.shard_pat[s], p1 = d.shard_pat[s + 1];
     double pos = 0.0, neg = 0.0;
     bool bad = false;
@@ -735,12 +983,13 @@ __device__ bool refresh_and_reduce(const DevLayout &d, unsigned long long seq, l
         else if (t < 0.0) neg -= t;
         else bad = true;  // NaN
     }
-    return block_grid_reduce(d, seq, timeout_ns, sh, pos, neg, bad);
+    const Fx fp = fx_from_double(pos, bad), fn = fx_from_double(neg, bad);
+    return block_grid_reduce(d, s, seq, timeout_ns, sh, fp, fn, bad);
 }
 
 // sum_j b_j Y'X_j (= Y'Xb) and the prior term, from this CTA's private beta, in j order.
-__device__ void beta_terms(const DevLayout &d, const FitParams &p, double &lin, double &logprior) {
-    const double *beta = d.beta_priv + static_cast<long long>(blockIdx.x) * d.J;
+__device__ void beta_terms(const DevLayout &d, int s, const FitParams &p, double &lin, double &logprior) {
+    const double *beta = d.beta_priv + static_cast<long long>(s) * d.J;
     double l = 0.0, sq = 0.0, ab = 0.0;
     for (int j = 0; j < d.J; ++j) {
         const double b = beta[j];
@@ -775,11 +1024,11 @@ __device__ __forceinline__ void bookkeep(double *beta, double *trust, int j, dou
 
 // ------------------------------------------------------------------ kernels
 
-__global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, FitOut *out, double *hist) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    SmemLayout &sm = *reinterpret_cast<SmemLayout *>(smem_raw);
-    __shared__ SharedState sh;
-    const int s = blockIdx.x;
+// One fit (Algorithm 1) on the CTA that owns shard `s` of `d` (d.S CTAs take part).  F32
+// selects the FP32 mode; the scalar step is FP64 in both.
+template <bool F32>
+__device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, double *hist, int s, SmemLayout &sm,
+                        SharedState &sh) {
     const bool leader = (s == 0) && (threadIdx.x == 0);
     const long long timeout = p.timeout_ns;
     unsigned long long seq = p.seq0;
@@ -814,10 +1063,11 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
     __syncthreads();
 
     // P at the start point.
-    if (!refresh_and_reduce(d, seq++, timeout, sh)) goto aborted;
+    if (!(F32 ? refresh_and_reduce32(d, s, seq++, timeout, sh) : refresh_and_reduce(d, s, seq++, timeout, sh)))
+        goto aborted;
     {
         double lin = 0.0, lp = 0.0;
-        if (threadIdx.x == 0) beta_terms(d, p, lin, lp);
+        if (threadIdx.x == 0) beta_terms(d, s, p, lin, lp);
         loglik = lin - (sh.G - sh.H);
         P_prev = loglik + lp;
         P = P_prev;
@@ -866,23 +1116,26 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
                         pend_j = -1;
                     }
                 }
-                double G = 0.0, H = 0.0;
+                Fx ga = fx_zero(), ha = fx_zero();
                 bool bad = false;
-                if (cd.staged) {
-                    if (staged_ok) {
-                        phase_a_staged(d, cd, sm.stage[buf], sm, G, H, bad);
-                    } else {                           // never read a stage that did not arrive
-                        bad = true;
-                        if (threadIdx.x == 0) atomicExch(d.abort_flag, 1);
-                    }
+                if (cd.staged && !staged_ok) {          // never read a stage that did not arrive
+                    bad = true;
+                    if (threadIdx.x == 0) atomicExch(d.abort_flag, 1);
+                } else if (F32) {
+                    if (cd.staged) phase_a_staged32(d, cd, sm.stage[buf], sm, ga, ha, bad);
+                    else phase_a_global32(d, s, j, ga, ha, bad);
                 } else {
-                    phase_a_global(d, s, j, G, H, bad);
+                    double G = 0.0, H = 0.0;
+                    if (cd.staged) phase_a_staged(d, cd, sm.stage[buf], sm, G, H, bad);
+                    else phase_a_global(d, s, j, G, H, bad);
+                    ga = fx_from_double(G, bad);
+                    ha = fx_from_double(H, bad);
                 }
                 // A slice of at most one group lives in warp 0 alone: its warp sum is the CTA's.
                 const bool one_warp = cd.staged && cd.ngrp <= 1;
                 if (!one_warp) {
-                    const Fx fa = fx_warp_sum(fx_from_double(G, bad));
-                    const Fx fb = fx_warp_sum(fx_from_double(H, bad));
+                    const Fx fa = fx_warp_sum(ga);
+                    const Fx fb = fx_warp_sum(ha);
                     const int wbad = __any_sync(kFull, bad);
                     if (lane == 0) {
                         sh.wa[warp] = fa;
@@ -895,8 +1148,8 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
                     Fx ta, tbx;
                     bool cbad;
                     if (one_warp) {
-                        ta = fx_warp_sum(fx_from_double(G, bad));
-                        tbx = fx_warp_sum(fx_from_double(H, bad));
+                        ta = fx_warp_sum(ga);
+                        tbx = fx_warp_sum(ha);
                         cbad = __any_sync(kFull, bad);
                     } else {
                         ta = lane < nwarps ? sh.wa[lane] : fx_zero();
@@ -911,7 +1164,7 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
                     cb = __shfl_sync(kFull, cb, 0);
                     // grid all-reduce, then the step in lane 0 (no extra barrier)
                     double At = 0.0, Bt = 0.0;
-                    const bool ok = grid_allreduce2(d, seq, ca, cb, At, Bt, timeout);
+                    const bool ok = grid_allreduce2(d, s, seq, ca, cb, At, Bt, timeout);
                     if (lane == 0) {
                         double db = 0.0, r = 1.0, em1 = 0.0;
                         if (ok) {
@@ -935,16 +1188,28 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
                     // warps 1..: desc[buf ^ 1] (written by thread tb) is visible after this barrier
                     if (one_warp) named_barrier_all_but_warp0();
                     const ColDesc &nd = sh.desc[buf ^ 1];
-                    if (nd.staged)
-                        prefetch_staged_state(d, nd, sm.stage[buf ^ 1], &sh.bar[buf ^ 1], (phase_bits >> (buf ^ 1)) & 1u);
+                    if (nd.staged) {
+                        if (F32)
+                            prefetch_staged_state32(d, nd, sm.stage[buf ^ 1], &sh.bar[buf ^ 1],
+                                                    (phase_bits >> (buf ^ 1)) & 1u);
+                        else
+                            prefetch_staged_state(d, nd, sm.stage[buf ^ 1], &sh.bar[buf ^ 1],
+                                                  (phase_bits >> (buf ^ 1)) & 1u);
+                    }
                 }
                 ++seq;
                 __syncthreads();
                 if (!sh.ok) goto aborted;
                 const double db = sh.db;
                 if (db != 0.0) {
-                    if (cd.staged) phase_c_staged(d, cd, sm.stage[buf], sm, sh.r, sh.em1);
-                    else phase_c_global(d, s, j, sh.r, sh.em1);
+                    if (F32) {
+                        const float r32 = static_cast<float>(sh.r), em32 = static_cast<float>(sh.em1);
+                        if (cd.staged) phase_c_staged32(d, cd, sm.stage[buf], sm, r32, em32);
+                        else phase_c_global32(d, s, j, r32, em32);
+                    } else {
+                        if (cd.staged) phase_c_staged(d, cd, sm.stage[buf], sm, sh.r, sh.em1);
+                        else phase_c_global(d, s, j, sh.r, sh.em1);
+                    }
                 }
                 if (threadIdx.x == tb) {
                     pend_j = j;
@@ -966,7 +1231,8 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
                 sh.nonzero = nonzero_tb;
             }
             __syncthreads();
-            if (!refresh_and_reduce(d, seq++, timeout, sh)) goto aborted;
+            if (!(F32 ? refresh_and_reduce32(d, s, seq++, timeout, sh) : refresh_and_reduce(d, s, seq++, timeout, sh)))
+                goto aborted;
             if (threadIdx.x == 0) {
                 const double lp = p.prior == 1 ? -0.5 * sh.sq * p.inv_var : (p.prior == 2 ? -p.lambda * sh.ab : 0.0);
                 loglik = sh.lin - (sh.G - sh.H);
@@ -1006,16 +1272,41 @@ aborted:
     }
 }
 
+
+template <bool F32>
+__global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, FitOut *out, double *hist) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ SharedState sh;
+    run_fit<F32>(d, p, out, hist, blockIdx.x, *reinterpret_cast<SmemLayout *>(smem_raw), sh);
+}
+
+// Several independent fits in one launch.  A fit's CTAs exchange partial sums only with each
+// other (its own all-reduce slots), so teams never wait on one another, and every fit computes
+// exactly what it computes when launched alone with the same number of shards.
+template <bool F32>
+__global__ void __launch_bounds__(512, 1) fit_batch_kernel(const BatchEntry *entries, const int2 *map) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ SharedState sh;
+    __shared__ __align__(16) BatchEntry e;
+    const int2 m = map[blockIdx.x];
+    const int *src = reinterpret_cast<const int *>(entries + m.x);
+    int *dst = reinterpret_cast<int *>(&e);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(BatchEntry) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    run_fit<F32>(e.d, e.p, e.out, e.hist, m.y, *reinterpret_cast<SmemLayout *>(smem_raw), sh);
+}
+
 __global__ void __launch_bounds__(512, 1) grad_hess_kernel(DevLayout d, int j, FitParams p, FitOut *out) {
     __shared__ SharedState sh;
     const long long timeout = p.timeout_ns;
     unsigned long long seq = p.seq0;
-    if (!refresh_and_reduce(d, seq++, timeout, sh)) goto aborted;
+    if (!refresh_and_reduce(d, blockIdx.x, seq++, timeout, sh)) goto aborted;
     {
         double G = 0.0, H = 0.0;
         bool bad = false;
         phase_a_global(d, blockIdx.x, j, G, H, bad);
-        if (!block_grid_reduce(d, seq++, timeout, sh, G, H, bad)) goto aborted;
+        const Fx fg = fx_from_double(G, bad), fh = fx_from_double(H, bad);
+        if (!block_grid_reduce(d, blockIdx.x, seq++, timeout, sh, fg, fh, bad)) goto aborted;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             out->g = d.ytx[j] - sh.G;
             out->h = -sh.H;
@@ -1033,14 +1324,14 @@ aborted:
 
 // E_k = l_k exp(Xb_k) on this CTA's rows, with Xb accumulated column by column in j order;
 // private beta copies and trust radii (= 1) are (re)set.
-__global__ void __launch_bounds__(512, 1) init_state_kernel(DevLayout d, const double *beta0) {
+__global__ void __launch_bounds__(512, 1) init_state_kernel(DevLayout d, const double *beta0, int keep_trust) {
     const int s = blockIdx.x;
     const long long r0 = d.shard_row[s], r1 = d.shard_row[s + 1];
     double *beta = d.beta_priv + static_cast<long long>(s) * d.J;
     double *trust = d.trust_priv + static_cast<long long>(s) * d.J;
     for (int j = threadIdx.x; j < d.J; j += blockDim.x) {
         beta[j] = beta0 ? beta0[j] : 0.0;
-        trust[j] = 1.0;
+        if (!keep_trust) trust[j] = 1.0;
     }
     if (!beta0) {
         for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k];
@@ -1059,9 +1350,20 @@ __global__ void __launch_bounds__(512, 1) init_state_kernel(DevLayout d, const d
     for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k] * exp(d.E[k]);
 }
 
+__global__ void __launch_bounds__(512, 1) e_to_f32_kernel(DevLayout d) {
+    const int s = blockIdx.x;
+    for (long long k = d.shard_row[s] + threadIdx.x; k < d.shard_row[s + 1]; k += blockDim.x)
+        d.E32[k] = static_cast<float>(d.E[k]);
+}
+
 int ensure_smem_attr() {
-    const cudaError_t e = cudaFuncSetAttribute(fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(sizeof(SmemLayout)));
+    const int bytes = static_cast<int>(sizeof(SmemLayout));
+    cudaError_t e = cudaFuncSetAttribute(fit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fit_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fit_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return static_cast<int>(e);
 }
 
@@ -1069,20 +1371,37 @@ int ensure_smem_attr() {
 
 size_t fit_kernel_smem_bytes() { return sizeof(SmemLayout); }
 
-int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, void *stream) {
-    init_state_kernel<<<d.S, threads, 0, static_cast<cudaStream_t>(stream)>>>(d, beta0_dev);
+int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, void *stream, bool keep_trust) {
+    init_state_kernel<<<d.S, threads, 0, static_cast<cudaStream_t>(stream)>>>(d, beta0_dev, keep_trust ? 1 : 0);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_e_to_f32(const DevLayout &d, int threads, void *stream) {
+    e_to_f32_kernel<<<d.S, threads, 0, static_cast<cudaStream_t>(stream)>>>(d);
     return static_cast<int>(cudaGetLastError());
 }
 
 int launch_fit(const DevLayout &d, const FitParams &p, FitOut *out_dev, double *hist_dev, int threads,
-               void *stream) {
+               void *stream, bool fp32) {
     int e = ensure_smem_attr();
     if (e) return e;
     DevLayout dd = d;
     FitParams pp = p;
     void *args[] = {&dd, &pp, &out_dev, &hist_dev};
-    return static_cast<int>(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(fit_kernel), dim3(d.S),
-                                                         dim3(threads), args, sizeof(SmemLayout),
+    void *fn = fp32 ? reinterpret_cast<void *>(fit_kernel<true>) : reinterpret_cast<void *>(fit_kernel<false>);
+    return static_cast<int>(cudaLaunchCooperativeKernel(fn, dim3(d.S), dim3(threads), args, sizeof(SmemLayout),
+                                                         static_cast<cudaStream_t>(stream)));
+}
+
+int launch_fit_batch(const BatchEntry *entries_dev, const int2 *map_dev, int ctas, int threads, void *stream,
+                     bool fp32) {
+    int e = ensure_smem_attr();
+    if (e) return e;
+    const BatchEntry *en = entries_dev;
+    const int2 *mp = map_dev;
+    void *args[] = {&en, &mp};
+    void *fn = fp32 ? reinterpret_cast<void *>(fit_batch_kernel<true>) : reinterpret_cast<void *>(fit_batch_kernel<false>);
+    return static_cast<int>(cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(threads), args, sizeof(SmemLayout),
                                                          static_cast<cudaStream_t>(stream)));
 }
 
@@ -1106,8 +1425,12 @@ int fit_kernel_max_blocks_per_sm(int threads, int *blocks) {
     int e = ensure_smem_attr();
     if (e) return e;
     int a = 0, b = 0;
-    cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fit_kernel, threads, sizeof(SmemLayout));
+    cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fit_kernel<false>, threads, sizeof(SmemLayout));
     if (ce != cudaSuccess) return static_cast<int>(ce);
+    int c = 0;
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, fit_batch_kernel<false>, threads, sizeof(SmemLayout));
+    if (ce != cudaSuccess) return static_cast<int>(ce);
+    if (c < a) a = c;
     ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grad_hess_kernel, threads, 0);
     if (ce != cudaSuccess) return static_cast<int>(ce);
     *blocks = a < b ? a : b;

@@ -19,7 +19,7 @@ E_INVAL, E_UNSORTED, E_NONBINARY, E_NOMEM, E_CUDA = -1, -2, -3, -4, -5
 E_TIMEOUT, E_NUMERIC, E_BUSY, E_DUPLICATE, E_UNSUPPORTED = -6, -7, -8, -9, -10
 PRIOR = {"none": 0, "normal": 1, "laplace": 2}
 TOL = {"abs_logpost": 0, "rel_logpost": 1, "genkin_xbeta": 2}
-PREC = {"fp64": 0}
+PREC = {"fp64": 0, "fp32_polish": 1, "fp32": 2}
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
@@ -55,7 +55,7 @@ class sccs_fit_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("cycles", ctypes.c_int32), ("steps", ctypes.c_int64),
                 ("nonzero_steps", ctypes.c_int64), ("logpost", ctypes.c_double), ("conv_value", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("warnings", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("fp32_cycles", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -70,6 +70,8 @@ _SIGS = {
     "sccs_set_prior": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double]),
     "sccs_fit": (ctypes.c_int, [_P, ctypes.POINTER(sccs_fit_opts), _dp, ctypes.POINTER(sccs_fit_info)]),
     "sccs_grad_hess": (ctypes.c_int, [_P, ctypes.c_int32, _dp, _dp, _dp]),
+    "sccs_fit_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(sccs_fit_opts),
+                                      ctypes.POINTER(_dp), ctypes.POINTER(sccs_fit_info)]),
     "sccs_logpost": (ctypes.c_int, [_P, _dp, _dp, _dp]),
     "sccs_get_beta": (ctypes.c_int, [_P, _dp]),
     "sccs_check_wait_timeout": (ctypes.c_int, [_P, ctypes.c_double]),
@@ -165,6 +167,27 @@ def sccs_fit(handle, J: int, *, beta0=None, warm_start=False, tol_mode="rel_logp
     out["beta"] = beta[:J]
     if history:
         out["history"] = hist[:info.cycles + 1]
+    return out
+
+
+def sccs_fit_batch(handles, Js, *, warm_start=False, tol_mode="rel_logpost", tol=1e-12, max_cycles=1000,
+                   precision="fp64") -> list:
+    """One persistent launch for several fits (one per handle); returns one result dict per fit."""
+    n = len(handles)
+    o = sccs_fit_opts(struct_size=ctypes.sizeof(sccs_fit_opts), warm_start=int(bool(warm_start)), beta0=None,
+                      tol_mode=TOL[tol_mode], max_cycles=int(max_cycles), tol=float(tol), precision=PREC[precision],
+                      logpost_history=None)
+    hs = (_P * n)(*handles)
+    betas = [np.zeros(max(J, 1)) for J in Js]
+    bptr = (_dp * n)(*[b.ctypes.data_as(_dp) for b in betas])
+    infos = (sccs_fit_info * n)()
+    rc = _lib.sccs_fit_batch(hs, n, ctypes.byref(o), bptr, infos)
+    out = []
+    for k in range(n):
+        d = {name: getattr(infos[k], name) for name, _ in sccs_fit_info._fields_}
+        d["beta"] = betas[k][:Js[k]]
+        out.append(d)
+    _check(rc, "sccs_fit_batch")
     return out
 
 

@@ -10,5 +10,6 @@ from .sccs_synth import (  # noqa: F401
     tiny_fit_config,
     mid_fit_config,
     paper_scale_config,
+    batched_fit_configs,
     CONFIGS,
 )

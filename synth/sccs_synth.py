@@ -162,6 +162,9 @@ def make_dataset(*, n_patients: int, eras: tuple, J: int, columns: tuple,
     ckind = columns[0]
     if ckind == "density":
         probs = np.full(J, float(columns[1]))
+    elif ckind == "densities":                      # one density per column (shared across datasets)
+        probs = np.asarray(columns[1], dtype=np.float64)
+        assert probs.shape == (J,)
     elif ckind == "density_range":
         probs = rng.uniform(float(columns[1]), float(columns[2]), size=J)
     elif ckind == "zipf":
@@ -234,6 +237,25 @@ def paper_scale_config(seed: int = 1210, scale: float = 1.0) -> tuple[SCCSData, 
                      name=f"paper-scale-{n}-subjects-5000-drugs-zipf1.1")
     fit = dict(prior="laplace", variance=0.05, tol_mode="rel_logpost", tol=1e-12, max_cycles=1000)
     return d, fit
+
+
+def batched_fit_configs(n_fits: int = 64, min_subjects: int = 2000, max_subjects: int = 100_000,
+                        J: int = 500, seed: int = 1211) -> list:
+    """Independent fits for a batched launch: subjects per fit log-uniform in
+    [min_subjects, max_subjects], eras geometric with mean 8, J binary drugs whose densities
+    (uniform 0.5-5%) are shared by all fits while the rows are drawn per fit, 3 true effects
+    per fit, Normal prior variance 0.01 / 0.1 / 1 in turn."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(min_subjects), np.log(max_subjects), size=n_fits)).astype(int)
+    dens = rng.uniform(0.005, 0.05, size=J)
+    out = []
+    for f in range(n_fits):
+        d = make_dataset(n_patients=int(sizes[f]), eras=("geometric", 8), J=J, columns=("densities", dens),
+                         n_true=3, beta_sd=0.5, seed=seed * 1000 + f, name=f"batched-fit-{f}")
+        fit = dict(prior="normal", variance=(0.01, 0.1, 1.0)[f % 3], tol_mode="rel_logpost", tol=1e-12,
+                   max_cycles=1000)
+        out.append((d, fit))
+    return out
 
 
 CONFIGS = {

@@ -302,3 +302,65 @@ def test_bounded_wait_times_out_and_handle_recovers(P):
         m.set_prior("normal", 1.0)
         r = m.fit(tol=-1.0, max_cycles=2)
     np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11)
+
+
+# ------------------------------------------------------------------ FP32 mode and FP64 polish
+
+def _converged_oracle(d, prior, var, cycles=60):
+    """The MAP to machine precision: a fixed, large number of cycles (a stop on |dP| resolves
+    beta only to about sqrt(dP / curvature))."""
+    return oracle.Problem.from_data(d).fit(prior=prior, variance=var, fixed_cycles=cycles)
+
+
+@pytest.mark.parametrize("prior,var", [("normal", 0.1), ("laplace", 0.05)])
+def test_fp32_phase_error_against_fp64_oracle(P, prior, var):
+    """FP32 E, compensated per-subject sums and exact cross-subject sums: the FP32 fit lands
+    within FP32 resolution of the FP64 MAP (the error is stated, and bounded here)."""
+    d, _ = mid_fit_config(scale=0.02)
+    ref = _converged_oracle(d, prior, var)
+    with gpu_model(P, d) as m:
+        m.set_prior(prior, var)
+        r32 = m.fit(precision="fp32", tol_mode="rel_logpost", tol=1e-7, max_cycles=200)
+    err = float(np.abs(r32["beta"] - ref["beta"]).max())
+    print(f"FP32-only max |beta - beta_oracle| = {err:.3e} ({prior}, {r32['cycles']} cycles)")
+    assert r32["fp32_cycles"] == r32["cycles"] > 0
+    assert err <= 2e-4
+
+
+@pytest.mark.parametrize("prior,var", [("normal", 0.1), ("laplace", 0.05)])
+def test_fp32_polish_meets_fp64_bar(P, prior, var):
+    """FP32 phase to a relative change of 1e-6, then FP64 cycles to convergence: the result
+    meets the FP64 bar against the oracle's MAP (beta <= 1e-8, P <= 1e-10)."""
+    d, _ = mid_fit_config(scale=0.02)
+    ref = _converged_oracle(d, prior, var)
+    with gpu_model(P, d) as m:
+        m.set_prior(prior, var)
+        r = m.fit(precision="fp32_polish", tol=-1.0, max_cycles=40)
+    err = float(np.abs(r["beta"] - ref["beta"]).max())
+    print(f"FP32+polish max |beta - beta_oracle| = {err:.3e} ({prior}, {r['fp32_cycles']} FP32 + "
+          f"{r['cycles'] - r['fp32_cycles']} FP64 cycles)")
+    assert r["fp32_cycles"] > 0 and r["cycles"] > r["fp32_cycles"]
+    assert err <= 1e-8
+    assert rel(r["logpost"], ref["logpost"]) <= 1e-10
+    if prior == "laplace":
+        assert np.array_equal(r["beta"] == 0, ref["beta"] == 0)
+
+
+def test_fp32_grad_path_and_tiny_config(P):
+    """The tiny workload in FP32+polish (every slice staged) and a config with slices too big to
+    stage (3 shards), against the oracle's converged fit."""
+    d, fit = tiny_fit_config()
+    ref = _converged_oracle(d, "normal", 1.0)
+    with gpu_model(P, d) as m:
+        m.set_prior("normal", 1.0)
+        r = m.fit(precision="fp32_polish", tol=-1.0, max_cycles=40)
+    assert float(np.abs(r["beta"] - ref["beta"]).max()) <= 1e-8
+    d2 = make_dataset(n_patients=60000, eras=("geometric", 8), J=10, columns=("density_range", 0.01, 0.2),
+                      n_true=4, beta_sd=0.5, seed=31)
+    ref2 = _converged_oracle(d2, "normal", 0.3)
+    with gpu_model(P, d2, num_shards=3) as m:
+        m.set_prior("normal", 0.3)
+        r2 = m.fit(precision="fp32_polish", tol=-1.0, max_cycles=40)
+        r32 = m.fit(precision="fp32", tol_mode="rel_logpost", tol=1e-7, max_cycles=200)
+    assert float(np.abs(r2["beta"] - ref2["beta"]).max()) <= 1e-8
+    assert float(np.abs(r32["beta"] - ref2["beta"]).max()) <= 2e-4
