@@ -213,6 +213,71 @@ int sccs_logpost(sccs_handle *h, const double *beta, double *logpost, double *lo
 /* Copy the handle's current beta (host [J]). */
 int sccs_get_beta(const sccs_handle *h, double *beta_out);
 
+/* ---- serving: continuous batching of fit requests (cross-validation / prior grids) ---- */
+
+typedef struct sccs_server sccs_server;
+
+typedef struct sccs_server_opts {
+    int32_t struct_size;       /* sizeof(sccs_server_opts) */
+    int32_t device;            /* CUDA device ordinal (datasets must live there) */
+    int32_t max_inflight;      /* fits on the device at once; 0 is invalid; default 64 */
+    int32_t queue_capacity;    /* queued requests before sccs_submit returns SCCS_E_BUSY; default 4096 */
+    int64_t hbm_budget_bytes;  /* device memory for per-fit state (datasets not counted); 0 = no limit */
+} sccs_server_opts;
+
+typedef struct sccs_request {
+    int32_t struct_size;       /* sizeof(sccs_request) */
+    int32_t prior_type;        /* SCCS_PRIOR_* */
+    sccs_handle *dataset;      /* from sccs_create; must outlive the request */
+    double variance;           /* prior variance (Eq. 3) */
+    int32_t tol_mode;          /* SCCS_TOL_ABS_LOGPOST or SCCS_TOL_REL_LOGPOST */
+    int32_t max_cycles;
+    double tol;
+    int32_t precision;         /* SCCS_PREC_* */
+    int32_t reserved;
+    const double *beta0;       /* host [J] start point (copied at submit) or NULL for 0 */
+} sccs_request;
+
+typedef struct sccs_result {
+    int32_t status;            /* SCCS_OK, SCCS_NOT_CONVERGED or the fit's error */
+    int32_t cycles;
+    int32_t fp32_cycles;
+    int32_t reserved;
+    double logpost;
+    double queue_ms;           /* submit -> start on the device */
+    double latency_ms;         /* submit -> result ready */
+    double *beta;              /* caller's host buffer [J] to receive beta, or NULL */
+} sccs_result;
+
+typedef struct sccs_server_stats {
+    int64_t pending, running, completed;
+    int64_t slot_bytes;        /* device memory held for per-fit state */
+    int32_t ctas_in_use, capacity_ctas;
+} sccs_server_stats;
+
+/*
+ * sccs_server_create -- start a fit server on one device.  A scheduler thread admits queued
+ * requests in arrival order as soon as their per-fit device state fits the HBM budget and their
+ * dataset's CTA team fits next to the fits already running; each admitted fit runs (Algorithm 1,
+ * as sccs_fit) on a stream of its own, so fits that arrive while others run overlap with them.
+ * A fit gives the same result alone or in the mix.  Errors: SCCS_E_INVAL, SCCS_E_CUDA.
+ */
+int sccs_server_create(sccs_server **out, const sccs_server_opts *opts);
+
+/* Queue one fit; never waits for the GPU.  SCCS_E_BUSY when the queue is full; SCCS_E_INVAL on a
+ * bad request.  *ticket identifies the request for sccs_poll. */
+int sccs_submit(sccs_server *srv, const sccs_request *req, uint64_t *ticket);
+
+/* SCCS_PENDING until the fit is done; then fills *res (and res->beta if given), retires the
+ * ticket and returns SCCS_OK.  The fit's own outcome is res->status.  Unknown ticket: SCCS_E_INVAL. */
+int sccs_poll(sccs_server *srv, uint64_t ticket, sccs_result *res);
+
+/* Queue depth, fits running, fits completed, state memory, CTAs in use. */
+int sccs_server_get_stats(sccs_server *srv, sccs_server_stats *stats);
+
+/* Finish the running fits, cancel the queued ones, release the server's device memory. */
+int sccs_server_destroy(sccs_server *srv);
+
 /*
  * sccs_check_wait_timeout -- self-test of the bounded device-side waits (failure detection).
  * Launches the gradient kernel on one CTA fewer than the all-reduce counts, so the last

@@ -5,6 +5,12 @@ The compute lives in libsccs.so (hand-written CUDA behind the C ABI of include/s
 """
 from .sccs import (  # noqa: F401
     EXPORTED,
+    FitServer,
+    sccs_poll,
+    sccs_server_create,
+    sccs_server_destroy,
+    sccs_server_get_stats,
+    sccs_submit,
     SCCSError,
     SCCSModel,
     sccs_check_wait_timeout,

@@ -490,6 +490,14 @@ int run_fit_phase(sccs_handle *h, const sccs::FitParams &p, bool fp32, sccs::Fit
 
 }  // namespace
 
+bool sccs_handle_view(const sccs_handle *h, sccs::HandleView *v) {
+    if (!h || !v) return false;
+    v->device = h->device;
+    v->threads = h->threads;
+    v->d = h->d;
+    return true;
+}
+
 extern "C" {
 
 int sccs_set_error(int code, const char *msg) { return fail(code, msg ? msg : ""); }

@@ -124,7 +124,19 @@ int fit_kernel_max_blocks_per_sm(int threads, int *blocks);
 int launch_fit_batch(const BatchEntry *entries_dev, const int2 *map_dev, int ctas, int threads, void *stream,
                      bool fp32);
 
+// What the serving layer needs of a dataset handle: its device, block size and layout (whose
+// static arrays it shares; the state pointers it replaces with a fit slot's own).
+struct HandleView {
+    int device;
+    int threads;
+    DevLayout d;
+};
+
 }  // namespace sccs
+
+struct sccs_handle;
+// Fill `v` from a created handle; false if h is null.
+bool sccs_handle_view(const sccs_handle *h, sccs::HandleView *v);
 
 // Record a thread-local error message for sccs_last_error and return `code`.
 extern "C" int sccs_set_error(int code, const char *msg);

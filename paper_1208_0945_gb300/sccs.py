@@ -58,6 +58,29 @@ class sccs_fit_info(ctypes.Structure):
                 ("fp32_cycles", ctypes.c_int32)]
 
 
+class sccs_server_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("queue_capacity", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class sccs_request(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("prior_type", ctypes.c_int32), ("dataset", ctypes.c_void_p),
+                ("variance", ctypes.c_double), ("tol_mode", ctypes.c_int32), ("max_cycles", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("beta0", ctypes.POINTER(ctypes.c_double))]
+
+
+class sccs_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("cycles", ctypes.c_int32), ("fp32_cycles", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("logpost", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("beta", ctypes.POINTER(ctypes.c_double))]
+
+
+class sccs_server_stats(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_int64), ("running", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("slot_bytes", ctypes.c_int64), ("ctas_in_use", ctypes.c_int32), ("capacity_ctas", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
@@ -76,6 +99,11 @@ _SIGS = {
     "sccs_get_beta": (ctypes.c_int, [_P, _dp]),
     "sccs_check_wait_timeout": (ctypes.c_int, [_P, ctypes.c_double]),
     "sccs_grad_hess_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int64, _P, _P]),
+    "sccs_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(sccs_server_opts)]),
+    "sccs_submit": (ctypes.c_int, [_P, ctypes.POINTER(sccs_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "sccs_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(sccs_result)]),
+    "sccs_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(sccs_server_stats)]),
+    "sccs_server_destroy": (ctypes.c_int, [_P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -226,6 +254,98 @@ def sccs_grad_hess_noalloc(seg_ptr, seg_subject, rows, E, D, n, ytx: float, P: i
     status (0 on success) and raises on errors."""
     return _check(_lib.sccs_grad_hess_noalloc(seg_ptr, seg_subject, rows, E, D, n, float(ytx), int(P), gh_out,
                                               stream), "sccs_grad_hess_noalloc")
+
+
+def sccs_server_create(device=0, max_inflight=64, queue_capacity=4096, hbm_budget_bytes=0):
+    o = sccs_server_opts(struct_size=ctypes.sizeof(sccs_server_opts), device=int(device),
+                         max_inflight=int(max_inflight), queue_capacity=int(queue_capacity),
+                         hbm_budget_bytes=int(hbm_budget_bytes))
+    srv = ctypes.c_void_p()
+    _check(_lib.sccs_server_create(ctypes.byref(srv), ctypes.byref(o)), "sccs_server_create")
+    return srv.value
+
+
+def sccs_submit(server, dataset, prior="normal", variance=1.0, tol_mode="rel_logpost", tol=1e-12,
+                max_cycles=1000, precision="fp64", beta0=None) -> int:
+    b0 = None if beta0 is None else np.ascontiguousarray(beta0, np.float64)
+    r = sccs_request(struct_size=ctypes.sizeof(sccs_request), prior_type=PRIOR[prior], dataset=dataset,
+                     variance=float(variance), tol_mode=TOL[tol_mode], max_cycles=int(max_cycles), tol=float(tol),
+                     precision=PREC[precision], reserved=0, beta0=_dptr(b0))
+    t = ctypes.c_uint64()
+    _check(_lib.sccs_submit(server, ctypes.byref(r), ctypes.byref(t)), "sccs_submit")
+    return t.value
+
+
+def sccs_poll(server, ticket: int, J: int):
+    """None while pending; else the result dict (beta included)."""
+    beta = np.zeros(max(J, 1))
+    res = sccs_result(beta=_dptr(beta))
+    rc = _check(_lib.sccs_poll(server, ctypes.c_uint64(ticket), ctypes.byref(res)), "sccs_poll")
+    if rc == PENDING:
+        return None
+    out = {name: getattr(res, name) for name, _ in sccs_result._fields_ if name not in ("reserved", "beta")}
+    out["beta"] = beta[:J]
+    return out
+
+
+def sccs_server_get_stats(server) -> dict:
+    st = sccs_server_stats()
+    _check(_lib.sccs_server_get_stats(server, ctypes.byref(st)), "sccs_server_get_stats")
+    return {name: getattr(st, name) for name, _ in sccs_server_stats._fields_}
+
+
+def sccs_server_destroy(server) -> int:
+    return _lib.sccs_server_destroy(server)
+
+
+class FitServer:
+    """Continuous-batching fit server over resident datasets (SCCSModel handles)."""
+
+    def __init__(self, device=0, max_inflight=64, queue_capacity=4096, hbm_budget_bytes=0):
+        self.server = sccs_server_create(device, max_inflight, queue_capacity, hbm_budget_bytes)
+        self._J = {}
+
+    def submit(self, model, **kw) -> int:
+        t = sccs_submit(self.server, model.handle, **kw)
+        self._J[t] = model.J
+        return t
+
+    def poll(self, ticket):
+        r = sccs_poll(self.server, ticket, self._J[ticket])
+        if r is not None:
+            del self._J[ticket]
+        return r
+
+    def wait(self, ticket, timeout_s=120.0):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError(f"request {ticket} still pending after {timeout_s} s")
+            time.sleep(0.0002)
+
+    def stats(self) -> dict:
+        return sccs_server_get_stats(self.server)
+
+    def close(self):
+        if getattr(self, "server", None):
+            sccs_server_destroy(self.server)
+            self.server = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ convenience wrapper

@@ -80,3 +80,18 @@ def test_validation_errors_need_no_gpu(lib, mutate, code):
         lib.sccs_create(5, pid, y, L, 2, cp, rows, xv)
     assert ei.value.code == code
     assert lib.sccs_last_error(None)
+
+
+@pytest.mark.parametrize("field,value", [("max_inflight", 0), ("queue_capacity", 0), ("hbm_budget_bytes", -1),
+                                         ("struct_size", 8)])
+def test_server_options_rejected_before_cuda(lib, field, value):
+    import ctypes
+    from paper_1208_0945_gb300 import sccs as S
+    o = S.sccs_server_opts(struct_size=ctypes.sizeof(S.sccs_server_opts), device=0, max_inflight=4,
+                           queue_capacity=4, hbm_budget_bytes=0)
+    setattr(o, field, value)
+    srv = ctypes.c_void_p()
+    assert S._lib.sccs_server_create(ctypes.byref(srv), ctypes.byref(o)) == -1
+    assert srv.value is None
+    assert S._lib.sccs_submit(None, None, None) == -1
+    assert S._lib.sccs_server_destroy(None) == 0
