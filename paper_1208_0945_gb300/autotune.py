@@ -7,9 +7,10 @@ A fit run by a team of S CTAs costs, per CCD cycle, about
 where lat(S) is the per-coordinate latency of a team of S CTAs (phase A on a tiny slice, the
 team's all-reduce, the FP64 step, phase C) and c the device time per nonzero on one CTA.  Both
 are measured on the device with probe fits through the library (`measure`).  `assign` then
-gives every fit of a batch a team size by greedy makespan minimisation: start from one CTA per
-fit and repeatedly grow the team of the currently slowest fit while that shortens it and the
-teams still fit on the device together.
+gives every fit of a batch a team size by greedy makespan minimisation against a simulation of
+the library's batched launch (a ticket queue: fits handed out longest first, each starting
+when its team's CTAs are free): start from one CTA per fit and keep growing the team of the
+fit that runs longest while the simulated makespan drops.
 """
 from __future__ import annotations
 
@@ -81,24 +82,57 @@ def _capacity(device: int) -> int:
     return int(props.multi_processor_count)   # one CTA per SM (512 threads, ~134 KB shared memory)
 
 
-def assign(fits, model: CostModel, capacity: int | None = None) -> list:
-    """fits: [(J, nnz per cycle)], returns a team size per fit (sum <= capacity when possible)."""
+def library_order(fits, S) -> list:
+    """The order in which the library's batched launch hands out tickets: longest first by its
+    own estimate (8192 per coordinate plus (nnz + 2 segments) per CTA of the team)."""
+    cost = [8192.0 * J + (nnz + 2.0 * segs) / s for (J, nnz, segs), s in zip(fits, S)]
+    return sorted(range(len(fits)), key=lambda k: -cost[k])
+
+
+def makespan(fits, S, model: CostModel, capacity: int | None = None) -> float:
+    """Device time per cycle of the batch under the queue launch: fits in library order, each
+    starting when its S CTAs are free (the S earliest-free CTAs), per-cycle cost from the model."""
+    import heapq
+
     cap = capacity or model.capacity
+    free = [0.0] * min(cap, sum(S))
+    heapq.heapify(free)
+    end = 0.0
+    for k in library_order(fits, S):
+        J, nnz, _ = fits[k]
+        got = [heapq.heappop(free) for _ in range(S[k])]
+        t1 = max(got) + model.cycle_us(J, nnz, S[k])
+        for _ in range(S[k]):
+            heapq.heappush(free, t1)
+        end = max(end, t1)
+    return end
+
+
+def assign(fits, model: CostModel, capacity: int | None = None, max_rounds: int = 4000) -> list:
+    """fits: [(J, nnz per cycle, segments)]; returns a team size per fit.
+
+    Starts from one CTA per fit and repeatedly doubles (then grows by one) the team of the fit
+    that ends last in the simulated schedule, keeping a change only when the makespan drops."""
+    cap = capacity or model.capacity
+    fits = [tuple(f) + (0,) * (3 - len(f)) for f in fits]
     S = [1] * len(fits)
-    t = [model.cycle_us(J, nnz, 1) for J, nnz in fits]
-    used = len(fits)
+    best = makespan(fits, S, model, cap)
     frozen = set()
-    while used < cap:
-        cand = [f for f in range(len(fits)) if f not in frozen]
+    for _ in range(max_rounds):
+        cand = [k for k in range(len(fits)) if k not in frozen]
         if not cand:
             break
-        f = max(cand, key=lambda k: t[k])
-        J, nnz = fits[f]
-        t_new = model.cycle_us(J, nnz, S[f] + 1)
-        if t_new >= t[f]:
+        f = max(cand, key=lambda k: model.cycle_us(fits[k][0], fits[k][1], S[k]))
+        improved = False
+        for new in (min(cap, 2 * S[f]), min(cap, S[f] + 1)):
+            if new <= S[f]:
+                continue
+            trial = list(S)
+            trial[f] = new
+            t = makespan(fits, trial, model, cap)
+            if t < best:
+                S, best, improved = trial, t, True
+                break
+        if not improved:
             frozen.add(f)
-            continue
-        S[f] += 1
-        t[f] = t_new
-        used += 1
     return S

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -462,6 +463,200 @@ sccs::FitParams base_params(const sccs_handle *h) {
     return p;
 }
 
+// ------------------------------------------------------------------ batched fits
+//
+// A batch plan holds what one batch of handles needs on the device (entries, team offsets,
+// counters, result buffers), pinned staging for the per-call entries and the results, and a
+// CUDA graph of the whole device side of a call: entries in, counters and outputs zeroed, the
+// persistent queue launch, the results gathered and copied out.  Plans are cached by handle
+// list and precision and dropped when one of their handles is destroyed, so repeated batches
+// over the same datasets (a prior-variance grid, say) replay the graph.
+constexpr long long kAssembleWaitNs = 30000000000LL;   // a team waits at most 30 s for its CTAs
+constexpr size_t kMaxPlans = 8;
+
+struct BatchPlan {
+    std::vector<sccs_handle *> handles;   // caller order
+    int mode = 0;
+    int device = 0;
+    int n = 0;
+    std::vector<int32_t> order;           // scheduling position -> caller index
+    std::vector<long long> beta_off;      // per scheduling position, in doubles
+    void *dev = nullptr;
+    void *host = nullptr;
+    size_t stage_bytes = 0, result_bytes = 0;
+    sccs::BatchEntry *ent_host = nullptr;
+    sccs::FitOut *out32_dev = nullptr;
+    sccs::FitOut *res_outs_host = nullptr, *res_outs32_host = nullptr;
+    double *res_beta_host = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long last_use = 0;
+};
+
+std::mutex g_batch_mu;
+std::vector<BatchPlan *> g_plans;
+unsigned long long g_plan_clock = 0;
+
+void free_plan(BatchPlan *pl) {
+    if (!pl) return;
+    cudaSetDevice(pl->device);
+    if (pl->stream) cudaStreamSynchronize(pl->stream);
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->dev) cudaFree(pl->dev);
+    if (pl->host) cudaFreeHost(pl->host);
+    if (pl->ev0) cudaEventDestroy(pl->ev0);
+    if (pl->ev1) cudaEventDestroy(pl->ev1);
+    if (pl->stream) cudaStreamDestroy(pl->stream);
+    delete pl;
+}
+
+void forget_plans_of(const sccs_handle *h) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_plans.size();) {
+        BatchPlan *pl = g_plans[i];
+        if (std::find(pl->handles.begin(), pl->handles.end(), h) != pl->handles.end()) {
+            free_plan(pl);
+            g_plans.erase(g_plans.begin() + static_cast<long>(i));
+        } else {
+            ++i;
+        }
+    }
+}
+
+size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Scheduling order: longest fits first (estimated device time per cycle: a latency term per
+// coordinate plus the nonzeros and segments each CTA of the team streams).
+std::vector<int32_t> lpt_order(sccs_handle *const *handles, int32_t n) {
+    std::vector<double> cost(n);
+    for (int32_t k = 0; k < n; ++k) {
+        const sccs_handle *h = handles[k];
+        cost[k] = 8192.0 * h->d.J +
+                  (static_cast<double>(h->info.nnz_kept) + 2.0 * static_cast<double>(h->info.segments)) /
+                      std::max(1, h->d.S);
+    }
+    std::vector<int32_t> order(n);
+    for (int32_t k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    return order;
+}
+
+// Called with g_batch_mu held.
+int get_batch_plan(sccs_handle *const *handles, int32_t n, int mode, BatchPlan **out) {
+    for (BatchPlan *pl : g_plans) {
+        if (pl->mode == mode && pl->n == n && std::equal(pl->handles.begin(), pl->handles.end(), handles)) {
+            pl->last_use = ++g_plan_clock;
+            *out = pl;
+            return SCCS_OK;
+        }
+    }
+    const int threads = handles[0]->threads;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, handles[0]->device);
+    int rc = sccs::fit_kernel_max_blocks_per_sm(threads, &per_sm);
+    if (rc) return cuda_fail(static_cast<cudaError_t>(rc), "occupancy");
+    const int capacity = sms * std::max(per_sm, 1);
+    long long tickets = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        if (handles[k]->d.S > capacity) return fail(SCCS_E_INVAL, "a handle has more shards than the device holds at once");
+        tickets += handles[k]->d.S;
+    }
+    auto pl = new BatchPlan();
+    auto bail = [&](int code) {
+        free_plan(pl);
+        return code;
+    };
+    pl->handles.assign(handles, handles + n);
+    pl->mode = mode;
+    pl->device = handles[0]->device;
+    pl->n = n;
+    pl->order = lpt_order(handles, n);
+    pl->beta_off.resize(n);
+    long long nbeta = 0;
+    std::vector<int> team_start(n + 1, 0);
+    for (int32_t q = 0; q < n; ++q) {
+        const sccs_handle *h = handles[pl->order[q]];
+        pl->beta_off[q] = nbeta;
+        nbeta += std::max<int32_t>(h->d.J, 1);
+        team_start[q + 1] = team_start[q] + h->d.S;
+    }
+    // device: [entries | team_start | beta_off | counters | out32] [outs | outs32 | betas]
+    const size_t b_ent = al256(sizeof(sccs::BatchEntry) * n), b_ts = al256(sizeof(int) * (n + 1)),
+                 b_off = al256(sizeof(long long) * n), b_cnt = al256(sizeof(unsigned) * (n + 1)),
+                 b_o32 = al256(sizeof(sccs::FitOut) * n), b_outs = al256(sizeof(sccs::FitOut) * n),
+                 b_beta = al256(sizeof(double) * static_cast<size_t>(nbeta));
+    pl->stage_bytes = b_ent + b_ts + b_off;
+    pl->result_bytes = 2 * b_outs + b_beta;
+    const size_t dev_bytes = pl->stage_bytes + b_cnt + b_o32 + pl->result_bytes;
+    if (cudaMalloc(&pl->dev, dev_bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        pl->dev = nullptr;
+        return bail(fail(SCCS_E_NOMEM, "batch buffers"));
+    }
+    if (cudaMallocHost(&pl->host, pl->stage_bytes + pl->result_bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        pl->host = nullptr;
+        return bail(fail(SCCS_E_NOMEM, "batch staging"));
+    }
+    char *d = static_cast<char *>(pl->dev);
+    char *hs = static_cast<char *>(pl->host);
+    auto *ent_dev = reinterpret_cast<sccs::BatchEntry *>(d);
+    auto *ts_dev = reinterpret_cast<int *>(d + b_ent);
+    auto *off_dev = reinterpret_cast<long long *>(d + b_ent + b_ts);
+    auto *cnt_dev = reinterpret_cast<unsigned *>(d + pl->stage_bytes);
+    pl->out32_dev = reinterpret_cast<sccs::FitOut *>(d + pl->stage_bytes + b_cnt);
+    char *res_dev = d + pl->stage_bytes + b_cnt + b_o32;
+    auto *outs_dev = reinterpret_cast<sccs::FitOut *>(res_dev);
+    auto *outs32_dev = reinterpret_cast<sccs::FitOut *>(res_dev + b_outs);
+    auto *beta_dev = reinterpret_cast<double *>(res_dev + 2 * b_outs);
+    pl->ent_host = reinterpret_cast<sccs::BatchEntry *>(hs);
+    std::memcpy(hs + b_ent, team_start.data(), sizeof(int) * (n + 1));
+    std::memcpy(hs + b_ent + b_ts, pl->beta_off.data(), sizeof(long long) * n);
+    char *res_host = hs + pl->stage_bytes;
+    pl->res_outs_host = reinterpret_cast<sccs::FitOut *>(res_host);
+    pl->res_outs32_host = reinterpret_cast<sccs::FitOut *>(res_host + b_outs);
+    pl->res_beta_host = reinterpret_cast<double *>(res_host + 2 * b_outs);
+    if (cudaStreamCreateWithFlags(&pl->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&pl->ev0) != cudaSuccess || cudaEventCreate(&pl->ev1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return bail(fail(SCCS_E_CUDA, "batch stream or events"));
+    }
+    const int grid = static_cast<int>(std::min<long long>(tickets, capacity));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(pl->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "batch capture"));
+    int le = static_cast<int>(cudaMemcpyAsync(pl->dev, pl->host, pl->stage_bytes, cudaMemcpyHostToDevice, pl->stream));
+    if (!le) le = sccs::launch_batch_prep(ent_dev, n, cnt_dev, pl->stream);
+    if (!le) le = sccs::launch_fit_queue(ent_dev, ts_dev, n, cnt_dev, grid, threads, pl->stream, mode, kAssembleWaitNs);
+    if (!le) le = sccs::launch_batch_gather(ent_dev, n, outs_dev, outs32_dev, beta_dev, off_dev, pl->stream);
+    if (!le)
+        le = static_cast<int>(cudaMemcpyAsync(res_host, res_dev, pl->result_bytes, cudaMemcpyDeviceToHost, pl->stream));
+    e = cudaStreamEndCapture(pl->stream, &graph);
+    if (le) {
+        if (graph) cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        return bail(cuda_fail(static_cast<cudaError_t>(le), "batch capture (launch)"));
+    }
+    if (e != cudaSuccess) return bail(cuda_fail(e, "batch capture (end)"));
+    e = cudaGraphInstantiate(&pl->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        pl->exec = nullptr;
+        return bail(cuda_fail(e, "batch graph instantiate"));
+    }
+    if (g_plans.size() >= kMaxPlans) {
+        auto lru = std::min_element(g_plans.begin(), g_plans.end(),
+                                    [](const BatchPlan *a, const BatchPlan *b) { return a->last_use < b->last_use; });
+        free_plan(*lru);
+        g_plans.erase(lru);
+    }
+    pl->last_use = ++g_plan_clock;
+    g_plans.push_back(pl);
+    *out = pl;
+    return SCCS_OK;
+}
+
 // One launch of the fit kernel (FP64 or FP32 body) with its result checks; `ms` gets the
 // kernel's event time.
 int run_fit_phase(sccs_handle *h, const sccs::FitParams &p, bool fp32, sccs::FitOut &r, float &ms) {
@@ -649,6 +844,7 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
 }
 
 int sccs_destroy(sccs_handle *h) {
+    if (h) forget_plans_of(h);
     destroy_handle(h);
     return SCCS_OK;
 }
@@ -809,28 +1005,25 @@ int sccs_fit_batch(sccs_handle *const *handles, int32_t n, const sccs_fit_opts *
         if (!handles[k]) return fail(SCCS_E_INVAL, "null handle in batch");
         if (handles[k]->device != handles[0]->device) return fail(SCCS_E_INVAL, "handles on different devices");
         if (handles[k]->threads != handles[0]->threads) return fail(SCCS_E_INVAL, "handles with different threads_per_block");
-        for (int32_t q = 0; q < k; ++q)
-            if (handles[q] == handles[k]) return fail(SCCS_E_INVAL, "a handle appears twice in the batch");
+    }
+    {
+        std::vector<sccs_handle *> sorted(handles, handles + n);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+            return fail(SCCS_E_INVAL, "a handle appears twice in the batch");
     }
     sccs_handle *h0 = handles[0];
     int rc = set_device(h0);
     if (rc) return rc;
-    const int threads = h0->threads;
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h0->device);
-    if ((rc = sccs::fit_kernel_max_blocks_per_sm(threads, &per_sm))) return cuda_fail(static_cast<cudaError_t>(rc), "occupancy");
-    const int capacity = sms * per_sm;
-    cudaStream_t st = h0->stream;
+    const int mode = o.precision == SCCS_PREC_FP64 ? sccs::kBatchFp64
+                     : o.precision == SCCS_PREC_FP32 ? sccs::kBatchFp32 : sccs::kBatchFp32Polish;
+    std::lock_guard<std::mutex> batch_lock(g_batch_mu);
+    BatchPlan *plan = nullptr;
+    if ((rc = get_batch_plan(handles, n, mode, &plan))) return rc;
     for (int32_t k = 0; k < n; ++k) {
         sccs_handle *h = handles[k];
-        if (h->stream != st) cudaStreamSynchronize(h->stream);   // no work of the handle in flight elsewhere
-        if (o.warm_start) {
-            cudaMemcpyAsync(h->beta_dev, h->d.beta_priv, sizeof(double) * std::max<int32_t>(h->d.J, 1),
-                            cudaMemcpyDeviceToDevice, st);
-            if ((rc = sccs::launch_init_state(h->d, h->beta_dev, threads, st))) return cuda_fail(static_cast<cudaError_t>(rc), "init");
-        } else if ((rc = sccs::launch_init_state(h->d, nullptr, threads, st))) {
-            return cuda_fail(static_cast<cudaError_t>(rc), "init");
-        }
+        cudaError_t e = cudaStreamSynchronize(h->stream);   // no work of the handle in flight
+        if (e != cudaSuccess) return cuda_fail(e, "handle stream");
         const int32_t need = o.max_cycles + 1;
         if (need > h->hist_cap) {
             if (h->hist_dev) cudaFree(h->hist_dev);
@@ -843,146 +1036,79 @@ int sccs_fit_batch(sccs_handle *const *handles, int32_t n, const sccs_fit_opts *
                 return fail(SCCS_E_NOMEM, "history buffer");
             h->hist_cap = need;
         }
-        if (h->d.S > capacity) return fail(SCCS_E_INVAL, "a handle has more shards than the device holds at once");
     }
-    // waves of fits whose shard counts fit on the device together
-    std::vector<std::vector<int32_t>> waves;
-    {
-        std::vector<int32_t> cur;
-        int used = 0;
-        for (int32_t k = 0; k < n; ++k) {
-            if (used + handles[k]->d.S > capacity) {
-                waves.push_back(cur);
-                cur.clear();
-                used = 0;
-            }
-            cur.push_back(k);
-            used += handles[k]->d.S;
-        }
-        if (!cur.empty()) waves.push_back(cur);
-    }
-    sccs::BatchEntry *ent_dev = nullptr;
-    int2 *map_dev = nullptr;
-    if (cudaMalloc(&ent_dev, sizeof(sccs::BatchEntry) * n) != cudaSuccess ||
-        cudaMalloc(&map_dev, sizeof(int2) * capacity) != cudaSuccess) {
-        cudaFree(ent_dev);
-        return fail(SCCS_E_NOMEM, "batch descriptors");
-    }
-    std::vector<sccs::BatchEntry> ent(n);
-    std::vector<int2> map;
-    std::vector<int> status(n, SCCS_OK);
-    std::vector<sccs::FitOut> res(n);
-    std::vector<int32_t> fp32_cycles(n, 0);
-    std::vector<int64_t> nonzero(n, 0);
-    std::vector<int32_t> warnings(n, 0);
-    double kernel_ms = 0.0;
-    auto run_phase = [&](bool fp32, bool polish_phase) -> int {
-        for (int32_t k = 0; k < n; ++k) {
-            sccs_handle *h = handles[k];
-            sccs::FitParams p = base_params(h);
-            p.tol_mode = o.tol_mode;
-            p.tol = o.tol;
-            p.max_cycles = o.max_cycles;
-            p.record_history = 1;
-            if (fp32 && o.precision == SCCS_PREC_FP32_POLISH) {
-                p.tol_mode = SCCS_TOL_REL_LOGPOST;
-                p.tol = kFp32PhaseRelTol;
-            }
-            ent[k] = sccs::BatchEntry{h->d, p, h->out_dev, h->hist_dev};
-        }
-        cudaMemcpyAsync(ent_dev, ent.data(), sizeof(sccs::BatchEntry) * n, cudaMemcpyHostToDevice, st);
-        for (const auto &w : waves) {
-            map.clear();
-            for (int32_t k : w)
-                for (int sidx = 0; sidx < handles[k]->d.S; ++sidx) map.push_back(make_int2(k, sidx));
-            cudaMemcpyAsync(map_dev, map.data(), sizeof(int2) * map.size(), cudaMemcpyHostToDevice, st);
-            cudaEventRecord(h0->ev0, st);
-            int le = sccs::launch_fit_batch(ent_dev, map_dev, static_cast<int>(map.size()), threads, st, fp32);
-            if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "batch kernel launch");
-            cudaEventRecord(h0->ev1, st);
-            cudaError_t e = cudaEventSynchronize(h0->ev1);
-            if (e != cudaSuccess) return cuda_fail(e, "batch kernel");
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, h0->ev0, h0->ev1);
-            kernel_ms += ms;
-        }
-        for (int32_t k = 0; k < n; ++k)
-            cudaMemcpyAsync(handles[k]->out_host, handles[k]->out_dev, sizeof(sccs::FitOut), cudaMemcpyDeviceToHost, st);
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_fail(e, "batch results");
-        for (int32_t k = 0; k < n; ++k) {
-            sccs_handle *h = handles[k];
-            if (status[k] != SCCS_OK) continue;
-            const sccs::FitOut r = *h->out_host;
-            if (r.status == -6 || r.abort_flag) {
-                reset_after_abort(h);
-                status[k] = SCCS_E_TIMEOUT;
-                continue;
-            }
-            h->seq = r.seq_end;
-            if (r.status == -7) {
-                run_init_state(h, nullptr);
-                status[k] = SCCS_E_NUMERIC;
-                continue;
-            }
-            res[k] = r;
-            nonzero[k] += r.nonzero_steps;
-            warnings[k] |= r.warnings;
-            if (fp32) fp32_cycles[k] = r.cycles;
-        }
-        (void)polish_phase;
-        return SCCS_OK;
-    };
-    auto done = [&](int code) {
-        cudaFree(ent_dev);
-        cudaFree(map_dev);
-        return code;
-    };
-    if (o.precision != SCCS_PREC_FP64) {
-        for (int32_t k = 0; k < n; ++k) {
-            int le = sccs::launch_e_to_f32(handles[k]->d, threads, st);
-            if (le != 0) return done(cuda_fail(static_cast<cudaError_t>(le), "E conversion launch"));
-        }
-        if ((rc = run_phase(true, false))) return done(rc);
-        if (o.precision == SCCS_PREC_FP32_POLISH) {
-            for (int32_t k = 0; k < n; ++k) {
-                sccs_handle *h = handles[k];
-                cudaMemcpyAsync(h->beta_dev, h->d.beta_priv, sizeof(double) * std::max<int32_t>(h->d.J, 1),
-                                cudaMemcpyDeviceToDevice, st);
-                int le = sccs::launch_init_state(h->d, h->beta_dev, threads, st, true);
-                if (le != 0) return done(cuda_fail(static_cast<cudaError_t>(le), "init_state launch"));
-            }
-            if ((rc = run_phase(false, true))) return done(rc);
-        }
-    } else if ((rc = run_phase(false, false))) {
-        return done(rc);
-    }
-    int first_err = SCCS_OK;
-    for (int32_t k = 0; k < n; ++k) {
+    // the entries, in the plan's scheduling order
+    for (int32_t q = 0; q < n; ++q) {
+        const int32_t k = plan->order[q];
         sccs_handle *h = handles[k];
-        const sccs::FitOut &r = res[k];
-        if (status[k] == SCCS_OK && beta_out && beta_out[k] && h->d.J > 0) {
-            cudaError_t e = cudaMemcpy(beta_out[k], h->d.beta_priv, sizeof(double) * h->d.J, cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) status[k] = SCCS_E_CUDA;
+        sccs::FitParams p = base_params(h);
+        p.tol_mode = o.tol_mode;
+        p.tol = o.tol;
+        p.max_cycles = o.max_cycles;
+        p.record_history = 1;
+        sccs::FitParams p32 = p;
+        if (mode == sccs::kBatchFp32Polish) {
+            p32.tol_mode = SCCS_TOL_REL_LOGPOST;
+            p32.tol = kFp32PhaseRelTol;
         }
+        sccs::BatchEntry &en = plan->ent_host[q];
+        en.d = h->d;
+        en.p = p;
+        en.p32 = p32;
+        en.out = h->out_dev;
+        en.out32 = mode == sccs::kBatchFp32Polish ? plan->out32_dev + q : nullptr;
+        en.hist = h->hist_dev;
+        en.warm = o.warm_start ? 1 : 0;
+        en.team = h->d.S;
+    }
+    cudaEventRecord(plan->ev0, plan->stream);
+    cudaError_t e = cudaGraphLaunch(plan->exec, plan->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+    cudaEventRecord(plan->ev1, plan->stream);
+    e = cudaStreamSynchronize(plan->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph");
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, plan->ev0, plan->ev1);
+
+    int first_err = SCCS_OK;
+    for (int32_t q = 0; q < n; ++q) {
+        const int32_t k = plan->order[q];
+        sccs_handle *h = handles[k];
+        const sccs::FitOut r = plan->res_outs_host[q];
+        const sccs::FitOut r32 = mode == sccs::kBatchFp32Polish ? plan->res_outs32_host[q] : sccs::FitOut{};
+        int status = SCCS_OK;
+        if (r.status == -6 || r.abort_flag || r32.status == -6) {
+            reset_after_abort(h);
+            status = SCCS_E_TIMEOUT;
+        } else if (r.status == -7 || r32.status == -7) {
+            h->seq = r.status == -7 ? r.seq_end : r32.seq_end;
+            run_init_state(h, nullptr);
+            cudaStreamSynchronize(h->stream);
+            status = SCCS_E_NUMERIC;
+        } else {
+            h->seq = r.seq_end;
+        }
+        const int32_t fp32_cycles = mode == sccs::kBatchFp32Polish ? r32.cycles : mode == sccs::kBatchFp32 ? r.cycles : 0;
+        if (status == SCCS_OK && beta_out && beta_out[k] && h->d.J > 0)
+            std::memcpy(beta_out[k], plan->res_beta_host + plan->beta_off[q], sizeof(double) * h->d.J);
         if (infos) {
             sccs_fit_info &fi = infos[k];
-            const int32_t cyc = o.precision == SCCS_PREC_FP32_POLISH ? fp32_cycles[k] + r.cycles : r.cycles;
-            fi.status = status[k] != SCCS_OK ? status[k] : r.status;
+            const int32_t cyc = mode == sccs::kBatchFp32Polish ? fp32_cycles + r.cycles : r.cycles;
+            fi.status = status != SCCS_OK ? status : r.status;
             fi.cycles = cyc;
             fi.steps = static_cast<int64_t>(cyc) * h->d.J;
-            fi.nonzero_steps = nonzero[k];
+            fi.nonzero_steps = r.nonzero_steps + (mode == sccs::kBatchFp32Polish ? r32.nonzero_steps : 0);
             fi.logpost = r.logpost;
             fi.conv_value = r.conv;
-            fi.kernel_ms = kernel_ms;
+            fi.kernel_ms = kms;
             fi.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-            fi.warnings = warnings[k];
-            fi.fp32_cycles = fp32_cycles[k];
+            fi.warnings = r.warnings | r32.warnings;
+            fi.fp32_cycles = fp32_cycles;
         }
-        if (status[k] != SCCS_OK && first_err == SCCS_OK) first_err = status[k];
+        if (status != SCCS_OK && first_err == SCCS_OK) first_err = status;
     }
-    if (first_err != SCCS_OK) return done(fail(first_err, "at least one fit of the batch failed (see infos[k].status)"));
-    return done(SCCS_OK);
+    if (first_err != SCCS_OK) return fail(first_err, "at least one fit of the batch failed (see infos[k].status)");
+    return SCCS_OK;
 }
 
 int sccs_grad_hess(sccs_handle *h, int32_t j, const double *beta, double *g, double *hess) {

@@ -93,13 +93,22 @@ struct FitOut {
     int32_t pad;
 };
 
-// One fit of a batched launch: its layout and state, parameters and outputs.
+// One fit of a batched launch: its layout and state, parameters and outputs.  p32 drives
+// the FP32 phase (FP32 and FP32-then-polish), p the FP64 fit or polish.  out receives the
+// fit's final result; out32 the FP32 phase's when a polish follows it.
 struct BatchEntry {
     DevLayout d;
     FitParams p;
+    FitParams p32;
     FitOut *out;
+    FitOut *out32;
     double *hist;
+    int32_t warm;              // start from the handle's current beta instead of 0
+    int32_t team;              // d.S: CTAs that run this fit together
 };
+
+// Precision of a batched launch.
+enum BatchMode : int { kBatchFp64 = 0, kBatchFp32Polish = 1, kBatchFp32 = 2 };
 
 // Dynamic shared memory the fit kernel needs.
 size_t fit_kernel_smem_bytes();
@@ -121,8 +130,20 @@ int launch_grad_hess_partial(const DevLayout &d, int32_t j, const FitParams &p, 
 int fit_kernel_max_blocks_per_sm(int threads, int *blocks);
 // Independent fits in one cooperative launch: CTA b runs shard map[b].y of fit map[b].x
 // (entries and map in device memory; every fit's CTAs form its own all-reduce team).
-int launch_fit_batch(const BatchEntry *entries_dev, const int2 *map_dev, int ctas, int threads, void *stream,
-                     bool fp32);
+// The batched fits in one persistent cooperative launch of `ctas` CTAs.  entries (device) are
+// in scheduling order; team_start (device, n + 1) is the prefix sum of the entries' team sizes;
+// counters (device, 1 + n unsigned, zeroed by launch_batch_prep) hold the ticket counter and
+// one arrival count per fit.  A CTA takes tickets in order: ticket t is shard
+// t - team_start[f] of the fit f whose range holds t.  The fit starts when its whole team has
+// arrived (a wait bounded by assemble_ns) and computes exactly what it computes alone.
+int launch_fit_queue(const BatchEntry *entries_dev, const int *team_start_dev, int n, unsigned *counters_dev,
+                     int ctas, int threads, void *stream, int mode, long long assemble_ns);
+// Zero the ticket/arrival counters and every entry's out / out32 (one small launch).
+int launch_batch_prep(const BatchEntry *entries_dev, int n, unsigned *counters_dev, void *stream);
+// Gather every fit's out, out32 and beta (shard 0's copy) into one buffer: outs[n], outs32[n],
+// then the betas at beta_off[f] doubles from `betas`.
+int launch_batch_gather(const BatchEntry *entries_dev, int n, FitOut *outs, FitOut *outs32, double *betas,
+                        const long long *beta_off_dev, void *stream);
 
 // What the serving layer needs of a dataset handle: its device, block size and layout (whose
 // static arrays it shares; the state pointers it replaces with a fit slot's own).

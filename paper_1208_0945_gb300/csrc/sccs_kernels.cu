@@ -96,6 +96,10 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_init_fence() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -272,6 +276,9 @@ struct SharedState {
     long long nonzero;
     int ok;
     int stop;
+    int run_status;         // a finished run_fit's status (thread 0 writes it)
+    int drained;            // its staging copies all landed (thread blockDim - 32 writes it)
+    unsigned long long run_seq;   // the all-reduce sequence number it ended at
     ColDesc desc[2];
     uint64_t bar[2];
 };
@@ -1005,8 +1012,25 @@ __device__ void beta_terms(const DevLayout &d, int s, const FitParams &p, double
 // into this CTA's shared memory.
 __device__ void drain_stages(SharedState &sh, unsigned pending, unsigned phase_bits, long long timeout_ns) {
     if (threadIdx.x != static_cast<int>(blockDim.x) - 32) return;
+    int ok = 1;
     for (int b = 0; b < 2; ++b)
-        if ((pending >> b) & 1u) (void)mbar_wait(&sh.bar[b], (phase_bits >> b) & 1u, timeout_ns);
+        if ((pending >> b) & 1u) ok &= mbar_wait(&sh.bar[b], (phase_bits >> b) & 1u, timeout_ns) ? 1 : 0;
+    sh.drained = ok;
+}
+
+// End of a run: publish its status and sequence number to the CTA, and retire the staging
+// barriers (when no copy is outstanding) so the next run can initialise them afresh.
+__device__ void finish_run(SharedState &sh, int status, unsigned long long seq) {
+    if (threadIdx.x == 0) {
+        sh.run_status = status;
+        sh.run_seq = seq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && sh.drained) {
+        mbar_inval(&sh.bar[0]);
+        mbar_inval(&sh.bar[1]);
+    }
+    __syncthreads();
 }
 
 // beta_j <- beta_j + db, the trust-region update T_j <- max(2|db|, T_j / 2), and the cycle's sums
@@ -1052,6 +1076,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
         sh.desc[0].staged = 0;
         sh.desc[1].staged = 0;
         sh.nonzero = 0;
+        sh.drained = 1;
     }
     __syncthreads();
     // staging (copies, pending set, next bounds) belongs to the last warp's lane 0
@@ -1263,6 +1288,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
         out->seq_end = seq;
         out->err_where = 0;
     }
+    finish_run(sh, status, seq);
     return;
 aborted:
     drain_stages(sh, pending, phase_bits, timeout);
@@ -1270,6 +1296,7 @@ aborted:
         out->status = kStTimeout;
         out->err_where = 1;
     }
+    finish_run(sh, kStTimeout, seq);
 }
 
 
@@ -1280,20 +1307,159 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
     run_fit<F32>(d, p, out, hist, blockIdx.x, *reinterpret_cast<SmemLayout *>(smem_raw), sh);
 }
 
-// Several independent fits in one launch.  A fit's CTAs exchange partial sums only with each
-// other (its own all-reduce slots), so teams never wait on one another, and every fit computes
-// exactly what it computes when launched alone with the same number of shards.
-template <bool F32>
-__global__ void __launch_bounds__(512, 1) fit_batch_kernel(const BatchEntry *entries, const int2 *map) {
+// E_k = l_k exp(Xb_k) on shard s's rows, with Xb accumulated column by column in j order;
+// the shard's private beta copy = beta0 (0 when null) and its trust radii = 1 unless kept.
+// beta0 may be the shard's own copy (a warm start).
+__device__ void init_shard(const DevLayout &d, int s, const double *beta0, bool keep_trust) {
+    const long long r0 = d.shard_row[s], r1 = d.shard_row[s + 1];
+    double *beta = d.beta_priv + static_cast<long long>(s) * d.J;
+    double *trust = d.trust_priv + static_cast<long long>(s) * d.J;
+    if (!beta0) {
+        for (int j = threadIdx.x; j < d.J; j += blockDim.x) {
+            beta[j] = 0.0;
+            if (!keep_trust) trust[j] = 1.0;
+        }
+        for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k];
+        __syncthreads();
+        return;
+    }
+    for (int j = threadIdx.x; j < d.J; j += blockDim.x) {
+        beta[j] = beta0[j];
+        if (!keep_trust) trust[j] = 1.0;
+    }
+    for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = 0.0;
+    __syncthreads();
+    for (int j = 0; j < d.J; ++j) {
+        const double bj = beta0[j];
+        if (bj == 0.0) continue;
+        const long long so = static_cast<long long>(s) * (d.J + 1) + j;
+        for (long long q = d.slice_row[so] + threadIdx.x; q < d.slice_row[so + 1]; q += blockDim.x)
+            d.E[d.rows[q]] += bj;
+        __syncthreads();
+    }
+    for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k] * exp(d.E[k]);
+    __syncthreads();
+}
+
+__device__ void e_to_f32_shard(const DevLayout &d, int s) {
+    for (long long k = d.shard_row[s] + threadIdx.x; k < d.shard_row[s + 1]; k += blockDim.x)
+        d.E32[k] = static_cast<float>(d.E[k]);
+    __syncthreads();
+}
+
+// Wait until all `team` CTAs of a fit have arrived (bounded; gives up early if the fit was
+// aborted).  Thread 0 only.
+__device__ bool team_assemble(unsigned *arrived, int team, long long limit_ns, int *abort_flag) {
+    __threadfence();
+    atomicAdd(arrived, 1u);
+    const long long t0 = now_ns();
+    for (unsigned it = 0;; ++it) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(arrived) : "memory");
+        if (static_cast<int>(v) >= team) return true;
+        if (*reinterpret_cast<volatile int *>(abort_flag)) return false;
+        if ((it & 63u) == 63u && now_ns() - t0 > limit_ns) {
+            atomicExch(abort_flag, 1);
+            return false;
+        }
+        __nanosleep(200);
+    }
+}
+
+// Several independent fits in one persistent launch, scheduled as a ticket queue (one ticket
+// per CTA of each fit's team, in the host's order).  A team's CTAs exchange partial sums only
+// with each other, through the fit's own all-reduce slots, so teams never wait on one another
+// and every fit computes exactly what it computes when launched alone with the same shards.
+template <int MODE>
+__global__ void __launch_bounds__(512, 1) fit_queue_kernel(const BatchEntry *entries, const int *team_start, int n,
+                                                          unsigned *counters, long long assemble_ns) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ SharedState sh;
     __shared__ __align__(16) BatchEntry e;
-    const int2 m = map[blockIdx.x];
-    const int *src = reinterpret_cast<const int *>(entries + m.x);
-    int *dst = reinterpret_cast<int *>(&e);
-    for (int i = threadIdx.x; i < static_cast<int>(sizeof(BatchEntry) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
-    __syncthreads();
-    run_fit<F32>(e.d, e.p, e.out, e.hist, m.y, *reinterpret_cast<SmemLayout *>(smem_raw), sh);
+    __shared__ int sh_t, sh_f, sh_go;
+    SmemLayout &sm = *reinterpret_cast<SmemLayout *>(smem_raw);
+    const int total = team_start[n];
+    if (threadIdx.x == 0) sh.drained = 1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = static_cast<int>(atomicAdd(&counters[0], 1u));
+            int f = -1;
+            if (t < total) {
+                int lo = 0, hi = n - 1;             // largest f with team_start[f] <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (team_start[mid] <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                f = lo;
+            }
+            sh_t = t;
+            sh_f = f;
+        }
+        __syncthreads();
+        const int t = sh_t, f = sh_f;
+        if (t >= total) break;
+        {
+            const int *src = reinterpret_cast<const int *>(entries + f);
+            int *dst = reinterpret_cast<int *>(&e);
+            for (int i = threadIdx.x; i < static_cast<int>(sizeof(BatchEntry) / sizeof(int)); i += blockDim.x)
+                dst[i] = src[i];
+        }
+        __syncthreads();
+        const int s = t - team_start[f];
+        init_shard(e.d, s, e.warm ? e.d.beta_priv + static_cast<long long>(s) * e.d.J : nullptr, false);
+        if (MODE != kBatchFp64) e_to_f32_shard(e.d, s);
+        if (threadIdx.x == 0) sh_go = team_assemble(&counters[1 + f], e.team, assemble_ns, e.d.abort_flag) ? 1 : 0;
+        __syncthreads();
+        if (!sh_go) {
+            if (threadIdx.x == 0 && s == 0) {
+                e.out->status = kStTimeout;
+                e.out->err_where = 3;
+            }
+            __syncthreads();
+            continue;
+        }
+        if (MODE == kBatchFp64) {
+            run_fit<false>(e.d, e.p, e.out, e.hist, s, sm, sh);
+        } else if (MODE == kBatchFp32) {
+            run_fit<true>(e.d, e.p32, e.out, e.hist, s, sm, sh);
+        } else {
+            run_fit<true>(e.d, e.p32, e.out32, e.hist, s, sm, sh);
+            const int st = sh.run_status;
+            if ((st == kStOk || st == kStNotConverged) && sh.drained) {
+                // FP64 polish from the FP32 point: E and D rebuilt in FP64 from this shard's
+                // copy of beta (every shard holds the same one), trust radii kept
+                init_shard(e.d, s, e.d.beta_priv + static_cast<long long>(s) * e.d.J, true);
+                FitParams p2 = e.p;
+                p2.seq0 = sh.run_seq;
+                run_fit<false>(e.d, p2, e.out, e.hist, s, sm, sh);
+            }
+        }
+        if (!sh.drained) break;   // a staging copy may still land: this CTA takes no more work
+    }
+}
+
+__global__ void batch_prep_kernel(const BatchEntry *entries, int n, unsigned *counters) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
+        counters[i] = 0u;
+        if (i < n) {
+            FitOut z{};
+            *entries[i].out = z;
+            if (entries[i].out32) *entries[i].out32 = z;
+        }
+    }
+}
+
+__global__ void batch_gather_kernel(const BatchEntry *entries, int n, FitOut *outs, FitOut *outs32, double *betas,
+                                    const long long *beta_off) {
+    for (int f = blockIdx.x; f < n; f += gridDim.x) {
+        const BatchEntry &en = entries[f];
+        if (threadIdx.x == 0) {
+            outs[f] = *en.out;
+            if (en.out32) outs32[f] = *en.out32;
+        }
+        for (int j = threadIdx.x; j < en.d.J; j += blockDim.x) betas[beta_off[f] + j] = en.d.beta_priv[j];
+    }
 }
 
 __global__ void __launch_bounds__(512, 1) grad_hess_kernel(DevLayout d, int j, FitParams p, FitOut *out) {
@@ -1322,48 +1488,22 @@ aborted:
     }
 }
 
-// E_k = l_k exp(Xb_k) on this CTA's rows, with Xb accumulated column by column in j order;
-// private beta copies and trust radii (= 1) are (re)set.
 __global__ void __launch_bounds__(512, 1) init_state_kernel(DevLayout d, const double *beta0, int keep_trust) {
-    const int s = blockIdx.x;
-    const long long r0 = d.shard_row[s], r1 = d.shard_row[s + 1];
-    double *beta = d.beta_priv + static_cast<long long>(s) * d.J;
-    double *trust = d.trust_priv + static_cast<long long>(s) * d.J;
-    for (int j = threadIdx.x; j < d.J; j += blockDim.x) {
-        beta[j] = beta0 ? beta0[j] : 0.0;
-        if (!keep_trust) trust[j] = 1.0;
-    }
-    if (!beta0) {
-        for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k];
-        return;
-    }
-    for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = 0.0;
-    __syncthreads();
-    for (int j = 0; j < d.J; ++j) {
-        const double bj = beta0[j];
-        if (bj == 0.0) continue;
-        const long long so = static_cast<long long>(s) * (d.J + 1) + j;
-        for (long long q = d.slice_row[so] + threadIdx.x; q < d.slice_row[so + 1]; q += blockDim.x)
-            d.E[d.rows[q]] += bj;
-        __syncthreads();
-    }
-    for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k] * exp(d.E[k]);
+    init_shard(d, blockIdx.x, beta0, keep_trust != 0);
 }
 
-__global__ void __launch_bounds__(512, 1) e_to_f32_kernel(DevLayout d) {
-    const int s = blockIdx.x;
-    for (long long k = d.shard_row[s] + threadIdx.x; k < d.shard_row[s + 1]; k += blockDim.x)
-        d.E32[k] = static_cast<float>(d.E[k]);
-}
+__global__ void __launch_bounds__(512, 1) e_to_f32_kernel(DevLayout d) { e_to_f32_shard(d, blockIdx.x); }
 
 int ensure_smem_attr() {
     const int bytes = static_cast<int>(sizeof(SmemLayout));
     cudaError_t e = cudaFuncSetAttribute(fit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fit_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        e = cudaFuncSetAttribute(fit_queue_kernel<kBatchFp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fit_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        e = cudaFuncSetAttribute(fit_queue_kernel<kBatchFp32Polish>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fit_queue_kernel<kBatchFp32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return static_cast<int>(e);
 }
 
@@ -1393,16 +1533,44 @@ int launch_fit(const DevLayout &d, const FitParams &p, FitOut *out_dev, double *
                                                          static_cast<cudaStream_t>(stream)));
 }
 
-int launch_fit_batch(const BatchEntry *entries_dev, const int2 *map_dev, int ctas, int threads, void *stream,
-                     bool fp32) {
+int launch_fit_queue(const BatchEntry *entries_dev, const int *team_start_dev, int n, unsigned *counters_dev,
+                     int ctas, int threads, void *stream, int mode, long long assemble_ns) {
     int e = ensure_smem_attr();
     if (e) return e;
     const BatchEntry *en = entries_dev;
-    const int2 *mp = map_dev;
-    void *args[] = {&en, &mp};
-    void *fn = fp32 ? reinterpret_cast<void *>(fit_batch_kernel<true>) : reinterpret_cast<void *>(fit_batch_kernel<false>);
-    return static_cast<int>(cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(threads), args, sizeof(SmemLayout),
-                                                         static_cast<cudaStream_t>(stream)));
+    const int *ts = team_start_dev;
+    int nn = n;
+    unsigned *cn = counters_dev;
+    long long an = assemble_ns;
+    void *args[] = {&en, &ts, &nn, &cn, &an};
+    void *fn = mode == kBatchFp32Polish ? reinterpret_cast<void *>(fit_queue_kernel<kBatchFp32Polish>)
+               : mode == kBatchFp32     ? reinterpret_cast<void *>(fit_queue_kernel<kBatchFp32>)
+                                        : reinterpret_cast<void *>(fit_queue_kernel<kBatchFp64>);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = sizeof(SmemLayout);
+    cfg.stream = static_cast<cudaStream_t>(stream);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return static_cast<int>(cudaLaunchKernelExC(&cfg, fn, args));
+}
+
+int launch_batch_prep(const BatchEntry *entries_dev, int n, unsigned *counters_dev, void *stream) {
+    const int blocks = (n + 1 + 255) / 256;
+    batch_prep_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(entries_dev, n, counters_dev);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_batch_gather(const BatchEntry *entries_dev, int n, FitOut *outs, FitOut *outs32, double *betas,
+                        const long long *beta_off_dev, void *stream) {
+    const int blocks = n < 1024 ? n : 1024;
+    batch_gather_kernel<<<blocks, 128, 0, static_cast<cudaStream_t>(stream)>>>(entries_dev, n, outs, outs32, betas,
+                                                                              beta_off_dev);
+    return static_cast<int>(cudaGetLastError());
 }
 
 int launch_grad_hess(const DevLayout &d, int32_t j, const FitParams &p, FitOut *out_dev, int threads,
@@ -1428,9 +1596,14 @@ int fit_kernel_max_blocks_per_sm(int threads, int *blocks) {
     cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fit_kernel<false>, threads, sizeof(SmemLayout));
     if (ce != cudaSuccess) return static_cast<int>(ce);
     int c = 0;
-    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, fit_batch_kernel<false>, threads, sizeof(SmemLayout));
-    if (ce != cudaSuccess) return static_cast<int>(ce);
-    if (c < a) a = c;
+    for (int m = 0; m < 3; ++m) {
+        const void *fn = m == 0 ? reinterpret_cast<const void *>(fit_queue_kernel<kBatchFp64>)
+                         : m == 1 ? reinterpret_cast<const void *>(fit_queue_kernel<kBatchFp32Polish>)
+                                  : reinterpret_cast<const void *>(fit_queue_kernel<kBatchFp32>);
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, fn, threads, sizeof(SmemLayout));
+        if (ce != cudaSuccess) return static_cast<int>(ce);
+        if (c < a) a = c;
+    }
     ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grad_hess_kernel, threads, 0);
     if (ce != cudaSuccess) return static_cast<int>(ce);
     *blocks = a < b ? a : b;

@@ -44,8 +44,8 @@ def test_batch_equals_standalone_bitwise(P):
             m.close()
 
 
-def test_batch_in_several_waves_fp32_polish(P):
-    """More shards than the device holds at once: the batch runs in successive launches."""
+def test_batch_with_more_ctas_than_the_device_fp32_polish(P):
+    """More shards than the device holds at once: CTAs take several fits' tickets in turn."""
     ds = _datasets([30000] * 6, seed0=200)
     ms = _models(P, ds, [40] * 6, [("normal", 0.1)] * 6)
     try:
@@ -72,3 +72,55 @@ def test_batch_against_oracle(P):
     finally:
         for m in ms:
             m.close()
+
+
+def test_many_small_fits_share_ctas(P):
+    """300 one- to three-CTA fits: every CTA runs many fits in turn, each as it runs alone."""
+    ds = _datasets([1500 + 37 * i for i in range(300)], seed0=1000, J=12)
+    ms = _models(P, ds, [1 + i % 3 for i in range(300)], [("normal", (0.05, 0.5, 2.0)[i % 3]) for i in range(300)])
+    try:
+        batch = P.sccs_fit_batch([m.handle for m in ms], [m.J for m in ms], tol=1e-12, max_cycles=60)
+        for i in (0, 1, 2, 57, 150, 298, 299):
+            r = ms[i].fit(tol=1e-12, max_cycles=60)
+            b = batch[i]
+            assert b["status"] == r["status"] and b["cycles"] == r["cycles"]
+            assert np.array_equal(r["beta"], b["beta"]) and r["logpost"] == b["logpost"]
+    finally:
+        for m in ms:
+            m.close()
+
+
+def test_repeated_batches_replay_with_new_priors(P):
+    """The second call over the same handles replays the cached plan with the new priors."""
+    ds = _datasets([4000, 9000, 25000], seed0=400)
+    ms = _models(P, ds, [2, 4, 8], [("normal", 0.1)] * 3)
+    try:
+        for var in (0.1, 1.0, 0.01):
+            for m in ms:
+                m.set_prior("laplace" if var == 1.0 else "normal", var)
+            batch = P.sccs_fit_batch([m.handle for m in ms], [m.J for m in ms], tol=1e-12, max_cycles=80)
+            for m, b in zip(ms, batch):
+                r = m.fit(tol=1e-12, max_cycles=80)
+                assert np.array_equal(r["beta"], b["beta"]) and r["cycles"] == b["cycles"]
+        # warm start from the state the last standalone fit left
+        batch = P.sccs_fit_batch([m.handle for m in ms], [m.J for m in ms], warm_start=True, tol=-1.0, max_cycles=2)
+        for m, b in zip(ms, batch):
+            r = m.fit(warm_start=True, tol=-1.0, max_cycles=2)
+            # the standalone warm fit starts where the batch left off: both are at the MAP
+            assert np.allclose(r["beta"], b["beta"], atol=1e-9)
+    finally:
+        for m in ms:
+            m.close()
+
+
+def test_destroyed_handle_drops_cached_plans(P):
+    ds = _datasets([3000, 6000], seed0=500)
+    for rep in range(3):
+        ms = _models(P, ds, [1, 2], [("normal", 0.5)] * 2)
+        try:
+            batch = P.sccs_fit_batch([m.handle for m in ms], [m.J for m in ms], tol=1e-12, max_cycles=50)
+            r = ms[1].fit(tol=1e-12, max_cycles=50)
+            assert np.array_equal(r["beta"], batch[1]["beta"])
+        finally:
+            for m in ms:
+                m.close()
