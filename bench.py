@@ -319,6 +319,294 @@ def cpu_baseline(d, fit):
                       f"serial FP64 C oracle, {dt:.1f} s"}
 
 
+# ------------------------------------------------------------------ batched and served fits
+
+def _spawn_pool(workers: int):
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    return ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_sample_batched(plan, f, cycles):
+    """Pool worker: draw fit f of the batch and time `cycles` cycles of the serial oracle on it."""
+    import oracle
+    from synth import batched_fit_one
+    d, fit = batched_fit_one(plan, f)
+    prob = oracle.Problem.from_data(d)
+    t0 = time.perf_counter()
+    prob.fit(prior=fit["prior"], variance=fit["variance"], fixed_cycles=cycles)
+    return f, int(d.nnz), time.perf_counter() - t0
+
+
+def _est_nnz_batched(plan, f):
+    return float(plan["sizes"][f]) * 8.0 * float(np.sum(plan["dens"]))
+
+
+def run_batched(args, rank, world, local):
+    """One step = one batched launch of all the batch's fits from beta = 0 to convergence."""
+    import ctypes
+    from synth import batched_fit_plan, batched_fit_one
+    import oracle
+
+    plan = batched_fit_plan(n_fits=args.fits, max_subjects=args.max_subjects)
+    n = args.fits
+    cores = _host_cores()
+    # oracle sample first (host cores only, before the GPU is touched): one fit per core,
+    # spread over the size range, 2 cycles each
+    cpu_sample = []
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oracle.build()
+        by_size = np.argsort(plan["sizes"])
+        pick = sorted(set(int(by_size[int(round(q))]) for q in np.linspace(0, n - 1, min(cores, n))))
+        t0 = time.perf_counter()
+        with _spawn_pool(min(cores, len(pick))) as ex:
+            cpu_sample = list(ex.map(_oracle_sample_batched, [plan] * len(pick), pick, [2] * len(pick)))
+        cpu_wall = time.perf_counter() - t0
+
+    import torch
+    import paper_1208_0945_gb300 as sccs
+    from paper_1208_0945_gb300 import autotune
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    model = autotune.measure(local)
+    est = [(int(plan["J"]), _est_nnz_batched(plan, f), 0.9 * _est_nnz_batched(plan, f)) for f in range(n)]
+    teams = autotune.assign(est, model)
+
+    # draw the fits in parallel and keep two resident copies of each: the autotuned team for
+    # the batch, and the library's default shard count for one-at-a-time fits
+    stream = torch.cuda.current_stream(dev)
+    cst = ctypes.c_void_p(stream.cuda_stream)
+    batch_m, plain_m, infos, fits = [], [], [], []
+    t_gen = time.perf_counter()
+    with _spawn_pool(min(cores, 16)) as ex:
+        for f, (d, fit) in enumerate(ex.map(batched_fit_one, [plan] * n, range(n))):
+            mb = sccs.SCCSModel(d, device=local, stream=cst, num_shards=teams[f])
+            mb.set_prior(fit["prior"], fit["variance"])
+            mp_ = sccs.SCCSModel(d, device=local, stream=cst)
+            mp_.set_prior(fit["prior"], fit["variance"])
+            batch_m.append(mb)
+            plain_m.append(mp_)
+            infos.append(mb.info)
+            fits.append(fit)
+    t_gen = time.perf_counter() - t_gen
+    fkw = dict(tol_mode="rel_logpost", tol=1e-12, max_cycles=1000)
+    handles = [m.handle for m in batch_m]
+    Js = [m.J for m in batch_m]
+
+    for _ in range(args.warmup):
+        sccs.sccs_fit_batch(handles, Js, **fkw)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    step_ms, walls, res = [], [], None
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            res = sccs.sccs_fit_batch(handles, Js, **fkw)
+            walls.append(1e3 * (time.perf_counter() - t0))
+            step_ms.append(res[0]["kernel_ms"])
+    barrier(world)
+    clocks = clk.summary()
+    ms = reduce_max(statistics.mean(step_ms), world, dev)
+    value = reduce_sum(float(n), world, dev) / (ms / 1e3)
+
+    # the same fits one at a time (plain sccs_fit, default shards), once
+    plain_m[0].fit(**fkw)
+    seq_ms, seq_wall, seq_res = 0.0, 0.0, []
+    torch.cuda.synchronize(dev)
+    for m in plain_m:
+        t0 = time.perf_counter()
+        r = m.fit(**fkw)
+        seq_wall += time.perf_counter() - t0
+        seq_ms += r["kernel_ms"]
+        seq_res.append(r)
+    seq_ms = reduce_max(seq_ms, world, dev)
+    same_cycles = sum(1 for a, b in zip(res, seq_res) if a["cycles"] == b["cycles"])
+    max_dlogpost = max(abs(a["logpost"] - b["logpost"]) / max(1.0, abs(b["logpost"])) for a, b in zip(res, seq_res))
+
+    total_bytes = 0.0
+    for info, r in zip(infos, res):
+        nz = r["nonzero_steps"] / max(1, r["steps"])
+        total_bytes += algorithmic_bytes(info, r["cycles"], nz)
+    peak, peak_kind = load_peaks()
+    achieved = total_bytes / (statistics.mean(step_ms) / 1e3) / 1e9
+
+    cpu = None
+    if cpu_sample:
+        # oracle seconds per nonzero-cycle on the sample, applied to every fit's nonzeros and
+        # the cycles the GPU needed, spread over the host cores
+        rate = sum(2.0 * nz for _, nz, _ in cpu_sample) / sum(dt for _, _, dt in cpu_sample)
+        cpu_s = sum(info["nnz_kept"] * r["cycles"] for info, r in zip(infos, res)) / rate / cores
+        cpu = {"value": n / cpu_s, "unit": "fits/s", "cores": cores, "kind": "oracle",
+               "sample": f"serial FP64 C oracle, 2 cycles on each of {len(cpu_sample)} fits spread over the "
+                         f"size range, one fit per process on {min(cores, len(cpu_sample))} cores "
+                         f"({cpu_wall:.1f} s wall); extrapolated to all {n} fits by nonzeros x the cycles "
+                         f"each fit needed, divided over {cores} cores"}
+    if rank == 0:
+        line = {
+            "metric": "batched SCCS MAP fits/s (FP64, one persistent graph-captured launch)",
+            "value": value, "unit": "fits/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator)", "workload": "batched",
+            "config": {"workload": f"batched: {n} independent SCCS fits, subjects log-uniform 2k-"
+                                   f"{args.max_subjects // 1000}k, eras geometric mean 8, {plan['J']} drugs "
+                                   "with shared densities U[0.5%,5%], Normal prior var 0.01/0.1/1 in turn, "
+                                   "FP64, rel |dP| < 1e-12; team sizes from the autotuner",
+                       "fits": n, "subjects": int(sum(i["subjects_kept"] for i in infos)),
+                       "eras": int(sum(i["rows_kept"] for i in infos)),
+                       "nnz": int(sum(i["nnz_kept"] for i in infos)),
+                       "teams": {"min": int(min(teams)), "max": int(max(teams)), "sum": int(sum(teams))},
+                       "seed": int(plan["seed"]), "l2": "256 MB buffer written between timed steps (L2 flushed)"},
+            "batch": {"kernel_ms": statistics.mean(step_ms), "wall_ms": statistics.mean(walls),
+                      "cycles_total": int(sum(r["cycles"] for r in res)),
+                      "setup_s": t_gen},
+            "one_at_a_time": {"fits_per_s": n / (seq_ms / 1e3), "kernel_ms": seq_ms, "wall_s": seq_wall,
+                              "speedup_of_batch": seq_ms / ms,
+                              "same_cycles": f"{same_cycles}/{n}",
+                              "max_rel_logpost_diff": max_dlogpost},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "fit_queue_kernel (one launch per batch)",
+                         "algorithmic_bytes_per_launch": total_bytes, "peak_source": peak_kind},
+            "e2e": {"value": n / (statistics.mean(walls) / 1e3), "unit": "fits/s",
+                    "h2d_bytes_per_step": None, "d2h_bytes_per_step": int(sum(8 * J for J in Js)),
+                    "what": "sccs_fit_batch wall time: per-fit entries staged, graph launched, results and betas "
+                            "copied back (datasets resident)"},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    for m in batch_m + plain_m:
+        m.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, budget, seed0):
+    """Submit each rate's Poisson arrivals to a fresh server and collect latencies."""
+    from synth import serving_requests
+    rows = []
+    for ri, rate in enumerate(rates):
+        reqs = serving_requests(n_per_rate, rate, len(Js), seed=seed0 + ri)
+        with sccs.FitServer(device=device, max_inflight=max_inflight, hbm_budget_bytes=budget) as srv:
+            tickets = []
+            t0 = time.perf_counter()
+            for (ta, o, prior, var, _fold) in reqs:
+                dt = t0 + ta - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append(sccs.sccs_submit(srv.server, handles_of[o], prior=prior, variance=var,
+                                                tol_mode="rel_logpost", tol=1e-12, max_cycles=1000))
+            out = []
+            for t, (ta, o, *_rest) in zip(tickets, reqs):
+                while True:
+                    r = sccs.sccs_poll(srv.server, t, Js[o])
+                    if r is not None:
+                        break
+                    time.sleep(0.0005)
+                out.append(r)
+            t_end = time.perf_counter()
+        lat = np.array([r["latency_ms"] for r in out])
+        done_span = (t_end - t0)
+        rows.append({"rate_per_s": rate, "requests": n_per_rate,
+                     "fits_per_s": n_per_rate / done_span,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "mean_queue_ms": float(np.mean([r["queue_ms"] for r in out])),
+                     "failed": int(sum(1 for r in out if r["status"] < 0))})
+    return rows
+
+
+def run_serving(args, rank, world, local):
+    """Poisson-arrival fit requests over a pool of resident outcomes, served with continuous
+    batching, beside the same arrivals served one fit at a time."""
+    import ctypes
+    from synth import serving_pool_plan, serving_outcome
+    import torch
+    import paper_1208_0945_gb300 as sccs
+    from paper_1208_0945_gb300 import autotune
+
+    plan = serving_pool_plan(n_outcomes=args.outcomes, max_eras=args.max_eras)
+    cores = _host_cores()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    model = autotune.measure(local)
+    stream = torch.cuda.current_stream(dev)
+    cst = ctypes.c_void_p(stream.cuda_stream)
+    served, plain, infos = [], [], []
+    t_gen = time.perf_counter()
+    with _spawn_pool(min(cores, 16)) as ex:
+        ds = list(ex.map(serving_outcome, [plan] * args.outcomes, range(args.outcomes)))
+    est = [(d.J, d.nnz, 0.9 * d.nnz) for d in ds]
+    teams = autotune.assign(est, model)
+    for d, S in zip(ds, teams):
+        served.append(sccs.SCCSModel(d, device=local, stream=cst, num_shards=S))
+        plain.append(sccs.SCCSModel(d, device=local, stream=cst))
+        infos.append(served[-1].info)
+    del ds
+    t_gen = time.perf_counter() - t_gen
+    Js = [m.J for m in served]
+    rates = [float(x) for x in args.rates.split(",")]
+    budget = int(args.hbm_budget_gb * (1 << 30))
+    # warm-up: one request per outcome through each arm
+    for arm in (served, plain):
+        _serve_sweep(sccs, local, [m.handle for m in arm], Js, [1000.0], min(args.outcomes, 8), 64, budget, 999)
+    with ClockSampler(local) as clk:
+        ours = _serve_sweep(sccs, local, [m.handle for m in served], Js, rates, args.requests, 64, budget, 2000)
+    clocks = clk.summary()
+    one = _serve_sweep(sccs, local, [m.handle for m in plain], Js, rates, args.requests, 1, 0, 2000)
+    top = ours[-1]
+    if rank == 0:
+        line = {
+            "metric": "served SCCS MAP fits/s and p50/p99 latency (FP64, Poisson arrivals, continuous batching)",
+            "value": top["fits_per_s"], "unit": "fits/s", "n_gpus": world, "steps": len(rates),
+            "warmup": 1, "ms_per_step": 1e3 / top["fits_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)", "workload": "serving",
+            "config": {"workload": f"serving: {args.outcomes} resident outcomes, eras log-uniform 20k-"
+                                   f"{args.max_eras / 1e6:g}M, 1000-5000 drugs, Zipf(1.2) columns up to eras/5; "
+                                   "requests = outcome x Normal/Laplace x variance grid "
+                                   "{0.01..1}, FP64 to rel |dP| < 1e-12; "
+                                   f"{args.requests} Poisson arrivals per rate",
+                       "outcomes": args.outcomes, "eras": int(sum(i["rows_kept"] for i in infos)),
+                       "nnz": int(sum(i["nnz_kept"] for i in infos)), "rates_per_s": rates,
+                       "teams": {"min": int(min(teams)), "max": int(max(teams))},
+                       "max_inflight": 64, "hbm_budget_gb": args.hbm_budget_gb, "setup_s": t_gen},
+            "sweep": ours,
+            "one_at_a_time": one,
+            "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"],
+            "roofline": None,
+            "e2e": {"value": top["fits_per_s"], "unit": "fits/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(8 * np.mean(Js)),
+                    "what": "submit -> poll through the C ABI, datasets resident; the value itself is end to end"},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    for m in served + plain:
+        m.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,10 +615,30 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's subjects")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fit", choices=["fit", "batched", "serving"],
+                    help="fit: one full MAP fit per step (default); batched: all fits of a batch in one "
+                         "launch per step; serving: Poisson-arrival requests over resident outcomes")
+    ap.add_argument("--fits", type=int, default=256, help="batched: fits per batch")
+    ap.add_argument("--max-subjects", type=int, default=500_000, help="batched: largest fit's subjects")
+    ap.add_argument("--outcomes", type=int, default=32, help="serving: resident outcomes")
+    ap.add_argument("--max-eras", type=float, default=20e6, help="serving: largest outcome's eras")
+    ap.add_argument("--rates", default="1,2,5,10,20,50,100,200", help="serving: arrival rates per second")
+    ap.add_argument("--requests", type=int, default=32, help="serving: requests per rate")
+    ap.add_argument("--hbm-budget-gb", type=float, default=48.0, help="serving: fit-slot memory budget")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
+        if args.workload != "fit":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "workload": args.workload,
+                                  "unavailable": "the oracle arm times the single-fit workload; batched and "
+                                                 "serving lines carry their own oracle sample"}), flush=True)
+            return 0
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        return run_batched(args, rank, world, local)
+    if args.workload == "serving":
+        return run_serving(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

@@ -11,5 +11,11 @@ from .sccs_synth import (  # noqa: F401
     mid_fit_config,
     paper_scale_config,
     batched_fit_configs,
+    batched_fit_plan,
+    batched_fit_one,
+    serving_pool_plan,
+    serving_outcome,
+    serving_requests,
+    PRIOR_VARIANCE_GRID,
     CONFIGS,
 )

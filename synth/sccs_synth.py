@@ -245,16 +245,62 @@ def batched_fit_configs(n_fits: int = 64, min_subjects: int = 2000, max_subjects
     [min_subjects, max_subjects], eras geometric with mean 8, J binary drugs whose densities
     (uniform 0.5-5%) are shared by all fits while the rows are drawn per fit, 3 true effects
     per fit, Normal prior variance 0.01 / 0.1 / 1 in turn."""
+    plan = batched_fit_plan(n_fits, min_subjects, max_subjects, J, seed)
+    return [batched_fit_one(plan, f) for f in range(n_fits)]
+
+
+def batched_fit_plan(n_fits: int = 256, min_subjects: int = 2000, max_subjects: int = 500_000, J: int = 500,
+                     seed: int = 1211) -> dict:
+    """What batched_fit_one needs to draw fit f of a batch on its own (for parallel drawing)."""
     rng = np.random.default_rng(seed)
     sizes = np.exp(rng.uniform(np.log(min_subjects), np.log(max_subjects), size=n_fits)).astype(int)
     dens = rng.uniform(0.005, 0.05, size=J)
+    return dict(sizes=sizes, dens=dens, J=J, seed=seed)
+
+
+def batched_fit_one(plan: dict, f: int):
+    """Fit f of a batch: the same draw as batched_fit_configs gives for f."""
+    d = make_dataset(n_patients=int(plan["sizes"][f]), eras=("geometric", 8), J=plan["J"],
+                     columns=("densities", plan["dens"]), n_true=3, beta_sd=0.5, seed=plan["seed"] * 1000 + f,
+                     name=f"batched-fit-{f}")
+    fit = dict(prior="normal", variance=(0.01, 0.1, 1.0)[f % 3], tol_mode="rel_logpost", tol=1e-12,
+               max_cycles=1000)
+    return d, fit
+
+
+PRIOR_VARIANCE_GRID = (0.01, 0.02, 0.05, 0.1, 0.2, 0.5, 1.0)
+
+
+def serving_pool_plan(n_outcomes: int = 32, min_eras: int = 20_000, max_eras: int = 20_000_000,
+                      min_drugs: int = 1000, max_drugs: int = 5000, seed: int = 1212) -> dict:
+    """Outcomes a fit server holds: eras log-uniform in [min_eras, max_eras] (subjects = eras / 10,
+    geometric eras with mean 10), drugs uniform in [min_drugs, max_drugs], columns drawn like
+    the 1M-subject workload's (Zipf(1.2) sizes from 10 up to eras / 5)."""
+    rng = np.random.default_rng(seed)
+    eras = np.exp(rng.uniform(np.log(min_eras), np.log(max_eras), size=n_outcomes))
+    drugs = rng.integers(min_drugs, max_drugs + 1, size=n_outcomes)
+    return dict(eras=eras, drugs=drugs, seed=seed)
+
+
+def serving_outcome(plan: dict, o: int) -> SCCSData:
+    K = float(plan["eras"][o])
+    n = max(int(round(K / 10.0)), 100)
+    b = max(K / 5.0, 20.0)
+    return make_dataset(n_patients=n, eras=("geometric", 10), J=int(plan["drugs"][o]), columns=("zipf", 1.2, 10, b),
+                        n_true=20, beta_sd=0.5, seed=plan["seed"] * 1000 + o, name=f"served-outcome-{o}")
+
+
+def serving_requests(n_requests: int, rate_per_s: float, n_outcomes: int, seed: int = 1213, folds: int = 0) -> list:
+    """Poisson arrivals at `rate_per_s`: (arrival time s, outcome, prior, variance, fold) with the
+    prior Normal or Laplace at even odds and the variance drawn from PRIOR_VARIANCE_GRID; fold is
+    uniform in 1..folds (0 when folds = 0, a fit on all subjects)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n_requests))
     out = []
-    for f in range(n_fits):
-        d = make_dataset(n_patients=int(sizes[f]), eras=("geometric", 8), J=J, columns=("densities", dens),
-                         n_true=3, beta_sd=0.5, seed=seed * 1000 + f, name=f"batched-fit-{f}")
-        fit = dict(prior="normal", variance=(0.01, 0.1, 1.0)[f % 3], tol_mode="rel_logpost", tol=1e-12,
-                   max_cycles=1000)
-        out.append((d, fit))
+    for k in range(n_requests):
+        out.append((float(t[k]), int(rng.integers(n_outcomes)), "normal" if rng.random() < 0.5 else "laplace",
+                    float(PRIOR_VARIANCE_GRID[rng.integers(len(PRIOR_VARIANCE_GRID))]),
+                    int(rng.integers(1, folds + 1)) if folds > 0 else 0))
     return out
 
 
