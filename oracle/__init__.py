@@ -10,6 +10,9 @@ Functions follow the paper (Suchard et al., arXiv 1208.0945):
   grad_hess   Eqs. 7-9 from scratch at a given beta (log-likelihood derivatives only)
   fit         Algorithm 1 with the Newton step of Eq. 4, a Genkin trust region and the
               Section 2.3 sparse updates of Xb, L x exp(Xb) and M[L x exp(Xb)]
+  weights=    (loglik, grad_hess, fit) Section 2.5's resampling: subject i counted w_i times,
+              the bootstrap's multiplicities or a cross-validation fold's 0/1 mask; the
+              held-out predictive log-likelihood is loglik with the fold's mask
 Readings of points the paper leaves open are listed at the top of ``sccs_oracle.c``.
 """
 from __future__ import annotations
@@ -79,6 +82,17 @@ def _bind(lib):
     lib.oracle_fit.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                ctypes.c_int, P, f64p, f64p, ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_subjects_in.restype = ctypes.c_int64
+    lib.oracle_subjects_in.argtypes = [P]
+    lib.oracle_loglik_w.restype = ctypes.c_double
+    lib.oracle_loglik_w.argtypes = [P, f64p, P]
+    lib.oracle_grad_hess_w.restype = ctypes.c_int
+    lib.oracle_grad_hess_w.argtypes = [P, f64p, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+    lib.oracle_fit_w.restype = ctypes.c_int
+    lib.oracle_fit_w.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_int, P, P, f64p, f64p, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
     return lib
 
 
@@ -112,6 +126,7 @@ class Problem:
         dims = np.zeros(6, np.int64)
         lib.oracle_dims(self._p, dims)
         self.K, self.N, self.J, self.nnz, self.dropped_patients, self.dropped_rows = (int(v) for v in dims)
+        self.subjects_in = int(lib.oracle_subjects_in(self._p))
 
     @classmethod
     def from_data(cls, d, lib=None) -> "Problem":
@@ -128,22 +143,39 @@ class Problem:
         assert b.shape == (self.J,)
         return b
 
-    def loglik(self, beta=None) -> float:
+    def _w(self, weights):
+        """Subject weights (R9), one non-negative integer per input subject; None = all 1."""
+        if weights is None:
+            return None, None
+        w = np.ascontiguousarray(weights, np.int64)
+        assert w.shape == (self.subjects_in,) and (w >= 0).all()
+        return w, w.ctypes.data
+
+    def loglik(self, beta=None, weights=None) -> float:
+        if weights is not None:
+            w, wp = self._w(weights)
+            return float(self._lib.oracle_loglik_w(self._p, self._beta(beta), wp))
         return float(self._lib.oracle_loglik(self._p, self._beta(beta)))
 
     def logpost(self, beta=None, prior="normal", variance=1.0) -> float:
         return float(self._lib.oracle_logpost(self._p, self._beta(beta), PRIOR[prior], float(variance)))
 
-    def grad_hess(self, j: int, beta=None) -> tuple[float, float]:
+    def grad_hess(self, j: int, beta=None, weights=None) -> tuple[float, float]:
         g, h = ctypes.c_double(), ctypes.c_double()
-        rc = self._lib.oracle_grad_hess(self._p, self._beta(beta), int(j), ctypes.byref(g), ctypes.byref(h))
+        if weights is not None:
+            w, wp = self._w(weights)
+            rc = self._lib.oracle_grad_hess_w(self._p, self._beta(beta), int(j), wp, ctypes.byref(g),
+                                              ctypes.byref(h))
+        else:
+            rc = self._lib.oracle_grad_hess(self._p, self._beta(beta), int(j), ctypes.byref(g), ctypes.byref(h))
         if rc != OK:
             raise OracleError(rc, "grad_hess")
         return g.value, h.value
 
     def fit(self, prior="normal", variance=1.0, tol_mode="abs_logpost", tol=1e-10,
-            max_cycles=1000, beta0=None, fixed_cycles: int | None = None) -> dict:
-        """Algorithm 1.  fixed_cycles=T runs exactly T cycles (no convergence test)."""
+            max_cycles=1000, beta0=None, fixed_cycles: int | None = None, weights=None) -> dict:
+        """Algorithm 1.  fixed_cycles=T runs exactly T cycles (no convergence test); weights (R9)
+        count subject i w_i times (per input subject; None = all 1)."""
         if fixed_cycles is not None:
             max_cycles, tol = int(fixed_cycles), -1.0
         beta = np.zeros(self.J)
@@ -155,9 +187,15 @@ class Problem:
         if beta0 is not None:
             b0 = np.ascontiguousarray(beta0, np.float64)
             assert b0.shape == (self.J,)
-        rc = self._lib.oracle_fit(self._p, PRIOR[prior], float(variance), TOL[tol_mode], float(tol),
-                                  int(max_cycles), None if b0 is None else b0.ctypes.data, beta, hist,
-                                  ctypes.byref(cyc), ctypes.byref(nz), ctypes.byref(warn))
+        if weights is not None:
+            w, wp = self._w(weights)
+            rc = self._lib.oracle_fit_w(self._p, PRIOR[prior], float(variance), TOL[tol_mode], float(tol),
+                                        int(max_cycles), None if b0 is None else b0.ctypes.data, wp, beta, hist,
+                                        ctypes.byref(cyc), ctypes.byref(nz), ctypes.byref(warn))
+        else:
+            rc = self._lib.oracle_fit(self._p, PRIOR[prior], float(variance), TOL[tol_mode], float(tol),
+                                      int(max_cycles), None if b0 is None else b0.ctypes.data, beta, hist,
+                                      ctypes.byref(cyc), ctypes.byref(nz), ctypes.byref(warn))
         if rc < 0:
             raise OracleError(rc, "fit")
         t = cyc.value

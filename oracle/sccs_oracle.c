@@ -35,6 +35,13 @@
  *   R7 the denominators M[L x exp(Xb)] are recomputed from L x exp(Xb) at the end of every
  *      cycle (the incremental update accumulates rounding otherwise).
  *   R8 subjects with n_i = 0 contribute nothing (Section 2.1) and are removed up front.
+ *   R9 subject weights (Section 2.5): a non-negative integer w_i per input subject stands for
+ *      subject i appearing w_i times.  The bootstrap's resample with replacement gives the
+ *      multiplicities; a cross-validation fit on the other folds gives w_i = 1 outside the
+ *      held-out fold and 0 inside it; the predictive log-likelihood of the held-out fold is
+ *      Eq. 2 summed over that fold's subjects, i.e. weights 1 on the fold and 0 elsewhere.
+ *      Weighted, Eq. 2 reads  L_w(b) = sum_i w_i [ sum_k y_ik x_ik'b - n_i log sum_k l_ik e^{x_ik'b} ],
+ *      so Y'X_j becomes sum_k w_i(k) y_k x_kj and n_i becomes w_i n_i in Eqs. 7-9.
  */
 #include <math.h>
 #include <stdint.h>
@@ -70,6 +77,8 @@ typedef struct {
     int64_t *col_ptr; /* J+1 */
     int64_t *rows;    /* nnz: rows of each column, ascending */
     int64_t *ytx;     /* J: Y'X_j (Eq. 7, first term) */
+    int64_t *sub_in;  /* N: input subject index of each kept subject (R9 weights are per input subject) */
+    int64_t n_in;     /* input subjects */
     int64_t dropped_patients, dropped_rows;
 } oracle_problem;
 
@@ -78,7 +87,7 @@ static void *xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz ? sz : 1
 void oracle_free(oracle_problem *p) {
     if (!p) return;
     free(p->pat_ptr); free(p->row_pat); free(p->y); free(p->L); free(p->n);
-    free(p->col_ptr); free(p->rows); free(p->ytx);
+    free(p->col_ptr); free(p->rows); free(p->ytx); free(p->sub_in);
     free(p);
 }
 
@@ -135,7 +144,9 @@ oracle_problem *oracle_create(int64_t K, const int64_t *patient_id, const int32_
     p->n = (int64_t *)xcalloc((size_t)Nk, sizeof(int64_t));
     p->col_ptr = (int64_t *)xcalloc((size_t)J + 1, sizeof(int64_t));
     p->ytx = (int64_t *)xcalloc((size_t)J, sizeof(int64_t));
-    if (!p->pat_ptr || !p->row_pat || !p->y || !p->L || !p->n || !p->col_ptr || !p->ytx) {
+    p->sub_in = (int64_t *)xcalloc((size_t)Nk, sizeof(int64_t));
+    p->n_in = nsub;
+    if (!p->pat_ptr || !p->row_pat || !p->y || !p->L || !p->n || !p->col_ptr || !p->ytx || !p->sub_in) {
         free(sub_start); free(sub_n); free(newrow); oracle_free(p); *err = ORC_E_NOMEM; return NULL;
     }
     int64_t i2 = 0, k2 = 0;
@@ -146,6 +157,7 @@ oracle_problem *oracle_create(int64_t K, const int64_t *patient_id, const int32_
         }
         p->pat_ptr[i2] = k2;
         p->n[i2] = sub_n[i];
+        p->sub_in[i2] = i;
         for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) {
             newrow[k] = k2;
             p->row_pat[k2] = i2;
@@ -190,6 +202,26 @@ void oracle_dims(const oracle_problem *p, int64_t *out6) {
     out6[4] = p->dropped_patients; out6[5] = p->dropped_rows;
 }
 
+int64_t oracle_subjects_in(const oracle_problem *p) { return p->n_in; }
+
+/* R9: weight of kept subject i (1 without weights). */
+static int64_t weight_of(const oracle_problem *p, const int64_t *w_in, int64_t i) {
+    return w_in ? w_in[p->sub_in[i]] : 1;
+}
+
+/* R9: w_i n_i per kept subject and sum_k w_i(k) y_k x_kj per column, from their definitions. */
+static void weighted_counts(const oracle_problem *p, const int64_t *w_in, int64_t *wn, int64_t *wytx) {
+    for (int64_t i = 0; i < p->N; ++i) wn[i] = weight_of(p, w_in, i) * p->n[i];
+    for (int32_t j = 0; j < p->J; ++j) {
+        int64_t t = 0;
+        for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e) {
+            int64_t k = p->rows[e];
+            t += weight_of(p, w_in, p->row_pat[k]) * p->y[k];
+        }
+        wytx[j] = t;
+    }
+}
+
 /* Xb from scratch: for each column j, add b_j to its rows (column order ascending). */
 static void xbeta_from_scratch(const oracle_problem *p, const double *beta, double *xb) {
     for (int64_t k = 0; k < p->K; ++k) xb[k] = 0.0;
@@ -199,8 +231,9 @@ static void xbeta_from_scratch(const oracle_problem *p, const double *beta, doub
     }
 }
 
-/* Eq. 2, evaluated directly from its definition. */
-double oracle_loglik(const oracle_problem *p, const double *beta) {
+/* Eq. 2, evaluated directly from its definition; with weights (R9) each subject's term is
+ * counted w_i times (w_in: per input subject, NULL = all 1). */
+double oracle_loglik_w(const oracle_problem *p, const double *beta, const int64_t *w_in) {
     double *xb = (double *)xcalloc((size_t)p->K, sizeof(double));
     if (!xb) return NAN;
     xbeta_from_scratch(p, beta, xb);
@@ -211,11 +244,13 @@ double oracle_loglik(const oracle_problem *p, const double *beta) {
             lin += (double)p->y[k] * xb[k];
             den += p->L[k] * exp(xb[k]);
         }
-        total += lin - (double)p->n[i] * log(den);
+        total += (double)weight_of(p, w_in, i) * (lin - (double)p->n[i] * log(den));
     }
     free(xb);
     return total;
 }
+
+double oracle_loglik(const oracle_problem *p, const double *beta) { return oracle_loglik_w(p, beta, NULL); }
 
 /* log p(b) with every constant dropped (R3). */
 static double log_prior(int prior, double var, const double *beta, int32_t J) {
@@ -237,7 +272,8 @@ double oracle_logpost(const oracle_problem *p, const double *beta, int prior, do
 }
 
 /* Eqs. 7-9 from scratch at beta: W_i = sum_{k in X_j, k in i} l_k e^{Xb_k} / sum_{k in i} l_k e^{Xb_k}. */
-int oracle_grad_hess(const oracle_problem *p, const double *beta, int32_t j, double *g, double *h) {
+int oracle_grad_hess_w(const oracle_problem *p, const double *beta, int32_t j, const int64_t *w_in,
+                       double *g, double *h) {
     if (j < 0 || j >= p->J) return ORC_E_INVAL;
     double *xb = (double *)xcalloc((size_t)p->K, sizeof(double));
     double *D = (double *)xcalloc((size_t)p->N, sizeof(double));
@@ -250,15 +286,23 @@ int oracle_grad_hess(const oracle_problem *p, const double *beta, int32_t j, dou
         num[p->row_pat[k]] += p->L[k] * exp(xb[k]);
     }
     double nW = 0.0, nWW = 0.0;
+    int64_t ytx = 0;
+    for (int64_t e = p->col_ptr[j]; e < p->col_ptr[j + 1]; ++e)
+        ytx += weight_of(p, w_in, p->row_pat[p->rows[e]]) * p->y[p->rows[e]];
     for (int64_t i = 0; i < p->N; ++i) {
         double Wi = num[i] / D[i];
-        nW += (double)p->n[i] * Wi;
-        nWW += (double)p->n[i] * Wi * (1.0 - Wi);
+        double ni = (double)(weight_of(p, w_in, i) * p->n[i]);
+        nW += ni * Wi;
+        nWW += ni * Wi * (1.0 - Wi);
     }
-    *g = (double)p->ytx[j] - nW;
+    *g = (double)ytx - nW;
     *h = -nWW;
     free(xb); free(D); free(num);
     return ORC_OK;
+}
+
+int oracle_grad_hess(const oracle_problem *p, const double *beta, int32_t j, double *g, double *h) {
+    return oracle_grad_hess_w(p, beta, j, NULL, g, h);
 }
 
 /* The coordinate step of Eq. 4 under the prior (R2, R5) and the trust region (R1).
@@ -317,9 +361,9 @@ static double coordinate_step(double g, double h, double bj, int prior, double v
 
 /* Algorithm 1.  hist[0] = P(b0), hist[t] = P after cycle t (length max_cycles + 1).
  * tol < 0 runs exactly max_cycles cycles.  Returns ORC_OK, ORC_NOT_CONVERGED or an error. */
-int oracle_fit(const oracle_problem *p, int prior, double var, int tol_mode, double tol,
-               int max_cycles, const double *beta0, double *beta_out, double *hist,
-               int *cycles_out, int64_t *nonzero_steps_out, int *warn_out) {
+int oracle_fit_w(const oracle_problem *p, int prior, double var, int tol_mode, double tol,
+                 int max_cycles, const double *beta0, const int64_t *w_in, double *beta_out, double *hist,
+                 int *cycles_out, int64_t *nonzero_steps_out, int *warn_out) {
     if ((prior == ORC_PRIOR_NORMAL || prior == ORC_PRIOR_LAPLACE) && !(var > 0.0)) return ORC_E_INVAL;
     if (max_cycles < 0) return ORC_E_INVAL;
     const int64_t K = p->K, N = p->N;
@@ -330,9 +374,15 @@ int oracle_fit(const oracle_problem *p, int prior, double var, int tol_mode, dou
     double *E = (double *)xcalloc((size_t)K, sizeof(double));
     double *D = (double *)xcalloc((size_t)N, sizeof(double));
     double *trust = (double *)xcalloc((size_t)J, sizeof(double));
-    if (!xb || !xb_prev || !E || !D || !trust) {
-        free(xb); free(xb_prev); free(E); free(D); free(trust); return ORC_E_NOMEM;
+    int64_t *wn = (int64_t *)xcalloc((size_t)N, sizeof(int64_t));    /* R9: w_i n_i */
+    int64_t *wytx = (int64_t *)xcalloc((size_t)J, sizeof(int64_t));  /* R9: weighted Y'X_j */
+    int64_t *wy = (int64_t *)xcalloc((size_t)K, sizeof(int64_t));    /* R9: w_i(k) y_k */
+    if (!xb || !xb_prev || !E || !D || !trust || !wn || !wytx || !wy) {
+        free(xb); free(xb_prev); free(E); free(D); free(trust); free(wn); free(wytx); free(wy);
+        return ORC_E_NOMEM;
     }
+    weighted_counts(p, w_in, wn, wytx);
+    for (int64_t k = 0; k < K; ++k) wy[k] = weight_of(p, w_in, p->row_pat[k]) * p->y[k];
     for (int32_t j = 0; j < J; ++j) { beta[j] = beta0 ? beta0[j] : 0.0; trust[j] = 1.0; }
 
     /* Initialise: Xb, L x exp(Xb), M[L x exp(Xb)] (b = 0 gives Xb = 0, E = L, D = M L). */
@@ -344,8 +394,8 @@ int oracle_fit(const oracle_problem *p, int prior, double var, int tol_mode, dou
         D[i] = s;
     }
     double ylin = 0.0, nlog = 0.0;
-    for (int64_t k = 0; k < K; ++k) ylin += (double)p->y[k] * xb[k];
-    for (int64_t i = 0; i < N; ++i) nlog += (double)p->n[i] * log(D[i]);
+    for (int64_t k = 0; k < K; ++k) ylin += (double)wy[k] * xb[k];
+    for (int64_t i = 0; i < N; ++i) nlog += (double)wn[i] * log(D[i]);
     double P_prev = ylin - nlog + log_prior(prior, var, beta, J);
     if (hist) hist[0] = P_prev;
 
@@ -362,8 +412,8 @@ int oracle_fit(const oracle_problem *p, int prior, double var, int tol_mode, dou
                 if (i != cur) {
                     if (cur >= 0) {
                         double Wi = num / D[cur];
-                        nW += (double)p->n[cur] * Wi;
-                        nWW += (double)p->n[cur] * Wi * (1.0 - Wi);
+                        nW += (double)wn[cur] * Wi;
+                        nWW += (double)wn[cur] * Wi * (1.0 - Wi);
                     }
                     cur = i; num = 0.0;
                 }
@@ -371,10 +421,10 @@ int oracle_fit(const oracle_problem *p, int prior, double var, int tol_mode, dou
             }
             if (cur >= 0) {
                 double Wi = num / D[cur];
-                nW += (double)p->n[cur] * Wi;
-                nWW += (double)p->n[cur] * Wi * (1.0 - Wi);
+                nW += (double)wn[cur] * Wi;
+                nWW += (double)wn[cur] * Wi * (1.0 - Wi);
             }
-            double g = (double)p->ytx[j] - nW, h = -nWW;
+            double g = (double)wytx[j] - nW, h = -nWW;
             double db = coordinate_step(g, h, beta[j], prior, var, &trust[j], &warn);
             if (!isfinite(db)) { status = ORC_E_NUMERIC; goto done; }
             if (db != 0.0) { /* R6 */
@@ -397,8 +447,8 @@ int oracle_fit(const oracle_problem *p, int prior, double var, int tol_mode, dou
             D[i] = s;
         }
         ylin = 0.0; nlog = 0.0;
-        for (int64_t k = 0; k < K; ++k) ylin += (double)p->y[k] * xb[k];
-        for (int64_t i = 0; i < N; ++i) nlog += (double)p->n[i] * log(D[i]);
+        for (int64_t k = 0; k < K; ++k) ylin += (double)wy[k] * xb[k];
+        for (int64_t i = 0; i < N; ++i) nlog += (double)wn[i] * log(D[i]);
         double P = ylin - nlog + log_prior(prior, var, beta, J);
         if (!isfinite(P)) { status = ORC_E_NUMERIC; goto done; }
         if (hist) hist[t] = P;
@@ -418,6 +468,13 @@ done:
     if (cycles_out) *cycles_out = t;
     if (nonzero_steps_out) *nonzero_steps_out = nonzero_steps;
     if (warn_out) *warn_out = warn;
-    free(xb); free(xb_prev); free(E); free(D); free(trust);
+    free(xb); free(xb_prev); free(E); free(D); free(trust); free(wn); free(wytx); free(wy);
     return status;
+}
+
+int oracle_fit(const oracle_problem *p, int prior, double var, int tol_mode, double tol,
+               int max_cycles, const double *beta0, double *beta_out, double *hist,
+               int *cycles_out, int64_t *nonzero_steps_out, int *warn_out) {
+    return oracle_fit_w(p, prior, var, tol_mode, tol, max_cycles, beta0, NULL, beta_out, hist,
+                        cycles_out, nonzero_steps_out, warn_out);
 }

@@ -140,3 +140,28 @@ def read_golden(path):
     pid = a[:, 0].astype(np.int64)
     X = a[:, 2:3]
     return from_dense(pid, a[:, 3].astype(np.int32), a[:, 1], X), expected
+
+
+def input_subjects(d: SCCSData) -> list:
+    """Row ranges of the input subjects (runs of equal patient_id, in input order)."""
+    pid = np.asarray(d.patient_id)
+    starts = [0] + [k for k in range(1, pid.size) if pid[k] != pid[k - 1]]
+    ends = starts[1:] + [pid.size]
+    return list(zip(starts, ends))
+
+
+def replicate_subjects(d: SCCSData, w) -> SCCSData:
+    """The dataset in which input subject i appears w[i] times (each copy a subject of its own):
+    what a bootstrap resample with multiplicities w, or a fold split with 0/1 weights, is."""
+    X = to_dense(d)
+    pid, y, L, rows = [], [], [], []
+    new_id = 0
+    for (a, b), wi in zip(input_subjects(d), w):
+        for _ in range(int(wi)):
+            pid.extend([new_id] * (b - a))
+            y.extend(d.y[a:b])
+            L.extend(d.L[a:b])
+            rows.append(X[a:b])
+            new_id += 1
+    Xn = np.concatenate(rows) if rows else np.zeros((0, X.shape[1]))
+    return from_dense(np.asarray(pid, np.int64), np.asarray(y), np.asarray(L, float), Xn)

@@ -9,15 +9,15 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_weights as wpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "sccs_oracle.c")
 
 # (name, exact text in the oracle, replacement)
 MUTATIONS = [
-    ("hessian_sign_1_plus_w", "nWW += (double)p->n[i] * Wi * (1.0 - Wi);",
-     "nWW += (double)p->n[i] * Wi * (1.0 + Wi);"),
-    ("gradient_sign", "*g = (double)p->ytx[j] - nW;", "*g = (double)p->ytx[j] + nW;"),
-    ("loglik_dropped_log_term", "total += lin - (double)p->n[i] * log(den);", "total += lin - log(den);"),
+    ("hessian_sign_1_plus_w", "nWW += ni * Wi * (1.0 - Wi);", "nWW += ni * Wi * (1.0 + Wi);"),
+    ("gradient_sign", "*g = (double)ytx - nW;", "*g = (double)ytx + nW;"),
+    ("loglik_dropped_log_term", "(lin - (double)p->n[i] * log(den))", "(lin - log(den))"),
     ("laplace_scale", "double lambda = sqrt(2.0 / var);\n        if (q > 0.0)",
      "double lambda = sqrt(1.0 / var);\n        if (q > 0.0)"),
     ("normal_prior_curvature", "dv = (g - bj / var) / (q + 1.0 / var);", "dv = (g - bj / var) / (q + 2.0 / var);"),
@@ -25,6 +25,11 @@ MUTATIONS = [
     ("off_by_one_subject", "if (cur >= 0) {\n                        double Wi = num / D[cur];",
      "if (cur >= 0) {\n                        double Wi = num / D[cur > 0 ? cur - 1 : 0];"),
     ("offset_ignored_in_update", "double En = p->L[k] * exp(xb[k]);", "double En = exp(xb[k]);"),
+    # subject weights (Section 2.5)
+    ("weights_ignored_in_ytx", "t += weight_of(p, w_in, p->row_pat[k]) * p->y[k];", "t += p->y[k];"),
+    ("weights_ignored_in_n", "wn[i] = weight_of(p, w_in, i) * p->n[i];", "wn[i] = p->n[i];"),
+    ("weights_ignored_in_loglik", "total += (double)weight_of(p, w_in, i) * (", "total += ("),
+    ("weights_by_kept_subject", "return w_in ? w_in[p->sub_in[i]] : 1;", "return w_in ? w_in[i] : 1;"),
 ]
 
 PIN_CASES = [
@@ -35,6 +40,8 @@ PIN_CASES = [
     (pins.test_one_covariate_general_minimiser, dict(seed=0)),
     (pins.test_ccd_matches_multivariate_newton, dict(seed=1, prior="normal")),
     (pins.test_laplace_kkt_certificate, dict(seed=1, var=0.2)),
+    (wpins.test_weighted_fit_equals_replicated_dataset, dict(seed=0, prior="normal", var=0.5)),
+    (wpins.test_fold_fit_and_heldout_loglik, dict(seed=0)),
 ]
 
 
@@ -50,8 +57,8 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new):
     subprocess.run(oracle.compile_command(str(mutated), str(so)), check=True)
     lib = oracle.load_variant(str(so))
     failed = []
-    saved = pins.ORACLE_LIB
-    pins.ORACLE_LIB = lib
+    saved = pins.ORACLE_LIB, wpins.ORACLE_LIB
+    pins.ORACLE_LIB = wpins.ORACLE_LIB = lib
     try:
         for fn, kw in PIN_CASES:
             try:
@@ -59,7 +66,7 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new):
             except (AssertionError, oracle.OracleError):
                 failed.append(fn.__name__)
     finally:
-        pins.ORACLE_LIB = saved
+        pins.ORACLE_LIB, wpins.ORACLE_LIB = saved
     assert failed, f"planted mistake {name} passed every pin"
 
 
