@@ -107,6 +107,14 @@ typedef struct sccs_fit_opts {
     int32_t reserved;
     double *logpost_history;   /* optional host buffer of max_cycles + 1 values: P_0 .. P_c of the
                                   last phase run (the FP64 polish in SCCS_PREC_FP32_POLISH) */
+    const int32_t *subject_weights;  /* host, one weight w_i >= 0 per INPUT subject (a run of
+                                  equal patient_id, dropped subjects included, in input order), or
+                                  NULL for all 1.  Subject i counts w_i times in Eq. 2 and Eqs. 7-9
+                                  (n_i -> w_i n_i, Y'X_j -> sum over X_j of w_i y): Section 2.5's
+                                  bootstrap multiplicities, or a cross-validation fold's 0/1 mask
+                                  for the fit on the other folds.  Integer arithmetic, so all-ones
+                                  weights give exactly the unweighted fit.  SCCS_E_INVAL if a
+                                  weight is negative or w_i n_i exceeds 2^31 - 1. */
 } sccs_fit_opts;
 
 typedef struct sccs_fit_info {
@@ -213,6 +221,17 @@ int sccs_logpost(sccs_handle *h, const double *beta, double *logpost, double *lo
 /* Copy the handle's current beta (host [J]). */
 int sccs_get_beta(const sccs_handle *h, double *beta_out);
 
+/*
+ * sccs_heldout_loglik -- the predictive log-likelihood of Section 2.5's cross-validation: Eq. 2
+ * with subject i counted weights[i] times (the held-out fold's 0/1 mask, one value per input
+ * subject as in sccs_fit_opts.subject_weights; NULL = all subjects once).
+ *   beta  host [J]: evaluate there; NULL: at the handle's current beta (after a fit, its MAP).
+ * The state (L x exp(Xb) and the denominators) is rebuilt from beta in FP64 first; the trust
+ * radii are kept, so a warm-started fit afterwards continues as if nothing had happened.
+ * Errors: SCCS_E_INVAL (bad weights, non-finite beta), SCCS_E_TIMEOUT, SCCS_E_CUDA.
+ */
+int sccs_heldout_loglik(sccs_handle *h, const double *beta, const int32_t *weights, double *loglik);
+
 /* ---- serving: continuous batching of fit requests (cross-validation / prior grids) ---- */
 
 typedef struct sccs_server sccs_server;
@@ -236,6 +255,12 @@ typedef struct sccs_request {
     int32_t precision;         /* SCCS_PREC_* */
     int32_t reserved;
     const double *beta0;       /* host [J] start point (copied at submit) or NULL for 0 */
+    const int32_t *subject_weights;  /* per input subject, as sccs_fit_opts.subject_weights
+                                  (copied at submit): a bootstrap replicate's multiplicities, or a
+                                  cross-validation fit's training mask; NULL = all 1 */
+    const int32_t *heldout_weights;  /* per input subject (copied at submit): after the fit,
+                                  res->heldout_loglik = sccs_heldout_loglik at the fitted beta with
+                                  these weights (the held-out fold's mask); NULL = not evaluated */
 } sccs_request;
 
 typedef struct sccs_result {
@@ -247,6 +272,7 @@ typedef struct sccs_result {
     double queue_ms;           /* submit -> start on the device */
     double latency_ms;         /* submit -> result ready */
     double *beta;              /* caller's host buffer [J] to receive beta, or NULL */
+    double heldout_loglik;     /* the request's held-out predictive log-likelihood, NaN if none */
 } sccs_result;
 
 typedef struct sccs_server_stats {

@@ -22,6 +22,7 @@ from .sccs import (  # noqa: F401
     sccs_get_info,
     sccs_grad_hess,
     sccs_grad_hess_noalloc,
+    sccs_heldout_loglik,
     sccs_last_error,
     sccs_logpost,
     sccs_set_prior,

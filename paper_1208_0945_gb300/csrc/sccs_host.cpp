@@ -121,6 +121,14 @@ struct sccs_handle {
     double *beta_host = nullptr;       // pinned, J
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     sccs_data_info info{};
+    // subject weights (Section 2.5): host maps, and device scratch made on first use
+    std::vector<int64_t> kept_from;    // N: input subject of each kept subject
+    std::vector<int32_t> nev_host;     // N: n_i
+    int32_t max_nev = 0;
+    int32_t *w_dev = nullptr;          // N: weights per kept subject
+    int32_t *nev_w = nullptr;          // N: w_i n_i
+    double *ytx_w = nullptr;           // J: weighted Y'X_j
+    int32_t *w_host = nullptr;         // N, pinned
 };
 
 namespace {
@@ -167,6 +175,7 @@ void destroy_handle(sccs_handle *h) {
     if (h->hist_host) cudaFreeHost(h->hist_host);
     if (h->beta_host) cudaFreeHost(h->beta_host);
     if (h->hist_dev) cudaFree(h->hist_dev);
+    if (h->w_host) cudaFreeHost(h->w_host);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -190,6 +199,9 @@ struct HostLayout {
     int64_t segments = 0;
     int64_t max_col = 0;
     int64_t subjects_in = 0;
+    std::vector<int64_t> kept_from;   // N: input subject of each kept subject
+    std::vector<int64_t> ycol_ptr;    // J+1: per column, (subject, sum of y) pairs with events
+    std::vector<int32_t> ysub, ycnt;
 };
 
 // Checks everything about the inputs that needs no GPU.
@@ -251,6 +263,7 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     hl.J = J;
     hl.pat_ptr.assign(static_cast<size_t>(Nk) + 1, 0);
     hl.nev.assign(static_cast<size_t>(Nk), 0);
+    hl.kept_from.assign(static_cast<size_t>(Nk), 0);
     hl.L.assign(static_cast<size_t>(Kk), 0.0);
     std::vector<int32_t> row_pat(static_cast<size_t>(Kk));
     std::vector<int64_t> ykept(static_cast<size_t>(Kk));
@@ -260,6 +273,7 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             if (sub_n[i] == 0) continue;
             hl.pat_ptr[i2] = k2;
             hl.nev[i2] = static_cast<int32_t>(sub_n[i]);
+            hl.kept_from[i2] = i;
             for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) {
                 newrow[k] = static_cast<int32_t>(k2);
                 row_pat[k2] = static_cast<int32_t>(i2);
@@ -304,6 +318,42 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     for (int32_t j = 0; j < J; ++j)
         if (dup[j]) return fail(SCCS_E_DUPLICATE, "a row appears twice in column " + std::to_string(j));
     for (int32_t j = 0; j < J; ++j) hl.max_col = std::max<int64_t>(hl.max_col, cptr[j + 1] - cptr[j]);
+
+    // ---- per column, the subjects with events on its rows and their event sums (what a
+    //      weighted Y'X_j needs, Section 2.5); rows are ascending, so a subject's rows are adjacent
+    {
+        std::vector<int64_t> npairs(static_cast<size_t>(J), 0);
+        parallel_for(J, [&](int64_t j) {
+            int64_t c = 0;
+            int32_t cur = -1;
+            for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) {
+                const int32_t r = crow[e];
+                if (ykept[r] > 0 && row_pat[r] != cur) {
+                    cur = row_pat[r];
+                    ++c;
+                }
+            }
+            npairs[j] = c;
+        });
+        hl.ycol_ptr.assign(static_cast<size_t>(J) + 1, 0);
+        for (int32_t j = 0; j < J; ++j) hl.ycol_ptr[j + 1] = hl.ycol_ptr[j] + npairs[j];
+        hl.ysub.assign(static_cast<size_t>(hl.ycol_ptr[J]), 0);
+        hl.ycnt.assign(static_cast<size_t>(hl.ycol_ptr[J]), 0);
+        parallel_for(J, [&](int64_t j) {
+            int64_t q = hl.ycol_ptr[j] - 1;
+            int32_t cur = -1;
+            for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) {
+                const int32_t r = crow[e];
+                if (ykept[r] <= 0) continue;
+                if (row_pat[r] != cur) {
+                    cur = row_pat[r];
+                    ++q;
+                    hl.ysub[q] = cur;
+                }
+                hl.ycnt[q] += static_cast<int32_t>(ykept[r]);   // <= n_i < 2^31
+            }
+        });
+    }
 
     // ---- shards at subject boundaries, balanced by rows
     hl.S = S;
@@ -447,6 +497,59 @@ int set_state(sccs_handle *h, const double *beta) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync beta");
     return run_init_state(h, h->beta_dev);
 }
+
+// ---- subject weights (Section 2.5)
+
+int ensure_weight_scratch(sccs_handle *h) {
+    if (h->w_dev) return SCCS_OK;
+    const size_t N = static_cast<size_t>(std::max<int64_t>(h->d.N, 1));
+    const size_t J = static_cast<size_t>(std::max<int32_t>(h->d.J, 1));
+    auto *w = static_cast<int32_t *>(h->arena.get(4 * N));
+    auto *nw = static_cast<int32_t *>(h->arena.get(4 * N));
+    auto *yw = static_cast<double *>(h->arena.get(8 * J));
+    if (!w || !nw || !yw) return fail(SCCS_E_NOMEM, "device memory for subject weights");
+    if (cudaMallocHost(&h->w_host, 4 * N) != cudaSuccess) {
+        (void)cudaGetLastError();
+        h->w_host = nullptr;
+        return fail(SCCS_E_NOMEM, "pinned memory for subject weights");
+    }
+    h->w_dev = w;
+    h->nev_w = nw;
+    h->ytx_w = yw;
+    return SCCS_OK;
+}
+
+// Map the weights to kept subjects, upload them and form w_i n_i and the weighted Y'X_j.
+int prepare_weights(sccs_handle *h, const int32_t *w_in) {
+    int rc = ensure_weight_scratch(h);
+    if (rc) return rc;
+    sccs::HandleView v{};
+    sccs_handle_view(h, &v);
+    if ((rc = sccs::map_subject_weights(v, w_in, h->w_host))) return rc;
+    cudaError_t e = cudaMemcpyAsync(h->w_dev, h->w_host, sizeof(int32_t) * static_cast<size_t>(std::max<int64_t>(h->d.N, 1)),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync weights");
+    const int le = sccs::launch_weighted_counts(h->d, h->w_dev, h->nev_w, h->ytx_w, h->stream);
+    if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "weighted counts launch");
+    return SCCS_OK;
+}
+
+// While alive, the handle's layout carries the weighted counts in place of n_i and Y'X_j.
+struct CountsScope {
+    sccs_handle *h;
+    const int32_t *nev;
+    const double *ytx;
+    CountsScope(sccs_handle *hh, bool weighted) : h(hh), nev(hh->d.nev), ytx(hh->d.ytx) {
+        if (weighted) {
+            h->d.nev = h->nev_w;
+            h->d.ytx = h->ytx_w;
+        }
+    }
+    ~CountsScope() {
+        h->d.nev = nev;
+        h->d.ytx = ytx;
+    }
+};
 
 sccs::FitParams base_params(const sccs_handle *h) {
     sccs::FitParams p{};
@@ -690,8 +793,28 @@ bool sccs_handle_view(const sccs_handle *h, sccs::HandleView *v) {
     v->device = h->device;
     v->threads = h->threads;
     v->d = h->d;
+    v->kept_from = h->kept_from.data();
+    v->nev_host = h->nev_host.data();
+    v->subjects_in = h->info.subjects_in;
+    v->max_nev = h->max_nev;
     return true;
 }
+
+namespace sccs {
+
+int map_subject_weights(const HandleView &v, const int32_t *w_in, int32_t *w_kept) {
+    for (int64_t i = 0; i < v.d.N; ++i) {
+        const int64_t src = v.kept_from[i];
+        const int32_t w = w_in[src];
+        if (w < 0) return fail(SCCS_E_INVAL, "negative weight for input subject " + std::to_string(src));
+        if (static_cast<int64_t>(w) * v.nev_host[i] > INT32_MAX)
+            return fail(SCCS_E_INVAL, "weight x events exceeds 2^31 - 1 for input subject " + std::to_string(src));
+        w_kept[i] = w;
+    }
+    return SCCS_OK;
+}
+
+}  // namespace sccs
 
 extern "C" {
 
@@ -782,8 +905,9 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     int32_t *rows;
     int2 *segs;
     int64_t *grp_base, *slice_row, *slice_seg, *slice_grp, *shard_row, *shard_pat, *pat_ptr;
-    int32_t *nev;
+    int32_t *nev, *ysub, *ycnt;
     double *L, *ytx;
+    int64_t *ycol_ptr;
     if ((rc = upload(h, &rows, hl.rows.data(), hl.rows.size(), sccs::kCopyPad)) ||
         (rc = upload(h, &segs, hl.segs.data(), hl.segs.size(), sccs::kCopyPad)) ||
         (rc = upload(h, &grp_base, hl.grp_base.data(), hl.grp_base.size(), sccs::kCopyPad)) ||
@@ -795,8 +919,17 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
         (rc = upload(h, &pat_ptr, hl.pat_ptr.data(), hl.pat_ptr.size())) ||
         (rc = upload(h, &nev, hl.nev.data(), hl.nev.size())) ||
         (rc = upload(h, &L, hl.L.data(), hl.L.size())) ||
-        (rc = upload(h, &ytx, hl.ytx.data(), hl.ytx.size())))
+        (rc = upload(h, &ytx, hl.ytx.data(), hl.ytx.size())) ||
+        (rc = upload(h, &ycol_ptr, hl.ycol_ptr.data(), hl.ycol_ptr.size())) ||
+        (rc = upload(h, &ysub, hl.ysub.data(), hl.ysub.size())) ||
+        (rc = upload(h, &ycnt, hl.ycnt.data(), hl.ycnt.size())))
         return bail(rc);
+    d.ycol_ptr = ycol_ptr;
+    d.ysub = ysub;
+    d.ycnt = ycnt;
+    h->kept_from = std::move(hl.kept_from);
+    h->nev_host = hl.nev;
+    for (int32_t v : h->nev_host) h->max_nev = std::max(h->max_nev, v);
     d.rows = rows;
     d.segs = segs;
     d.grp_base = grp_base;
@@ -889,6 +1022,8 @@ int sccs_fit(sccs_handle *h, const sccs_fit_opts *opts, double *beta_out, sccs_f
         return fail(SCCS_E_INVAL, "unknown precision");
     int rc = set_device(h);
     if (rc) return rc;
+    if (o.subject_weights && (rc = prepare_weights(h, o.subject_weights))) return rc;
+    CountsScope counts(h, o.subject_weights != nullptr);
 
     // start point
     if (o.beta0) {
@@ -1157,6 +1292,50 @@ int sccs_logpost(sccs_handle *h, const double *beta, double *logpost, double *lo
     h->seq = r.seq_end;
     if (logpost) *logpost = r.logpost;
     if (loglik) *loglik = r.loglik;
+    return SCCS_OK;
+}
+
+int sccs_heldout_loglik(sccs_handle *h, const double *beta, const int32_t *weights, double *loglik) {
+    if (!h || !loglik) return fail(SCCS_E_INVAL, "null argument");
+    int rc = set_device(h);
+    if (rc) return rc;
+    const int32_t J = h->d.J;
+    if (beta) {
+        for (int32_t j = 0; j < J; ++j)
+            if (!std::isfinite(beta[j])) return fail(SCCS_E_INVAL, "beta has a non-finite entry");
+        std::memcpy(h->beta_host, beta, sizeof(double) * static_cast<size_t>(J));
+        cudaError_t e = cudaMemcpyAsync(h->beta_dev, h->beta_host, sizeof(double) * std::max<int32_t>(J, 1),
+                                        cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync beta");
+    } else {
+        cudaError_t e = cudaMemcpyAsync(h->beta_dev, h->d.beta_priv, sizeof(double) * std::max<int32_t>(J, 1),
+                                        cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync beta");
+    }
+    // E and D rebuilt from beta in FP64, trust radii kept
+    int le = sccs::launch_init_state(h->d, h->beta_dev, h->threads, h->stream, true);
+    if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "init_state launch");
+    if (weights && (rc = prepare_weights(h, weights))) return rc;
+    CountsScope counts(h, weights != nullptr);
+    if (h->hist_cap < 1) {
+        cudaError_t e = cudaMalloc(&h->hist_dev, sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc history");
+        e = cudaMallocHost(&h->hist_host, sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost history");
+        h->hist_cap = 1;
+    }
+    sccs::FitParams p = base_params(h);
+    p.max_cycles = 0;
+    le = sccs::launch_fit(h->d, p, h->out_dev, h->hist_dev, h->threads, h->stream);
+    if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "fit kernel launch");
+    if ((rc = sync_out(h))) return rc;
+    const sccs::FitOut r = *h->out_host;
+    if (r.status == -6 || r.abort_flag) {
+        reset_after_abort(h);
+        return fail(SCCS_E_TIMEOUT, "a device-side wait exceeded its bound; the handle was reset to beta = 0");
+    }
+    h->seq = r.seq_end;
+    *loglik = r.loglik;
     return SCCS_OK;
 }
 

@@ -48,9 +48,12 @@ struct DevLayout {
     const int64_t *shard_row;  // S+1
     const int64_t *shard_pat;  // S+1
     const int64_t *pat_ptr;    // N+1: rows of subject i
-    const int32_t *nev;        // N: n_i
+    const int32_t *nev;        // N: n_i (or w_i n_i in a weighted fit)
     const double *L;           // K: offsets l_k
-    const double *ytx;         // J: Y'X_j
+    const double *ytx;         // J: Y'X_j (or its weighted form)
+    const int64_t *ycol_ptr;   // J+1: per column, its (subject, sum of y) pairs with events
+    const int32_t *ysub;       //   kept subject of each pair
+    const int32_t *ycnt;       //   sum of y over the column's rows of that subject
     // state
     double *E;                 // K: L x exp(Xb)
     double *D;                 // N: M[L x exp(Xb)]
@@ -76,6 +79,8 @@ struct FitParams {
     int32_t record_history;
     unsigned long long seq0;   // all-reduce sequence number at launch
     long long timeout_ns;      // bound on each device-side wait (from the start of that wait)
+    const unsigned long long *seq_src;  // device; if set, seq0 is read from here at launch (the
+                                        // seq_end of the launch before it on the same stream)
 };
 
 struct FitOut {
@@ -120,6 +125,9 @@ int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, 
                       bool keep_trust = false);
 // E32 = (float) E on every shard.
 int launch_e_to_f32(const DevLayout &d, int threads, void *stream);
+// Weighted counts of a fit with subject weights w_kept (device [N]): nev_w[i] = w_i n_i and
+// ytx_w[j] = sum over X_j's (subject, y) pairs of w_i y, both exact (integer sums).
+int launch_weighted_counts(const DevLayout &d, const int32_t *w_kept, int32_t *nev_w, double *ytx_w, void *stream);
 int launch_fit(const DevLayout &d, const FitParams &p, FitOut *out_dev, double *hist_dev,
                int threads, void *stream, bool fp32 = false);
 int launch_grad_hess(const DevLayout &d, int32_t j, const FitParams &p, FitOut *out_dev,
@@ -151,7 +159,15 @@ struct HandleView {
     int device;
     int threads;
     DevLayout d;
+    const int64_t *kept_from;  // host [N]: input subject index of each kept subject
+    const int32_t *nev_host;   // host [N]: n_i
+    int64_t subjects_in;
+    int32_t max_nev;           // largest n_i
 };
+
+// Subject weights given per input subject -> per kept subject (host arrays).  SCCS_E_INVAL for
+// a negative weight or a product w_i n_i above 2^31 - 1 (the message names the subject).
+int map_subject_weights(const HandleView &v, const int32_t *w_in, int32_t *w_kept);
 
 }  // namespace sccs
 

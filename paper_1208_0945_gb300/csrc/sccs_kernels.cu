@@ -33,6 +33,7 @@
 // flag and return too.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -1055,7 +1056,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                         SharedState &sh) {
     const bool leader = (s == 0) && (threadIdx.x == 0);
     const long long timeout = p.timeout_ns;
-    unsigned long long seq = p.seq0;
+    unsigned long long seq = p.seq_src ? *p.seq_src : p.seq0;
     double *beta = d.beta_priv + static_cast<long long>(s) * d.J;
     double *trust = d.trust_priv + static_cast<long long>(s) * d.J;
     const int J = d.J;
@@ -1494,6 +1495,30 @@ __global__ void __launch_bounds__(512, 1) init_state_kernel(DevLayout d, const d
 
 __global__ void __launch_bounds__(512, 1) e_to_f32_kernel(DevLayout d) { e_to_f32_shard(d, blockIdx.x); }
 
+// Section 2.5 weights: w_i n_i per subject (grid-stride) and, one block per column, the
+// weighted Y'X_j as an exact integer sum over the column's (subject, y) pairs.
+__global__ void __launch_bounds__(256) weighted_counts_kernel(DevLayout d, const int32_t *w, int32_t *nev_w,
+                                                              double *ytx_w) {
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < d.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        nev_w[i] = w[i] * d.nev[i];
+    __shared__ long long part[8];
+    for (int j = blockIdx.x; j < d.J; j += gridDim.x) {
+        long long t = 0;
+        for (long long e = d.ycol_ptr[j] + threadIdx.x; e < d.ycol_ptr[j + 1]; e += blockDim.x)
+            t += static_cast<long long>(w[d.ysub[e]]) * d.ycnt[e];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long s = 0;
+            for (int q = 0; q < static_cast<int>(blockDim.x >> 5); ++q) s += part[q];
+            ytx_w[j] = static_cast<double>(s);
+        }
+        __syncthreads();
+    }
+}
+
 int ensure_smem_attr() {
     const int bytes = static_cast<int>(sizeof(SmemLayout));
     cudaError_t e = cudaFuncSetAttribute(fit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1518,6 +1543,13 @@ int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, 
 
 int launch_e_to_f32(const DevLayout &d, int threads, void *stream) {
     e_to_f32_kernel<<<d.S, threads, 0, static_cast<cudaStream_t>(stream)>>>(d);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_weighted_counts(const DevLayout &d, const int32_t *w_kept, int32_t *nev_w, double *ytx_w, void *stream) {
+    const long long want = std::max<long long>(static_cast<long long>(d.J), (d.N + 255) / 256);
+    const int blocks = static_cast<int>(std::min<long long>(std::max<long long>(want, 1), 4096));
+    weighted_counts_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d, w_kept, nev_w, ytx_w);
     return static_cast<int>(cudaGetLastError());
 }
 

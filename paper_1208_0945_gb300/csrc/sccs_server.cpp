@@ -35,6 +35,14 @@ constexpr double kFp32PhaseRelTol = 1e-6;   // same switch point as sccs_fit
 struct FitSlot {
     const sccs_handle *dataset = nullptr;
     sccs::DevLayout d{};
+    const int32_t *base_nev = nullptr;  // the dataset's n_i and Y'X_j (unweighted requests)
+    const double *base_ytx = nullptr;
+    int32_t *w_dev = nullptr;           // N: a request's weights per kept subject
+    int32_t *nev_w = nullptr;           // N: w_i n_i
+    double *ytx_w = nullptr;            // J: weighted Y'X_j
+    int32_t *w_host = nullptr;          // 2N pinned: training weights, then held-out weights
+    sccs::FitOut *out_ho_dev = nullptr; // held-out evaluation
+    sccs::FitOut *out_ho_host = nullptr;
     int threads = 512;
     size_t bytes = 0;
     void *block = nullptr;
@@ -59,6 +67,8 @@ struct Request {
     int max_cycles = 1000;
     int precision = SCCS_PREC_FP64;
     std::vector<double> beta0;
+    std::vector<int32_t> w_train, w_ho;   // per kept subject (empty: none)
+    double heldout_loglik = std::nan("");
     int J = 0;
     int S = 0;
     Clock::time_point t_submit, t_start, t_done;
@@ -76,9 +86,10 @@ size_t slot_bytes(const sccs::DevLayout &d, int max_cycles) {
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t K = static_cast<size_t>(d.K), N = static_cast<size_t>(d.N), S = d.S,
                  J = static_cast<size_t>(std::max(d.J, 1));
+    const size_t N1 = std::max<size_t>(N, 1);
     return al(8 * K) + al(8 * N) + al(4 * K) + al(8 * N) + 2 * al(8 * S * J) +
-           al(16 * S * static_cast<size_t>(d.stash_stride)) + al(32 * S) + al(sizeof(sccs::FitOut)) +
-           al(8 * J) + al(8 * static_cast<size_t>(max_cycles + 1));
+           al(16 * S * static_cast<size_t>(d.stash_stride)) + al(32 * S) + 2 * al(sizeof(sccs::FitOut)) +
+           al(8 * J) + al(8 * static_cast<size_t>(max_cycles + 1)) + 2 * al(4 * N1) + al(8 * J);
 }
 
 }  // namespace
@@ -113,6 +124,8 @@ void free_slot(FitSlot *s) {
     if (s->hist_dev) cudaFree(s->hist_dev);
     if (s->out_host) cudaFreeHost(s->out_host);
     if (s->beta_host) cudaFreeHost(s->beta_host);
+    if (s->w_host) cudaFreeHost(s->w_host);
+    if (s->out_ho_host) cudaFreeHost(s->out_ho_host);
     if (s->done) cudaEventDestroy(s->done);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
@@ -126,6 +139,8 @@ FitSlot *make_slot(const sccs_handle *dataset, int max_cycles) {
     s->dataset = dataset;
     s->threads = v.threads;
     s->d = v.d;
+    s->base_nev = v.d.nev;
+    s->base_ytx = v.d.ytx;
     sccs::DevLayout &d = s->d;
     const size_t bytes = slot_bytes(d, 0);
     s->bytes = bytes;
@@ -160,10 +175,17 @@ FitSlot *make_slot(const sccs_handle *dataset, int max_cycles) {
     d.stash = reinterpret_cast<double *>(take(16 * S * static_cast<size_t>(d.stash_stride)));
     d.slots = reinterpret_cast<unsigned long long *>(take(32 * S));
     s->out_dev = reinterpret_cast<sccs::FitOut *>(take(sizeof(sccs::FitOut)));
+    s->out_ho_dev = reinterpret_cast<sccs::FitOut *>(take(sizeof(sccs::FitOut)));
     s->beta_dev = reinterpret_cast<double *>(take(8 * J));
+    const size_t N1 = std::max<size_t>(N, 1);
+    s->w_dev = reinterpret_cast<int32_t *>(take(4 * N1));
+    s->nev_w = reinterpret_cast<int32_t *>(take(4 * N1));
+    s->ytx_w = reinterpret_cast<double *>(take(8 * J));
     d.abort_flag = &s->out_dev->abort_flag;
     if (cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&s->out_host, sizeof(sccs::FitOut)) != cudaSuccess ||
+        cudaMallocHost(&s->out_ho_host, sizeof(sccs::FitOut)) != cudaSuccess ||
+        cudaMallocHost(&s->w_host, 8 * N1) != cudaSuccess ||
         cudaMallocHost(&s->beta_host, 8 * J) != cudaSuccess) {
         (void)cudaGetLastError();
         free_slot(s);
@@ -209,8 +231,26 @@ sccs::FitParams params_for(const Request &r, const FitSlot &s, bool fp32_phase) 
 int enqueue_phase(Request &r, bool first) {
     FitSlot &s = *r.slot;
     const bool fp32 = r.phase == 1;
+    const bool final_phase = !(r.phase == 1 && r.precision == SCCS_PREC_FP32_POLISH);
+    const size_t N1 = static_cast<size_t>(std::max<int64_t>(s.d.N, 1));
+    // weighted counts are always formed from the dataset's own n_i and Y'X_j pairs
+    sccs::DevLayout base = s.d;
+    base.nev = s.base_nev;
+    base.ytx = s.base_ytx;
     int e = 0;
     if (first) {
+        // the request's counts: weighted (Section 2.5) or the dataset's own
+        if (!r.w_train.empty()) {
+            std::memcpy(s.w_host, r.w_train.data(), sizeof(int32_t) * r.w_train.size());
+            cudaMemcpyAsync(s.w_dev, s.w_host, sizeof(int32_t) * N1, cudaMemcpyHostToDevice, s.stream);
+            e = sccs::launch_weighted_counts(base, s.w_dev, s.nev_w, s.ytx_w, s.stream);
+            if (e) return e;
+            s.d.nev = s.nev_w;
+            s.d.ytx = s.ytx_w;
+        } else {
+            s.d.nev = s.base_nev;
+            s.d.ytx = s.base_ytx;
+        }
         if (!r.beta0.empty()) {
             std::memcpy(s.beta_host, r.beta0.data(), sizeof(double) * r.J);
             cudaMemcpyAsync(s.beta_dev, s.beta_host, sizeof(double) * r.J, cudaMemcpyHostToDevice, s.stream);
@@ -231,6 +271,27 @@ int enqueue_phase(Request &r, bool first) {
     if (e) return e;
     cudaMemcpyAsync(s.out_host, s.out_dev, sizeof(sccs::FitOut), cudaMemcpyDeviceToHost, s.stream);
     if (r.J > 0) cudaMemcpyAsync(s.beta_host, s.d.beta_priv, sizeof(double) * r.J, cudaMemcpyDeviceToHost, s.stream);
+    if (final_phase && !r.w_ho.empty()) {
+        // held-out predictive log-likelihood at the fitted beta (as sccs_heldout_loglik)
+        int32_t *wh = s.w_host + N1;
+        std::memcpy(wh, r.w_ho.data(), sizeof(int32_t) * r.w_ho.size());
+        cudaMemcpyAsync(s.w_dev, wh, sizeof(int32_t) * N1, cudaMemcpyHostToDevice, s.stream);
+        e = sccs::launch_weighted_counts(base, s.w_dev, s.nev_w, s.ytx_w, s.stream);
+        if (e) return e;
+        sccs::DevLayout dh = s.d;
+        dh.nev = s.nev_w;
+        dh.ytx = s.ytx_w;
+        cudaMemcpyAsync(s.beta_dev, s.d.beta_priv, sizeof(double) * std::max(r.J, 1), cudaMemcpyDeviceToDevice,
+                        s.stream);
+        e = sccs::launch_init_state(dh, s.beta_dev, s.threads, s.stream, true);
+        if (e) return e;
+        sccs::FitParams ph = params_for(r, s, false);
+        ph.max_cycles = 0;
+        ph.seq_src = &s.out_dev->seq_end;   // continues where the fit's all-reduces ended
+        e = sccs::launch_fit(dh, ph, s.out_ho_dev, s.hist_dev, s.threads, s.stream, false);
+        if (e) return e;
+        cudaMemcpyAsync(s.out_ho_host, s.out_ho_dev, sizeof(sccs::FitOut), cudaMemcpyDeviceToHost, s.stream);
+    }
     return static_cast<int>(cudaEventRecord(s.done, s.stream));
 }
 
@@ -347,16 +408,19 @@ void worker_main(sccs_server *sv) {
             if (q == cudaErrorNotReady) continue;
             progressed = true;
             const sccs::FitOut out = *s.out_host;
+            const bool final_phase = !(r->phase == 1 && r->precision == SCCS_PREC_FP32_POLISH);
+            const bool heldout = final_phase && !r->w_ho.empty();
+            const sccs::FitOut out_ho = heldout ? *s.out_ho_host : sccs::FitOut{};
             int status = SCCS_OK;
             if (q != cudaSuccess) {
                 (void)cudaGetLastError();
                 status = SCCS_E_CUDA;
-            } else if (out.status == -6 || out.abort_flag) {
+            } else if (out.status == -6 || out.abort_flag || (heldout && (out_ho.status == -6 || out_ho.abort_flag))) {
                 status = SCCS_E_TIMEOUT;
-            } else if (out.status == -7) {
+            } else if (out.status == -7 || (heldout && out_ho.status == -7)) {
                 status = SCCS_E_NUMERIC;
             }
-            if (status == SCCS_OK) s.seq = out.seq_end;
+            if (status == SCCS_OK) s.seq = heldout ? out_ho.seq_end : out.seq_end;
             else reset_slot_after_abort(s);
             if (status == SCCS_OK && r->phase == 1 && r->precision == SCCS_PREC_FP32_POLISH) {
                 {
@@ -373,6 +437,7 @@ void worker_main(sccs_server *sv) {
                 r->cycles = out.cycles + (r->precision == SCCS_PREC_FP32_POLISH ? r->fp32_cycles : 0);
                 if (r->precision == SCCS_PREC_FP32) r->fp32_cycles = out.cycles;
                 r->logpost = out.logpost;
+                r->heldout_loglik = heldout ? out_ho.loglik : std::nan("");
                 r->beta.assign(s.beta_host, s.beta_host + r->J);
                 status = out.status == 0 ? SCCS_OK : SCCS_NOT_CONVERGED;
             }
@@ -455,6 +520,18 @@ int sccs_submit(sccs_server *sv, const sccs_request *req, uint64_t *ticket) {
             }
         r->beta0.assign(req->beta0, req->beta0 + r->J);
     }
+    // Section 2.5 weights, mapped to kept subjects now (the caller's arrays need not outlive this call)
+    for (int which = 0; which < 2; ++which) {
+        const int32_t *w_in = which == 0 ? req->subject_weights : req->heldout_weights;
+        if (!w_in) continue;
+        std::vector<int32_t> &w = which == 0 ? r->w_train : r->w_ho;
+        w.assign(static_cast<size_t>(std::max<int64_t>(v.d.N, 1)), 0);
+        const int rc = sccs::map_subject_weights(v, w_in, w.data());
+        if (rc != SCCS_OK) {
+            delete r;
+            return rc;
+        }
+    }
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -486,6 +563,7 @@ int sccs_poll(sccs_server *sv, uint64_t ticket, sccs_result *res) {
     res->cycles = r->cycles;
     res->fp32_cycles = r->fp32_cycles;
     res->logpost = r->logpost;
+    res->heldout_loglik = r->status == SCCS_OK || r->status == SCCS_NOT_CONVERGED ? r->heldout_loglik : std::nan("");
     res->queue_ms = std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count();
     res->latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
     if (r->phase == 3 && r->t_start < r->t_submit) res->queue_ms = 0.0;

@@ -48,7 +48,8 @@ class sccs_fit_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("beta0", ctypes.POINTER(ctypes.c_double)), ("tol_mode", ctypes.c_int32),
                 ("max_cycles", ctypes.c_int32), ("tol", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("logpost_history", ctypes.POINTER(ctypes.c_double))]
+                ("reserved", ctypes.c_int32), ("logpost_history", ctypes.POINTER(ctypes.c_double)),
+                ("subject_weights", ctypes.POINTER(ctypes.c_int32))]
 
 
 class sccs_fit_info(ctypes.Structure):
@@ -67,13 +68,15 @@ class sccs_request(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("prior_type", ctypes.c_int32), ("dataset", ctypes.c_void_p),
                 ("variance", ctypes.c_double), ("tol_mode", ctypes.c_int32), ("max_cycles", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("beta0", ctypes.POINTER(ctypes.c_double))]
+                ("beta0", ctypes.POINTER(ctypes.c_double)), ("subject_weights", ctypes.POINTER(ctypes.c_int32)),
+                ("heldout_weights", ctypes.POINTER(ctypes.c_int32))]
 
 
 class sccs_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("cycles", ctypes.c_int32), ("fp32_cycles", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("logpost", ctypes.c_double), ("queue_ms", ctypes.c_double),
-                ("latency_ms", ctypes.c_double), ("beta", ctypes.POINTER(ctypes.c_double))]
+                ("latency_ms", ctypes.c_double), ("beta", ctypes.POINTER(ctypes.c_double)),
+                ("heldout_loglik", ctypes.c_double)]
 
 
 class sccs_server_stats(ctypes.Structure):
@@ -97,6 +100,7 @@ _SIGS = {
                                       ctypes.POINTER(_dp), ctypes.POINTER(sccs_fit_info)]),
     "sccs_logpost": (ctypes.c_int, [_P, _dp, _dp, _dp]),
     "sccs_get_beta": (ctypes.c_int, [_P, _dp]),
+    "sccs_heldout_loglik": (ctypes.c_int, [_P, _dp, _P, _dp]),
     "sccs_check_wait_timeout": (ctypes.c_int, [_P, ctypes.c_double]),
     "sccs_grad_hess_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int64, _P, _P]),
     "sccs_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(sccs_server_opts)]),
@@ -132,6 +136,15 @@ def _ptr(a: np.ndarray | None):
 
 def _dptr(a: np.ndarray | None):
     return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _weights(w):
+    """Subject weights (one non-negative integer per input subject) as an int32 array, or None."""
+    return None if w is None else np.ascontiguousarray(w, np.int32)
+
+
+def _iptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
 
 
 # ------------------------------------------------------------------ the C ABI, name for name
@@ -181,12 +194,13 @@ def sccs_set_prior(handle, prior: str | int, variance: float = 1.0) -> int:
 
 
 def sccs_fit(handle, J: int, *, beta0=None, warm_start=False, tol_mode="rel_logpost", tol=1e-12,
-             max_cycles=1000, precision="fp64", history=False) -> dict:
+             max_cycles=1000, precision="fp64", history=False, weights=None) -> dict:
     b0 = None if beta0 is None else np.ascontiguousarray(beta0, np.float64)
     hist = np.full(max_cycles + 1, np.nan) if history else None
+    w = _weights(weights)
     o = sccs_fit_opts(struct_size=ctypes.sizeof(sccs_fit_opts), warm_start=int(bool(warm_start)),
                       beta0=_dptr(b0), tol_mode=TOL[tol_mode], max_cycles=int(max_cycles), tol=float(tol),
-                      precision=PREC[precision], logpost_history=_dptr(hist))
+                      precision=PREC[precision], logpost_history=_dptr(hist), subject_weights=_iptr(w))
     beta = np.zeros(max(J, 1))
     info = sccs_fit_info()
     rc = _check(_lib.sccs_fit(handle, ctypes.byref(o), _dptr(beta), ctypes.byref(info)), "sccs_fit")
@@ -233,6 +247,17 @@ def sccs_logpost(handle, beta=None) -> tuple[float, float]:
     return lp.value, ll.value
 
 
+def sccs_heldout_loglik(handle, weights=None, beta=None) -> float:
+    """Eq. 2 with subject i counted weights[i] times (a held-out fold's mask) at beta, or at the
+    handle's current beta (after a fit: its MAP) when beta is None."""
+    b = None if beta is None else np.ascontiguousarray(beta, np.float64)
+    w = _weights(weights)
+    ll = ctypes.c_double()
+    _check(_lib.sccs_heldout_loglik(handle, _dptr(b), None if w is None else ctypes.c_void_p(w.ctypes.data),
+                                    ctypes.byref(ll)), "sccs_heldout_loglik")
+    return ll.value
+
+
 def sccs_get_beta(handle, J: int) -> np.ndarray:
     b = np.zeros(max(J, 1))
     _check(_lib.sccs_get_beta(handle, _dptr(b)), "sccs_get_beta")
@@ -266,11 +291,13 @@ def sccs_server_create(device=0, max_inflight=64, queue_capacity=4096, hbm_budge
 
 
 def sccs_submit(server, dataset, prior="normal", variance=1.0, tol_mode="rel_logpost", tol=1e-12,
-                max_cycles=1000, precision="fp64", beta0=None) -> int:
+                max_cycles=1000, precision="fp64", beta0=None, weights=None, heldout_weights=None) -> int:
     b0 = None if beta0 is None else np.ascontiguousarray(beta0, np.float64)
+    w, wh = _weights(weights), _weights(heldout_weights)
     r = sccs_request(struct_size=ctypes.sizeof(sccs_request), prior_type=PRIOR[prior], dataset=dataset,
                      variance=float(variance), tol_mode=TOL[tol_mode], max_cycles=int(max_cycles), tol=float(tol),
-                     precision=PREC[precision], reserved=0, beta0=_dptr(b0))
+                     precision=PREC[precision], reserved=0, beta0=_dptr(b0), subject_weights=_iptr(w),
+                     heldout_weights=_iptr(wh))
     t = ctypes.c_uint64()
     _check(_lib.sccs_submit(server, ctypes.byref(r), ctypes.byref(t)), "sccs_submit")
     return t.value
@@ -406,6 +433,9 @@ class SCCSModel:
 
     def logpost(self, beta=None):
         return sccs_logpost(self.handle, beta)
+
+    def heldout_loglik(self, weights=None, beta=None) -> float:
+        return sccs_heldout_loglik(self.handle, weights, beta)
 
     @property
     def beta(self) -> np.ndarray:

@@ -17,5 +17,8 @@ from .sccs_synth import (  # noqa: F401
     serving_outcome,
     serving_requests,
     PRIOR_VARIANCE_GRID,
+    cv_folds,
+    fold_weights,
+    bootstrap_weights,
     CONFIGS,
 )

@@ -304,6 +304,28 @@ def serving_requests(n_requests: int, rate_per_s: float, n_outcomes: int, seed: 
     return out
 
 
+def cv_folds(n_subjects: int, folds: int = 10, seed: int = 1214) -> np.ndarray:
+    """Section 2.5's random split of the subjects into `folds` portions of (nearly) equal size:
+    the fold index 0..folds-1 of each input subject."""
+    rng = np.random.default_rng(seed)
+    fold_of = np.empty(n_subjects, np.int32)
+    fold_of[rng.permutation(n_subjects)] = np.arange(n_subjects) % folds
+    return fold_of
+
+
+def fold_weights(fold_of: np.ndarray, k: int) -> tuple:
+    """(training weights, held-out weights) for fold k: 1 off the fold and 1 on it."""
+    held = (fold_of == k).astype(np.int32)
+    return (1 - held).astype(np.int32), held
+
+
+def bootstrap_weights(n_subjects: int, seed: int) -> np.ndarray:
+    """One non-parametric bootstrap replicate of the subjects (Section 2.5): how many times each
+    input subject is drawn when n_subjects are drawn with replacement."""
+    rng = np.random.default_rng(seed)
+    return rng.multinomial(n_subjects, np.full(n_subjects, 1.0 / n_subjects)).astype(np.int32)
+
+
 CONFIGS = {
     "tiny": tiny_fit_config,
     "mid": mid_fit_config,
