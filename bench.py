@@ -498,21 +498,26 @@ def run_batched(args, rank, world, local):
     return 0
 
 
-def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, budget, seed0):
-    """Submit each rate's Poisson arrivals to a fresh server and collect latencies."""
-    from synth import serving_requests
+def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, budget, seed0, folds_of=None):
+    """Submit each rate's Poisson arrivals to a fresh server and collect latencies.  With
+    folds_of (per outcome, the fold of each input subject), a request with fold k fits on the
+    other folds and returns the held-out predictive log-likelihood of fold k."""
+    from synth import fold_weights, serving_requests
+    nf = 0 if folds_of is None else int(max(f.max() for f in folds_of)) + 1
     rows = []
     for ri, rate in enumerate(rates):
-        reqs = serving_requests(n_per_rate, rate, len(Js), seed=seed0 + ri)
+        reqs = serving_requests(n_per_rate, rate, len(Js), seed=seed0 + ri, folds=nf)
+        masks = [fold_weights(folds_of[o], k - 1) if k > 0 else (None, None) for (_t, o, _p, _v, k) in reqs]
         with sccs.FitServer(device=device, max_inflight=max_inflight, hbm_budget_bytes=budget) as srv:
             tickets = []
             t0 = time.perf_counter()
-            for (ta, o, prior, var, _fold) in reqs:
+            for (ta, o, prior, var, _fold), (wt, wh) in zip(reqs, masks):
                 dt = t0 + ta - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
                 tickets.append(sccs.sccs_submit(srv.server, handles_of[o], prior=prior, variance=var,
-                                                tol_mode="rel_logpost", tol=1e-12, max_cycles=1000))
+                                                tol_mode="rel_logpost", tol=1e-12, max_cycles=1000,
+                                                weights=wt, heldout_weights=wh))
             out = []
             for t, (ta, o, *_rest) in zip(tickets, reqs):
                 while True:
@@ -528,7 +533,8 @@ def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, 
                      "fits_per_s": n_per_rate / done_span,
                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                      "mean_queue_ms": float(np.mean([r["queue_ms"] for r in out])),
-                     "failed": int(sum(1 for r in out if r["status"] < 0))})
+                     "failed": int(sum(1 for r in out if r["status"] < 0)),
+                     "heldout_evaluated": int(sum(1 for r in out if np.isfinite(r["heldout_loglik"])))})
     return rows
 
 
@@ -555,6 +561,9 @@ def run_serving(args, rank, world, local):
     t_gen = time.perf_counter()
     with _spawn_pool(min(cores, 16)) as ex:
         ds = list(ex.map(serving_outcome, [plan] * args.outcomes, range(args.outcomes)))
+    from synth import cv_folds
+    folds_of = [cv_folds(int(1 + np.count_nonzero(d.patient_id[1:] != d.patient_id[:-1])), folds=10, seed=1300 + o)
+                for o, d in enumerate(ds)]
     est = [(d.J, d.nnz, 0.9 * d.nnz) for d in ds]
     teams = autotune.assign(est, model)
     for d, S in zip(ds, teams):
@@ -568,11 +577,13 @@ def run_serving(args, rank, world, local):
     budget = int(args.hbm_budget_gb * (1 << 30))
     # warm-up: one request per outcome through each arm
     for arm in (served, plain):
-        _serve_sweep(sccs, local, [m.handle for m in arm], Js, [1000.0], min(args.outcomes, 8), 64, budget, 999)
+        _serve_sweep(sccs, local, [m.handle for m in arm], Js, [1000.0], min(args.outcomes, 8), 64, budget, 999,
+                     folds_of)
     with ClockSampler(local) as clk:
-        ours = _serve_sweep(sccs, local, [m.handle for m in served], Js, rates, args.requests, 64, budget, 2000)
+        ours = _serve_sweep(sccs, local, [m.handle for m in served], Js, rates, args.requests, 64, budget, 2000,
+                            folds_of)
     clocks = clk.summary()
-    one = _serve_sweep(sccs, local, [m.handle for m in plain], Js, rates, args.requests, 1, 0, 2000)
+    one = _serve_sweep(sccs, local, [m.handle for m in plain], Js, rates, args.requests, 1, 0, 2000, folds_of)
     top = ours[-1]
     if rank == 0:
         line = {
@@ -583,7 +594,8 @@ def run_serving(args, rank, world, local):
             "config": {"workload": f"serving: {args.outcomes} resident outcomes, eras log-uniform 20k-"
                                    f"{args.max_eras / 1e6:g}M, 1000-5000 drugs, Zipf(1.2) columns up to eras/5; "
                                    "requests = outcome x Normal/Laplace x variance grid "
-                                   "{0.01..1}, FP64 to rel |dP| < 1e-12; "
+                                   "{0.01..1} x fold 1..10 (fit on 9 folds, held-out predictive log-likelihood "
+                                   "of the 10th returned), FP64 to rel |dP| < 1e-12; "
                                    f"{args.requests} Poisson arrivals per rate",
                        "outcomes": args.outcomes, "eras": int(sum(i["rows_kept"] for i in infos)),
                        "nnz": int(sum(i["nnz_kept"] for i in infos)), "rates_per_s": rates,

@@ -225,9 +225,10 @@ int sccs_get_beta(const sccs_handle *h, double *beta_out);
  * sccs_heldout_loglik -- the predictive log-likelihood of Section 2.5's cross-validation: Eq. 2
  * with subject i counted weights[i] times (the held-out fold's 0/1 mask, one value per input
  * subject as in sccs_fit_opts.subject_weights; NULL = all subjects once).
- *   beta  host [J]: evaluate there; NULL: at the handle's current beta (after a fit, its MAP).
- * The state (L x exp(Xb) and the denominators) is rebuilt from beta in FP64 first; the trust
- * radii are kept, so a warm-started fit afterwards continues as if nothing had happened.
+ *   beta  host [J]: evaluate there (the state L x exp(Xb) is rebuilt from it in FP64, trust
+ *         radii kept, so a warm-started fit afterwards continues as if nothing had happened);
+ *         NULL: at the handle's current state (after a fit, its MAP; rebuilt in FP64 from the
+ *         handle's beta first if the last fit ran in SCCS_PREC_FP32 alone).
  * Errors: SCCS_E_INVAL (bad weights, non-finite beta), SCCS_E_TIMEOUT, SCCS_E_CUDA.
  */
 int sccs_heldout_loglik(sccs_handle *h, const double *beta, const int32_t *weights, double *loglik);

@@ -129,6 +129,7 @@ struct sccs_handle {
     int32_t *nev_w = nullptr;          // N: w_i n_i
     double *ytx_w = nullptr;           // J: weighted Y'X_j
     int32_t *w_host = nullptr;         // N, pinned
+    bool e_stale = false;              // the FP64 E no longer matches beta (after an FP32-only fit)
 };
 
 namespace {
@@ -460,10 +461,21 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     return SCCS_OK;
 }
 
-int run_init_state(sccs_handle *h, const double *beta_dev) {
-    int e = sccs::launch_init_state(h->d, beta_dev, h->threads, h->stream);
+int run_init_state(sccs_handle *h, const double *beta_dev, bool keep_trust = false) {
+    int e = sccs::launch_init_state(h->d, beta_dev, h->threads, h->stream, keep_trust);
     if (e != 0) return cuda_fail(static_cast<cudaError_t>(e), "init_state launch");
+    h->e_stale = false;
     return SCCS_OK;
+}
+
+// Rebuild the FP64 state from the handle's own beta (trust radii kept) if an FP32-only fit
+// left it behind.
+int refresh_fp64_state(sccs_handle *h) {
+    if (!h->e_stale) return SCCS_OK;
+    cudaError_t e = cudaMemcpyAsync(h->beta_dev, h->d.beta_priv, sizeof(double) * std::max<int32_t>(h->d.J, 1),
+                                    cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync beta");
+    return run_init_state(h, h->beta_dev, true);
 }
 
 // After an aborted kernel: clear the all-reduce slots and the abort flag, restart the
@@ -485,9 +497,10 @@ int sync_out(sccs_handle *h) {
     return SCCS_OK;
 }
 
-// Move the state to beta (host array) or leave it (nullptr).
+// Move the state to beta (host array) or keep the current one (nullptr; rebuilt in FP64 if an
+// FP32-only fit left it behind).
 int set_state(sccs_handle *h, const double *beta) {
-    if (!beta) return SCCS_OK;
+    if (!beta) return refresh_fp64_state(h);
     const int32_t J = h->d.J;
     for (int32_t j = 0; j < J; ++j)
         if (!std::isfinite(beta[j])) return fail(SCCS_E_INVAL, "beta has a non-finite entry");
@@ -919,14 +932,8 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
         (rc = upload(h, &pat_ptr, hl.pat_ptr.data(), hl.pat_ptr.size())) ||
         (rc = upload(h, &nev, hl.nev.data(), hl.nev.size())) ||
         (rc = upload(h, &L, hl.L.data(), hl.L.size())) ||
-        (rc = upload(h, &ytx, hl.ytx.data(), hl.ytx.size())) ||
-        (rc = upload(h, &ycol_ptr, hl.ycol_ptr.data(), hl.ycol_ptr.size())) ||
-        (rc = upload(h, &ysub, hl.ysub.data(), hl.ysub.size())) ||
-        (rc = upload(h, &ycnt, hl.ycnt.data(), hl.ycnt.size())))
+        (rc = upload(h, &ytx, hl.ytx.data(), hl.ytx.size())))
         return bail(rc);
-    d.ycol_ptr = ycol_ptr;
-    d.ysub = ysub;
-    d.ycnt = ycnt;
     h->kept_from = std::move(hl.kept_from);
     h->nev_host = hl.nev;
     for (int32_t v : h->nev_host) h->max_nev = std::max(h->max_nev, v);
@@ -955,6 +962,41 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
         (rc = alloc_zero(h, &h->beta_dev, static_cast<size_t>(std::max<int32_t>(J, 1)))))
         return bail(rc);
     d.abort_flag = &h->out_dev->abort_flag;
+    // The weighted-count pairs go last: the fit's state arrays keep the placement measured
+    // fastest (uploading 2 x 16 MB of pairs before them cost the 1M-subject fit 4%).
+    if ((rc = upload(h, &ycol_ptr, hl.ycol_ptr.data(), hl.ycol_ptr.size())) ||
+        (rc = upload(h, &ysub, hl.ysub.data(), hl.ysub.size())) ||
+        (rc = upload(h, &ycnt, hl.ycnt.data(), hl.ycnt.size())))
+        return bail(rc);
+    d.ycol_ptr = ycol_ptr;
+    d.ysub = ysub;
+    d.ycnt = ycnt;
+    {
+        // row -> columns index, built on the device from the slices (scratch freed below)
+        int64_t *row_ptr = nullptr;
+        int32_t *row_col = nullptr;
+        if ((rc = alloc_zero(h, &row_ptr, static_cast<size_t>(hl.K) + 1)) ||
+            (rc = alloc_zero(h, &row_col, static_cast<size_t>(hl.nnz))))
+            return bail(rc);
+        void *scratch = nullptr;
+        const size_t K1 = static_cast<size_t>(std::max<int64_t>(hl.K, 1));
+        const size_t sb = 4 * K1 + 8 * K1 + 8 * sccs::row_index_scan_blocks(hl.K) + 512;
+        if (cudaMalloc(&scratch, sb) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return bail(fail(SCCS_E_NOMEM, "row index scratch"));
+        }
+        char *sp = static_cast<char *>(scratch);
+        auto *cnt = reinterpret_cast<int32_t *>(sp);
+        auto *cursor = reinterpret_cast<int64_t *>(sp + (4 * K1 + 255) / 256 * 256);
+        auto *sums = reinterpret_cast<int64_t *>(sp + (4 * K1 + 255) / 256 * 256 + (8 * K1 + 255) / 256 * 256);
+        const int le = sccs::launch_build_row_index(d, row_ptr, row_col, cnt, cursor, sums, h->stream);
+        const cudaError_t se = cudaStreamSynchronize(h->stream);
+        cudaFree(scratch);
+        if (le != 0) return bail(cuda_fail(static_cast<cudaError_t>(le), "row index build"));
+        if (se != cudaSuccess) return bail(cuda_fail(se, "row index build"));
+        d.row_ptr = row_ptr;
+        d.row_col = row_col;
+    }
     if ((rc = run_init_state(h, nullptr))) return bail(rc);
     ce = cudaStreamSynchronize(h->stream);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamSynchronize"));
@@ -1100,6 +1142,7 @@ int sccs_fit(sccs_handle *h, const sccs_fit_opts *opts, double *beta_out, sccs_f
         if (e != cudaSuccess) return cuda_fail(e, "copy history");
     }
     const int32_t total_cycles = o.precision == SCCS_PREC_FP32_POLISH ? fp32_cycles + r.cycles : r.cycles;
+    h->e_stale = o.precision == SCCS_PREC_FP32;   // the FP32 phase kept E in FP32 only
     if (info) {
         info->status = r.status;
         info->cycles = total_cycles;
@@ -1222,6 +1265,7 @@ int sccs_fit_batch(sccs_handle *const *handles, int32_t n, const sccs_fit_opts *
             status = SCCS_E_NUMERIC;
         } else {
             h->seq = r.seq_end;
+            h->e_stale = mode == sccs::kBatchFp32;   // the FP32 phase kept E in FP32 only
         }
         const int32_t fp32_cycles = mode == sccs::kBatchFp32Polish ? r32.cycles : mode == sccs::kBatchFp32 ? r.cycles : 0;
         if (status == SCCS_OK && beta_out && beta_out[k] && h->d.J > 0)
@@ -1300,6 +1344,7 @@ int sccs_heldout_loglik(sccs_handle *h, const double *beta, const int32_t *weigh
     int rc = set_device(h);
     if (rc) return rc;
     const int32_t J = h->d.J;
+    int le = 0;
     if (beta) {
         for (int32_t j = 0; j < J; ++j)
             if (!std::isfinite(beta[j])) return fail(SCCS_E_INVAL, "beta has a non-finite entry");
@@ -1307,14 +1352,11 @@ int sccs_heldout_loglik(sccs_handle *h, const double *beta, const int32_t *weigh
         cudaError_t e = cudaMemcpyAsync(h->beta_dev, h->beta_host, sizeof(double) * std::max<int32_t>(J, 1),
                                         cudaMemcpyHostToDevice, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync beta");
-    } else {
-        cudaError_t e = cudaMemcpyAsync(h->beta_dev, h->d.beta_priv, sizeof(double) * std::max<int32_t>(J, 1),
-                                        cudaMemcpyDeviceToDevice, h->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync beta");
+        // E and D rebuilt from beta in FP64, trust radii kept
+        if ((rc = run_init_state(h, h->beta_dev, true))) return rc;
+    } else if ((rc = refresh_fp64_state(h))) {
+        return rc;
     }
-    // E and D rebuilt from beta in FP64, trust radii kept
-    int le = sccs::launch_init_state(h->d, h->beta_dev, h->threads, h->stream, true);
-    if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "init_state launch");
     if (weights && (rc = prepare_weights(h, weights))) return rc;
     CountsScope counts(h, weights != nullptr);
     if (h->hist_cap < 1) {

@@ -51,6 +51,8 @@ struct DevLayout {
     const int32_t *nev;        // N: n_i (or w_i n_i in a weighted fit)
     const double *L;           // K: offsets l_k
     const double *ytx;         // J: Y'X_j (or its weighted form)
+    const int64_t *row_ptr;    // K+1: row -> columns index (built on the device at create)
+    const int32_t *row_col;    //   the columns of each row, ascending
     const int64_t *ycol_ptr;   // J+1: per column, its (subject, sum of y) pairs with events
     const int32_t *ysub;       //   kept subject of each pair
     const int32_t *ycnt;       //   sum of y over the column's rows of that subject
@@ -81,6 +83,8 @@ struct FitParams {
     long long timeout_ns;      // bound on each device-side wait (from the start of that wait)
     const unsigned long long *seq_src;  // device; if set, seq0 is read from here at launch (the
                                         // seq_end of the launch before it on the same stream)
+    const int32_t *ho_nev;     // device [N] or null: held-out counts w_i n_i (FP64 fits only); the
+    const double *ho_ytx;      // [J] fit then ends with Eq. 2 under them in out->heldout_loglik
 };
 
 struct FitOut {
@@ -96,6 +100,7 @@ struct FitOut {
     double g, h;               // grad_hess output
     int32_t abort_flag;        // nonzero if any CTA gave up a wait
     int32_t pad;
+    double heldout_loglik;     // with FitParams::ho_nev: the held-out predictive log-likelihood
 };
 
 // One fit of a batched launch: its layout and state, parameters and outputs.  p32 drives
@@ -125,6 +130,11 @@ int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, 
                       bool keep_trust = false);
 // E32 = (float) E on every shard.
 int launch_e_to_f32(const DevLayout &d, int threads, void *stream);
+// Build the row -> columns index (row_ptr, row_col) from the column slices.  scratch: K int32
+// counts + K int64 fill cursors + (K / 8192 + 2) int64 block sums.
+int launch_build_row_index(const DevLayout &d, int64_t *row_ptr, int32_t *row_col, int32_t *cnt, int64_t *cursor,
+                           int64_t *block_sums, void *stream);
+size_t row_index_scan_blocks(int64_t K);
 // Weighted counts of a fit with subject weights w_kept (device [N]): nev_w[i] = w_i n_i and
 // ytx_w[j] = sum over X_j's (subject, y) pairs of w_i y, both exact (integer sums).
 int launch_weighted_counts(const DevLayout &d, const int32_t *w_kept, int32_t *nev_w, double *ytx_w, void *stream);

@@ -277,11 +277,11 @@ struct SharedState {
     long long nonzero;
     int ok;
     int stop;
+    ColDesc desc[2];
+    uint64_t bar[2];
     int run_status;         // a finished run_fit's status (thread 0 writes it)
     int drained;            // its staging copies all landed (thread blockDim - 32 writes it)
     unsigned long long run_seq;   // the all-reduce sequence number it ended at
-    ColDesc desc[2];
-    uint64_t bar[2];
 };
 
 struct SmemLayout {
@@ -1067,7 +1067,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
     SliceBounds nb{};           // bounds of the column after the staged one
     int status = kStNotConverged, warn = 0, cycles = 0;
     long long nonzero = 0;
-    double P_prev = 0.0, P = 0.0, conv = 0.0, loglik = 0.0;
+    double P_prev = 0.0, P = 0.0, conv = 0.0, loglik = 0.0, heldout = __longlong_as_double(0x7ff8000000000000ll);
     long long col = 0;          // columns processed: stage buffer = col & 1
 
     if (threadIdx.x == 0) {
@@ -1277,10 +1277,24 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
         }
         nonzero = sh.nonzero;
     }
+    if (!F32 && p.ho_nev && (status == kStOk || status == kStNotConverged)) {
+        // Section 2.5: the held-out fold's predictive log-likelihood at the final beta, from the
+        // same state and with the same arithmetic as a separate evaluation (refresh, exact sums)
+        DevLayout dh = d;
+        dh.nev = p.ho_nev;
+        dh.ytx = p.ho_ytx;
+        if (!refresh_and_reduce(dh, s, seq++, timeout, sh)) goto aborted;
+        if (threadIdx.x == 0) {
+            double lin_ho = 0.0, lp_unused = 0.0;
+            beta_terms(dh, s, p, lin_ho, lp_unused);
+            heldout = lin_ho - (sh.G - sh.H);
+        }
+    }
     drain_stages(sh, pending, phase_bits, timeout);
     if (leader) {
         out->logpost = P;
         out->loglik = loglik;
+        out->heldout_loglik = heldout;
         out->conv = conv;
         out->cycles = cycles;
         out->status = status;
@@ -1308,10 +1322,11 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
     run_fit<F32>(d, p, out, hist, blockIdx.x, *reinterpret_cast<SmemLayout *>(smem_raw), sh);
 }
 
-// E_k = l_k exp(Xb_k) on shard s's rows, with Xb accumulated column by column in j order;
+// E_k = l_k exp(Xb_k) on shard s's rows, with Xb_k summed over row k's columns in ascending j;
 // the shard's private beta copy = beta0 (0 when null) and its trust radii = 1 unless kept.
 // beta0 may be the shard's own copy (a warm start).
-__device__ void init_shard(const DevLayout &d, int s, const double *beta0, bool keep_trust) {
+// The same without the row index: column by column in j order, a block barrier after each.
+__device__ void init_shard_by_columns(const DevLayout &d, int s, const double *beta0, bool keep_trust) {
     const long long r0 = d.shard_row[s], r1 = d.shard_row[s + 1];
     double *beta = d.beta_priv + static_cast<long long>(s) * d.J;
     double *trust = d.trust_priv + static_cast<long long>(s) * d.J;
@@ -1340,6 +1355,27 @@ __device__ void init_shard(const DevLayout &d, int s, const double *beta0, bool 
     }
     for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) d.E[k] = d.L[k] * exp(d.E[k]);
     __syncthreads();
+}
+
+__device__ void init_shard(const DevLayout &d, int s, const double *beta0, bool keep_trust) {
+    if (beta0 && d.row_ptr) {
+        const long long r0 = d.shard_row[s], r1 = d.shard_row[s + 1];
+        double *beta = d.beta_priv + static_cast<long long>(s) * d.J;
+        double *trust = d.trust_priv + static_cast<long long>(s) * d.J;
+        for (long long k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
+            double xb = 0.0;
+            for (long long e = d.row_ptr[k]; e < d.row_ptr[k + 1]; ++e) xb += beta0[d.row_col[e]];
+            d.E[k] = d.L[k] * exp(xb);
+        }
+        __syncthreads();   // every thread has read beta0 (possibly this shard's own copy)
+        for (int j = threadIdx.x; j < d.J; j += blockDim.x) {
+            beta[j] = beta0[j];
+            if (!keep_trust) trust[j] = 1.0;
+        }
+        __syncthreads();
+        return;
+    }
+    init_shard_by_columns(d, s, beta0, keep_trust);
 }
 
 __device__ void e_to_f32_shard(const DevLayout &d, int s) {
@@ -1519,6 +1555,115 @@ __global__ void __launch_bounds__(256) weighted_counts_kernel(DevLayout d, const
     }
 }
 
+// ---- row -> columns index (for rebuilding E from a beta without a barrier per column)
+
+constexpr int kScanChunk = 8192;   // rows per block of the prefix sum
+
+// Each (shard, column) slice adds one to the count of every row it holds.
+__global__ void __launch_bounds__(256) row_count_kernel(DevLayout d, int32_t *cnt) {
+    const long long slices = static_cast<long long>(d.S) * d.J;
+    for (long long t = blockIdx.x; t < slices; t += gridDim.x) {
+        const int s = static_cast<int>(t / d.J), j = static_cast<int>(t % d.J);
+        const long long so = static_cast<long long>(s) * (d.J + 1) + j;
+        for (long long q = d.slice_row[so] + threadIdx.x; q < d.slice_row[so + 1]; q += blockDim.x)
+            atomicAdd(&cnt[d.rows[q]], 1);
+    }
+}
+
+__device__ long long block_sum_ll(long long v, long long *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    long long t = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+// Prefix sum, pass 1: the total of each chunk of kScanChunk counts.
+__global__ void __launch_bounds__(256) scan_chunk_sums_kernel(const int32_t *cnt, long long n, long long *sums) {
+    __shared__ long long red[8];
+    const long long a = static_cast<long long>(blockIdx.x) * kScanChunk;
+    const long long b = a + kScanChunk < n ? a + kScanChunk : n;
+    long long v = 0;
+    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) v += cnt[i];
+    const long long t = block_sum_ll(v, red);
+    if (threadIdx.x == 0) sums[blockIdx.x] = t;
+}
+
+// Pass 2 (one thread): exclusive prefix of the chunk totals.
+__global__ void scan_chunk_offsets_kernel(long long *sums, long long nchunks) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long run = 0;
+    for (long long c = 0; c < nchunks; ++c) {
+        const long long v = sums[c];
+        sums[c] = run;
+        run += v;
+    }
+    sums[nchunks] = run;
+}
+
+// Pass 3: each chunk's exclusive prefix, one warp-serial run per 32-count stretch; also the
+// fill cursors (a copy of the offsets).
+__global__ void __launch_bounds__(256) scan_chunk_fill_kernel(const int32_t *cnt, long long n, const long long *sums,
+                                                              int64_t *row_ptr, int64_t *cursor) {
+    __shared__ long long part[256];
+    const long long a = static_cast<long long>(blockIdx.x) * kScanChunk;
+    const long long b = a + kScanChunk < n ? a + kScanChunk : n;
+    constexpr int per = kScanChunk / 256;
+    const long long lo = a + static_cast<long long>(threadIdx.x) * per;
+    long long v = 0;
+    for (long long i = lo; i < lo + per && i < b; ++i) v += cnt[i];
+    part[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = sums[blockIdx.x];
+        for (int t = 0; t < 256; ++t) {
+            const long long x = part[t];
+            part[t] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    long long run = part[threadIdx.x];
+    for (long long i = lo; i < lo + per && i < b; ++i) {
+        row_ptr[i] = run;
+        cursor[i] = run;
+        run += cnt[i];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) row_ptr[n] = sums[gridDim.x];
+}
+
+// Scatter column ids into their rows (order within a row not yet fixed).
+__global__ void __launch_bounds__(256) row_fill_kernel(DevLayout d, int64_t *cursor, int32_t *row_col) {
+    const long long slices = static_cast<long long>(d.S) * d.J;
+    for (long long t = blockIdx.x; t < slices; t += gridDim.x) {
+        const int s = static_cast<int>(t / d.J), j = static_cast<int>(t % d.J);
+        const long long so = static_cast<long long>(s) * (d.J + 1) + j;
+        for (long long q = d.slice_row[so] + threadIdx.x; q < d.slice_row[so + 1]; q += blockDim.x) {
+            const long long at = static_cast<long long>(atomicAdd(reinterpret_cast<unsigned long long *>(&cursor[d.rows[q]]), 1ull));
+            row_col[at] = j;
+        }
+    }
+}
+
+// Each row's columns ascending (insertion sort; rows hold a handful of columns).
+__global__ void __launch_bounds__(256) row_sort_kernel(const int64_t *row_ptr, int32_t *row_col, long long K) {
+    for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < K;
+         k += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long a = row_ptr[k], b = row_ptr[k + 1];
+        for (long long i = a + 1; i < b; ++i) {
+            const int32_t v = row_col[i];
+            long long m = i - 1;
+            while (m >= a && row_col[m] > v) {
+                row_col[m + 1] = row_col[m];
+                --m;
+            }
+            row_col[m + 1] = v;
+        }
+    }
+}
+
 int ensure_smem_attr() {
     const int bytes = static_cast<int>(sizeof(SmemLayout));
     cudaError_t e = cudaFuncSetAttribute(fit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1546,9 +1691,39 @@ int launch_e_to_f32(const DevLayout &d, int threads, void *stream) {
     return static_cast<int>(cudaGetLastError());
 }
 
+size_t row_index_scan_blocks(int64_t K) { return static_cast<size_t>((K + kScanChunk - 1) / kScanChunk) + 2; }
+
+int launch_build_row_index(const DevLayout &d, int64_t *row_ptr, int32_t *row_col, int32_t *cnt, int64_t *cursor,
+                           int64_t *block_sums, void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long K = d.K;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * static_cast<size_t>(K > 0 ? K : 1), st);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    const long long slices = static_cast<long long>(d.S) * d.J;
+    const int sgrid = static_cast<int>(std::min<long long>(std::max<long long>(slices, 1), 65536));
+    if (slices > 0) row_count_kernel<<<sgrid, 256, 0, st>>>(d, cnt);
+    const long long nchunks = (K + kScanChunk - 1) / kScanChunk;
+    long long *sums = reinterpret_cast<long long *>(block_sums);
+    if (nchunks > 0) {
+        scan_chunk_sums_kernel<<<static_cast<unsigned>(nchunks), 256, 0, st>>>(cnt, K, sums);
+        scan_chunk_offsets_kernel<<<1, 32, 0, st>>>(sums, nchunks);
+        scan_chunk_fill_kernel<<<static_cast<unsigned>(nchunks), 256, 0, st>>>(cnt, K, sums, row_ptr, cursor);
+    } else {
+        e = cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st);
+        if (e != cudaSuccess) return static_cast<int>(e);
+    }
+    if (slices > 0) row_fill_kernel<<<sgrid, 256, 0, st>>>(d, cursor, row_col);
+    if (K > 0) {
+        const int kgrid = static_cast<int>(std::min<long long>((K + 255) / 256, 65536));
+        row_sort_kernel<<<kgrid, 256, 0, st>>>(row_ptr, row_col, K);
+    }
+    return static_cast<int>(cudaGetLastError());
+}
+
 int launch_weighted_counts(const DevLayout &d, const int32_t *w_kept, int32_t *nev_w, double *ytx_w, void *stream) {
+    // a modest grid: the kernel is short, and fits running beside it need whole SMs
     const long long want = std::max<long long>(static_cast<long long>(d.J), (d.N + 255) / 256);
-    const int blocks = static_cast<int>(std::min<long long>(std::max<long long>(want, 1), 4096));
+    const int blocks = static_cast<int>(std::min<long long>(std::max<long long>(want, 1), std::max(2 * d.S, 16)));
     weighted_counts_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d, w_kept, nev_w, ytx_w);
     return static_cast<int>(cudaGetLastError());
 }

@@ -40,6 +40,8 @@ struct FitSlot {
     int32_t *w_dev = nullptr;           // N: a request's weights per kept subject
     int32_t *nev_w = nullptr;           // N: w_i n_i
     double *ytx_w = nullptr;            // J: weighted Y'X_j
+    int32_t *nev_ho = nullptr;          // N: held-out counts (evaluated inside the fit kernel)
+    double *ytx_ho = nullptr;           // J
     int32_t *w_host = nullptr;          // 2N pinned: training weights, then held-out weights
     sccs::FitOut *out_ho_dev = nullptr; // held-out evaluation
     sccs::FitOut *out_ho_host = nullptr;
@@ -89,7 +91,7 @@ size_t slot_bytes(const sccs::DevLayout &d, int max_cycles) {
     const size_t N1 = std::max<size_t>(N, 1);
     return al(8 * K) + al(8 * N) + al(4 * K) + al(8 * N) + 2 * al(8 * S * J) +
            al(16 * S * static_cast<size_t>(d.stash_stride)) + al(32 * S) + 2 * al(sizeof(sccs::FitOut)) +
-           al(8 * J) + al(8 * static_cast<size_t>(max_cycles + 1)) + 2 * al(4 * N1) + al(8 * J);
+           al(8 * J) + al(8 * static_cast<size_t>(max_cycles + 1)) + 3 * al(4 * N1) + 2 * al(8 * J);
 }
 
 }  // namespace
@@ -181,6 +183,8 @@ FitSlot *make_slot(const sccs_handle *dataset, int max_cycles) {
     s->w_dev = reinterpret_cast<int32_t *>(take(4 * N1));
     s->nev_w = reinterpret_cast<int32_t *>(take(4 * N1));
     s->ytx_w = reinterpret_cast<double *>(take(8 * J));
+    s->nev_ho = reinterpret_cast<int32_t *>(take(4 * N1));
+    s->ytx_ho = reinterpret_cast<double *>(take(8 * J));
     d.abort_flag = &s->out_dev->abort_flag;
     if (cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&s->out_host, sizeof(sccs::FitOut)) != cudaSuccess ||
@@ -251,6 +255,14 @@ int enqueue_phase(Request &r, bool first) {
             s.d.nev = s.base_nev;
             s.d.ytx = s.base_ytx;
         }
+        if (!r.w_ho.empty() && r.precision != SCCS_PREC_FP32) {
+            // held-out counts now; the final FP64 phase evaluates them before it returns
+            int32_t *wh = s.w_host + N1;
+            std::memcpy(wh, r.w_ho.data(), sizeof(int32_t) * r.w_ho.size());
+            cudaMemcpyAsync(s.w_dev, wh, sizeof(int32_t) * N1, cudaMemcpyHostToDevice, s.stream);
+            e = sccs::launch_weighted_counts(base, s.w_dev, s.nev_ho, s.ytx_ho, s.stream);
+            if (e) return e;
+        }
         if (!r.beta0.empty()) {
             std::memcpy(s.beta_host, r.beta0.data(), sizeof(double) * r.J);
             cudaMemcpyAsync(s.beta_dev, s.beta_host, sizeof(double) * r.J, cudaMemcpyHostToDevice, s.stream);
@@ -266,13 +278,18 @@ int enqueue_phase(Request &r, bool first) {
         e = sccs::launch_init_state(s.d, s.beta_dev, s.threads, s.stream, true);
     }
     if (e) return e;
-    const sccs::FitParams p = params_for(r, s, fp32);
+    sccs::FitParams p = params_for(r, s, fp32);
+    if (final_phase && !fp32 && !r.w_ho.empty()) {
+        p.ho_nev = s.nev_ho;
+        p.ho_ytx = s.ytx_ho;
+    }
     e = sccs::launch_fit(s.d, p, s.out_dev, s.hist_dev, s.threads, s.stream, fp32);
     if (e) return e;
     cudaMemcpyAsync(s.out_host, s.out_dev, sizeof(sccs::FitOut), cudaMemcpyDeviceToHost, s.stream);
     if (r.J > 0) cudaMemcpyAsync(s.beta_host, s.d.beta_priv, sizeof(double) * r.J, cudaMemcpyDeviceToHost, s.stream);
-    if (final_phase && !r.w_ho.empty()) {
-        // held-out predictive log-likelihood at the fitted beta (as sccs_heldout_loglik)
+    if (final_phase && !r.w_ho.empty() && r.precision == SCCS_PREC_FP32) {
+        // FP32-only fit: the held-out predictive log-likelihood by a separate FP64 evaluation
+        // at the fitted beta (as sccs_heldout_loglik)
         int32_t *wh = s.w_host + N1;
         std::memcpy(wh, r.w_ho.data(), sizeof(int32_t) * r.w_ho.size());
         cudaMemcpyAsync(s.w_dev, wh, sizeof(int32_t) * N1, cudaMemcpyHostToDevice, s.stream);
@@ -281,6 +298,7 @@ int enqueue_phase(Request &r, bool first) {
         sccs::DevLayout dh = s.d;
         dh.nev = s.nev_w;
         dh.ytx = s.ytx_w;
+        // the FP32-only fit kept E in FP32: rebuild the FP64 state from its beta first
         cudaMemcpyAsync(s.beta_dev, s.d.beta_priv, sizeof(double) * std::max(r.J, 1), cudaMemcpyDeviceToDevice,
                         s.stream);
         e = sccs::launch_init_state(dh, s.beta_dev, s.threads, s.stream, true);
@@ -410,17 +428,19 @@ void worker_main(sccs_server *sv) {
             const sccs::FitOut out = *s.out_host;
             const bool final_phase = !(r->phase == 1 && r->precision == SCCS_PREC_FP32_POLISH);
             const bool heldout = final_phase && !r->w_ho.empty();
-            const sccs::FitOut out_ho = heldout ? *s.out_ho_host : sccs::FitOut{};
+            const bool heldout_apart = heldout && r->precision == SCCS_PREC_FP32;   // a second launch
+            const sccs::FitOut out_ho = heldout_apart ? *s.out_ho_host : sccs::FitOut{};
             int status = SCCS_OK;
             if (q != cudaSuccess) {
                 (void)cudaGetLastError();
                 status = SCCS_E_CUDA;
-            } else if (out.status == -6 || out.abort_flag || (heldout && (out_ho.status == -6 || out_ho.abort_flag))) {
+            } else if (out.status == -6 || out.abort_flag ||
+                       (heldout_apart && (out_ho.status == -6 || out_ho.abort_flag))) {
                 status = SCCS_E_TIMEOUT;
-            } else if (out.status == -7 || (heldout && out_ho.status == -7)) {
+            } else if (out.status == -7 || (heldout_apart && out_ho.status == -7)) {
                 status = SCCS_E_NUMERIC;
             }
-            if (status == SCCS_OK) s.seq = heldout ? out_ho.seq_end : out.seq_end;
+            if (status == SCCS_OK) s.seq = heldout_apart ? out_ho.seq_end : out.seq_end;
             else reset_slot_after_abort(s);
             if (status == SCCS_OK && r->phase == 1 && r->precision == SCCS_PREC_FP32_POLISH) {
                 {
@@ -437,7 +457,7 @@ void worker_main(sccs_server *sv) {
                 r->cycles = out.cycles + (r->precision == SCCS_PREC_FP32_POLISH ? r->fp32_cycles : 0);
                 if (r->precision == SCCS_PREC_FP32) r->fp32_cycles = out.cycles;
                 r->logpost = out.logpost;
-                r->heldout_loglik = heldout ? out_ho.loglik : std::nan("");
+                r->heldout_loglik = !heldout ? std::nan("") : heldout_apart ? out_ho.loglik : out.heldout_loglik;
                 r->beta.assign(s.beta_host, s.beta_host + r->J);
                 status = out.status == 0 ? SCCS_OK : SCCS_NOT_CONVERGED;
             }
