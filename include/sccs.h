@@ -79,6 +79,11 @@ typedef struct sccs_create_opts {
     sccs_alloc_fn alloc;       /* NULL = cudaMalloc */
     sccs_free_fn free;
     void *alloc_ctx;
+    int32_t narrow_max_nnz;    /* columns with at most this many nonzeros (and at most 2048
+                                  subjects) run whole on one CTA of the team with block-level sums
+                                  instead of a grid-wide reduction per coordinate (FP64 fits,
+                                  4 or more shards): 0 = the default 1024; < 0 = never */
+    int32_t reserved;
 } sccs_create_opts;
 
 typedef struct sccs_data_info {
@@ -92,7 +97,7 @@ typedef struct sccs_data_info {
     int32_t columns;                    /* J */
     int32_t num_shards;
     int32_t threads_per_block;
-    int32_t reserved;
+    int32_t narrow_columns;             /* columns run whole on one CTA (see narrow_max_nnz) */
 } sccs_data_info;
 
 typedef struct sccs_fit_opts {

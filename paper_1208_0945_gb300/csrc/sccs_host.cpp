@@ -203,7 +203,17 @@ struct HostLayout {
     std::vector<int64_t> kept_from;   // N: input subject of each kept subject
     std::vector<int64_t> ycol_ptr;    // J+1: per column, (subject, sum of y) pairs with events
     std::vector<int32_t> ysub, ycnt;
+    // narrow columns (whole column on one CTA)
+    int32_t narrow_count = 0, first_wide = -1;
+    std::vector<uint8_t> narrow;      // J
+    std::vector<int32_t> next_wide;   // J
+    std::vector<int64_t> nar_ptr;     // J+1
+    std::vector<int4> nar_seg;        // {subject, rows, first row in nar_row, 0}
+    std::vector<int32_t> nar_row;
 };
+
+constexpr int32_t kNarrowDefault = 1024;
+constexpr int32_t kNarrowMinShards = 4;
 
 // Checks everything about the inputs that needs no GPU.
 int validate_inputs(int64_t K, const int64_t *patient_id, const int32_t *y, const double *Lin, int32_t J,
@@ -235,7 +245,7 @@ int validate_inputs(int64_t K, const int64_t *patient_id, const int32_t *y, cons
 }
 
 int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const double *Lin, int32_t J,
-                 const int64_t *col_ptr, const int32_t *row_idx, int32_t S, HostLayout &hl) {
+                 const int64_t *col_ptr, const int32_t *row_idx, int32_t S, int32_t narrow_max, HostLayout &hl) {
     // ---- subjects, n_i, dropping n_i = 0
     std::vector<int64_t> sub_start;
     std::vector<int64_t> sub_n;
@@ -354,6 +364,66 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
                 hl.ycnt[q] += static_cast<int32_t>(ykept[r]);   // <= n_i < 2^31
             }
         });
+    }
+
+    // ---- narrow columns: few rows and subjects, run whole on one CTA (rows ascending, so a
+    //      subject's rows are adjacent and its segment is a run)
+    hl.narrow.assign(static_cast<size_t>(J), 0);
+    hl.next_wide.assign(static_cast<size_t>(J), 0);
+    hl.nar_ptr.assign(static_cast<size_t>(J) + 1, 0);
+    if (narrow_max > 0 && S >= kNarrowMinShards) {
+        std::vector<int64_t> nseg(static_cast<size_t>(J), 0);
+        parallel_for(J, [&](int64_t j) {
+            int64_t c = 0;
+            int32_t cur = -1;
+            for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e)
+                if (row_pat[crow[e]] != cur) {
+                    cur = row_pat[crow[e]];
+                    ++c;
+                }
+            nseg[j] = c;
+        });
+        int64_t rows_total = 0;
+        for (int32_t j = 0; j < J; ++j) {
+            const int64_t n = cptr[j + 1] - cptr[j];
+            const bool fits = n <= narrow_max && n <= sccs::kRowCap && nseg[j] <= sccs::kSegCap &&
+                              rows_total + n < (int64_t(1) << 31);
+            hl.narrow[j] = fits ? 1 : 0;
+            hl.nar_ptr[j + 1] = hl.nar_ptr[j] + (fits ? nseg[j] : 0);
+            if (fits) {
+                rows_total += n;
+                hl.narrow_count++;
+            }
+        }
+        hl.nar_seg.resize(static_cast<size_t>(hl.nar_ptr[J]));
+        hl.nar_row.reserve(static_cast<size_t>(rows_total));
+        for (int32_t j = 0; j < J; ++j) {
+            if (!hl.narrow[j]) continue;
+            int64_t q = hl.nar_ptr[j] - 1;
+            int32_t cur = -1;
+            for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) {
+                const int32_t r = crow[e];
+                if (row_pat[r] != cur) {
+                    cur = row_pat[r];
+                    ++q;
+                    hl.nar_seg[q] = make_int4(cur, 0, static_cast<int>(hl.nar_row.size()), 0);
+                }
+                hl.nar_seg[q].y++;
+                hl.nar_row.push_back(r);
+            }
+        }
+    }
+    for (int32_t j = 0; j < J; ++j)
+        if (!hl.narrow[j]) {
+            hl.first_wide = j;
+            break;
+        }
+    {
+        int32_t nxt = hl.first_wide;
+        for (int32_t j = J - 1; j >= 0; --j) {
+            hl.next_wide[j] = nxt;
+            if (!hl.narrow[j]) nxt = j;
+        }
     }
 
     // ---- shards at subject boundaries, balanced by rows
@@ -878,7 +948,8 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
         return fail(SCCS_E_INVAL, "num_shards must be in [1, " + std::to_string(std::min(sms * per_sm, sccs::kMaxShards)) + "]");
 
     HostLayout hl;
-    int rc = build_layout(K, patient_id, y, offset_L, J, col_ptr, row_idx, S, hl);
+    const int32_t narrow_max = o.narrow_max_nnz == 0 ? kNarrowDefault : o.narrow_max_nnz;
+    int rc = build_layout(K, patient_id, y, offset_L, J, col_ptr, row_idx, S, narrow_max, hl);
     if (rc != SCCS_OK) return rc;
 
     sccs_handle *h = new sccs_handle();
@@ -997,6 +1068,27 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
         d.row_ptr = row_ptr;
         d.row_col = row_col;
     }
+    if (hl.narrow_count > 0) {
+        uint8_t *nar;
+        int32_t *nxt, *nrow;
+        int64_t *nptr;
+        int4 *nseg;
+        unsigned long long *nsync;
+        if ((rc = upload(h, &nar, hl.narrow.data(), hl.narrow.size())) ||
+            (rc = upload(h, &nxt, hl.next_wide.data(), hl.next_wide.size())) ||
+            (rc = upload(h, &nptr, hl.nar_ptr.data(), hl.nar_ptr.size())) ||
+            (rc = upload(h, &nseg, hl.nar_seg.data(), hl.nar_seg.size())) ||
+            (rc = upload(h, &nrow, hl.nar_row.data(), hl.nar_row.size())) ||
+            (rc = alloc_zero(h, &nsync, static_cast<size_t>(32))))
+            return bail(rc);
+        d.narrow = nar;
+        d.next_wide = nxt;
+        d.first_wide = hl.first_wide;
+        d.nar_ptr = nptr;
+        d.nar_seg = nseg;
+        d.nar_row = nrow;
+        d.nar_sync = nsync;
+    }
     if ((rc = run_init_state(h, nullptr))) return bail(rc);
     ce = cudaStreamSynchronize(h->stream);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamSynchronize"));
@@ -1014,6 +1106,7 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     info.columns = J;
     info.num_shards = S;
     info.threads_per_block = threads;
+    info.narrow_columns = hl.narrow_count;
     *out = h;
     return SCCS_OK;
 }

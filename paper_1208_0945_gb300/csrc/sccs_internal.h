@@ -51,6 +51,15 @@ struct DevLayout {
     const int32_t *nev;        // N: n_i (or w_i n_i in a weighted fit)
     const double *L;           // K: offsets l_k
     const double *ytx;         // J: Y'X_j (or its weighted form)
+    // narrow columns: whole column on the team's CTA 0 with block-level sums (null: none)
+    const uint8_t *narrow;     // J: 1 for a narrow column
+    const int32_t *next_wide;  // J: the next wide column after j, cyclically
+    int32_t first_wide;        // first wide column (-1: none)
+    int32_t pad_nw;
+    const int64_t *nar_ptr;    // J+1: a narrow column's segments in nar_seg
+    const int4 *nar_seg;       //   {subject, rows, first row in nar_row, 0}, subjects ascending
+    const int32_t *nar_row;    //   rows of each segment, ascending
+    unsigned long long *nar_sync;  // per fit state: [0] CTAs arrived at a narrow run, [16] runs done
     const int64_t *row_ptr;    // K+1: row -> columns index (built on the device at create)
     const int32_t *row_col;    //   the columns of each row, ascending
     const int64_t *ycol_ptr;   // J+1: per column, its (subject, sum of y) pairs with events

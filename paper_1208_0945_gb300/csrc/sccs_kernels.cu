@@ -1047,6 +1047,142 @@ __device__ __forceinline__ void bookkeep(double *beta, double *trust, int j, dou
     if (db != 0.0) ++nonzero;
 }
 
+// ------------------------------------------------------------------ narrow columns
+//
+// A column whose subjects are few is run end to end by the team's CTA 0: gather L x exp(Xb) at
+// its rows, each subject's numerator (rows ascending), W terms, the exact CTA-level sums, the
+// Newton step (Eq. 4 with the prior and the trust region) and the sparse updates of Section 2.3,
+// all with block barriers, no grid-wide all-reduce.  The other CTAs wait for the run of narrow
+// columns to end.  The arithmetic per subject and per row is the wide path's; the sums are
+// the same exact fixed-point sums of per-thread partials.
+
+// Wait (thread 0) until *ctr >= target, acquiring; bounded, honours the abort flag.
+__device__ bool wait_counter(const unsigned long long *ctr, unsigned long long target, const int *abort_flag,
+                             long long timeout_ns) {
+    const long long t0 = now_ns();
+    for (unsigned it = 0;; ++it) {
+        unsigned long long v;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+        if (v >= target) return true;
+        if (*reinterpret_cast<const volatile int *>(abort_flag)) return false;
+        if ((it & 15u) == 15u && now_ns() - t0 > timeout_ns) {
+            atomicExch(const_cast<int *>(abort_flag), 1);
+            return false;
+        }
+    }
+}
+
+// Static data of narrow column j into L1 ahead of use (segments and rows never change, so an
+// early copy cannot go stale).
+__device__ __forceinline__ void prefetch_narrow(const DevLayout &d, int j) {
+    const long long a = d.nar_ptr[j], b = d.nar_ptr[j + 1];
+    const long long nseg = b - a;
+    if (nseg <= 0) return;
+    const char *sp = reinterpret_cast<const char *>(d.nar_seg + a);
+    const long long sbytes = nseg * static_cast<long long>(sizeof(int4));
+    for (long long o = static_cast<long long>(threadIdx.x) * 128; o < sbytes; o += static_cast<long long>(blockDim.x) * 128)
+        prefetch_l1(sp + o);
+    const int4 f = d.nar_seg[a], l = d.nar_seg[b - 1];
+    const char *rp = reinterpret_cast<const char *>(d.nar_row + f.z);
+    const long long rbytes = static_cast<long long>(l.z + l.y - f.z) * 4;
+    for (long long o = static_cast<long long>(threadIdx.x) * 128; o < rbytes; o += static_cast<long long>(blockDim.x) * 128)
+        prefetch_l1(rp + o);
+}
+
+// Narrow columns j0..j1-1 on this CTA (the team's CTA 0).  beta / trust: this CTA's copies;
+// every shard's copy of beta_j is written too.  Thread 0 carries status, warn, nonzero.
+__device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, int j1, SmemLayout &sm,
+                               SharedState &sh, double *beta, double *trust, int &status, int &warn,
+                               long long &nonzero) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    prefetch_narrow(d, j0);
+    for (int j = j0; j < j1; ++j) {
+        // the step's operands early, off the critical path
+        double bj = 0.0, tj = 0.0, yj = 0.0;
+        if (threadIdx.x == 0) {
+            bj = beta[j];
+            tj = trust[j];
+            yj = d.ytx[j];
+        }
+        const long long a = d.nar_ptr[j];
+        const int nseg = static_cast<int>(d.nar_ptr[j + 1] - a);
+        const int row0 = nseg > 0 ? d.nar_seg[a].z : 0;
+        if (j + 1 < j1) prefetch_narrow(d, j + 1);
+        double G = 0.0, H = 0.0;
+        bool bad = false, first = true;
+        for (int q = threadIdx.x; q < nseg; q += blockDim.x) {
+            const int4 sg = d.nar_seg[a + q];
+            double num = 0.0;
+            for (int t = 0; t < sg.y; ++t) {
+                const double e = d.E[d.nar_row[sg.z + t]];
+                sm.est[sg.z - row0 + t] = e;
+                num += e;
+            }
+            const double Dv = d.D[sg.x];
+            double gl = 0.0, hl = 0.0;
+            segment_terms(num, Dv, d.nev[sg.x], gl, hl, bad);
+            sm.seg_stash[q] = make_double2(num, Dv);
+            if (first) {
+                G = gl;
+                H = hl;
+                first = false;
+            } else {
+                G += gl;
+                H += hl;
+            }
+        }
+        const Fx fa = fx_warp_sum(fx_from_double(G, bad));
+        const Fx fb = fx_warp_sum(fx_from_double(H, bad));
+        const int wbad = __any_sync(kFull, bad);
+        if (lane == 0) {
+            sh.wa[warp] = fa;
+            sh.wb[warp] = fb;
+            sh.wbad[warp] = wbad;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            Fx ta = lane < nwarps ? sh.wa[lane] : fx_zero();
+            Fx tbx = lane < nwarps ? sh.wb[lane] : fx_zero();
+            const bool cbad = __any_sync(kFull, lane < nwarps ? sh.wbad[lane] != 0 : false);
+            ta = fx_warp_sum(ta);
+            tbx = fx_warp_sum(tbx);
+            if (lane == 0) {
+                double ca = fx_to_double(ta), cb = fx_to_double(tbx);
+                if (cbad) ca = cb = __longlong_as_double(0x7ff8000000000000ll);
+                const double g = yj - ca, q = cb;
+                double db = newton_step(g, q, bj, p, tj, warn), r = 1.0, em1 = 0.0;
+                if (!(db == db) || isinf(db) || !(g == g) || !(q == q)) {
+                    db = 0.0;
+                    status = kStNumeric;
+                } else if (db != 0.0) {
+                    r = exp(db);
+                    em1 = r - 1.0;
+                    ++nonzero;
+                }
+                beta[j] = bj + db;
+                trust[j] = fmax(2.0 * fabs(db), 0.5 * tj);
+                sh.db = db;
+                sh.r = r;
+                sh.em1 = em1;
+            }
+        }
+        __syncthreads();
+        const double db = sh.db;
+        if (db != 0.0) {
+            const double r = sh.r, em1 = sh.em1;
+            for (int q = threadIdx.x; q < nseg; q += blockDim.x) {
+                const int4 sg = d.nar_seg[a + q];
+                for (int t = 0; t < sg.y; ++t) d.E[d.nar_row[sg.z + t]] = sm.est[sg.z - row0 + t] * r;
+                const double2 st = sm.seg_stash[q];
+                d.D[sg.x] = fma(em1, st.x, st.y);
+            }
+        }
+        const double nbj = beta[j];
+        for (int t = threadIdx.x + 1; t < d.S; t += blockDim.x) d.beta_priv[static_cast<long long>(t) * d.J + j] = nbj;
+        __syncthreads();   // E and D as updated are what the next column reads
+    }
+}
+
 // ------------------------------------------------------------------ kernels
 
 // One fit (Algorithm 1) on the CTA that owns shard `s` of `d` (d.S CTAs take part).  F32
@@ -1068,9 +1204,17 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
     int status = kStNotConverged, warn = 0, cycles = 0;
     long long nonzero = 0;
     double P_prev = 0.0, P = 0.0, conv = 0.0, loglik = 0.0, heldout = __longlong_as_double(0x7ff8000000000000ll);
-    long long col = 0;          // columns processed: stage buffer = col & 1
+    long long col = 0;          // wide columns processed: stage buffer = col & 1
+    const bool use_narrow = !F32 && d.narrow != nullptr;
+    unsigned long long run_id = 0;   // narrow runs in this launch
+    long long nonzero_nar = 0;       // thread 0 of CTA 0: narrow steps with db != 0
 
     if (threadIdx.x == 0) {
+        if (use_narrow && s == 0) {   // reset before this CTA's first all-reduce arrival
+            d.nar_sync[0] = 0ull;
+            d.nar_sync[16] = 0ull;
+            __threadfence();
+        }
         mbar_init(&sh.bar[0], 1);
         mbar_init(&sh.bar[1], 1);
         mbar_init_fence();
@@ -1081,10 +1225,12 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
     }
     __syncthreads();
     // staging (copies, pending set, next bounds) belongs to the last warp's lane 0
-    if (threadIdx.x == static_cast<int>(blockDim.x) - 32 && J > 0 && p.max_cycles > 0) {
-        const SliceBounds b0 = load_bounds(d, s, 0);
+    if (threadIdx.x == static_cast<int>(blockDim.x) - 32 && J > 0 && p.max_cycles > 0 &&
+        (!use_narrow || d.first_wide >= 0)) {
+        const int j0 = use_narrow ? d.first_wide : 0;
+        const SliceBounds b0 = load_bounds(d, s, j0);
         if (issue_stage(d, b0, sm, sh, 0)) pending |= 1u;
-        nb = load_bounds(d, s, J > 1 ? 1 : 0);
+        nb = load_bounds(d, s, use_narrow ? d.next_wide[j0] : (J > 1 ? 1 : 0));
     }
     __syncthreads();
 
@@ -1114,6 +1260,51 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
         for (int c = 1; c <= p.max_cycles && status == kStNotConverged; ++c) {
             lin_c = sq_c = ab_c = 0.0;
             for (int j = 0; j < J; ++j, ++col) {
+                if (use_narrow && d.narrow[j]) {
+                    // a run of narrow columns: CTA 0 runs them, the others wait; then every CTA
+                    // adds the run's columns to its cycle sums, in column order
+                    int j1 = j + 1;
+                    while (j1 < J && d.narrow[j1]) ++j1;
+                    ++run_id;
+                    __threadfence();   // this thread's E and D writes, before the arrival below
+                    __syncthreads();
+                    if (s != 0) {
+                        if (threadIdx.x == 0) {
+                            atomicAdd(&d.nar_sync[0], 1ull);
+                            sh.ok = wait_counter(&d.nar_sync[16], run_id, d.abort_flag, timeout) ? 1 : 0;
+                        }
+                        __syncthreads();
+                    } else {
+                        if (threadIdx.x == 0)
+                            sh.ok = wait_counter(&d.nar_sync[0], run_id * static_cast<unsigned long long>(d.S - 1),
+                                                 d.abort_flag, timeout) ? 1 : 0;
+                        __syncthreads();
+                        if (sh.ok) {
+                            narrow_columns(d, p, j, j1, sm, sh, beta, trust, status, warn, nonzero_nar);
+                            __threadfence();
+                            __syncthreads();
+                            if (threadIdx.x == 0)
+                                asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&d.nar_sync[16]), "l"(run_id)
+                                             : "memory");
+                        }
+                    }
+                    if (!sh.ok) goto aborted;
+                    if (threadIdx.x == tb) {
+                        if (pend_j >= 0) {
+                            bookkeep(beta, trust, pend_j, pend_b, pend_t, pend_y, pend_db, lin_c, sq_c, ab_c, nonzero_tb);
+                            pend_j = -1;
+                        }
+                        for (int jj = j; jj < j1; ++jj) {
+                            const double b = beta[jj];
+                            lin_c = fma(b, d.ytx[jj], lin_c);
+                            sq_c = fma(b, b, sq_c);
+                            ab_c += fabs(b);
+                        }
+                    }
+                    j = j1 - 1;
+                    --col;             // the loop's increments: no wide column was processed
+                    continue;
+                }
                 const int buf = static_cast<int>(col & 1);
                 double bj = 0.0, tj = 0.0, yj = 0.0;
                 if (threadIdx.x == 0 || threadIdx.x == tb) {
@@ -1134,8 +1325,8 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                 if (threadIdx.x == tb) {
                     // stage the next column, then the deferred bookkeeping of the previous one
                     if (issue_stage(d, nb, sm, sh, buf ^ 1)) pending |= 1u << (buf ^ 1);
-                    const int jn = j + 1 < J ? j + 1 : 0;
-                    const int jnn = jn + 1 < J ? jn + 1 : 0;
+                    const int jn = use_narrow ? d.next_wide[j] : (j + 1 < J ? j + 1 : 0);
+                    const int jnn = use_narrow ? d.next_wide[jn] : (jn + 1 < J ? jn + 1 : 0);
                     nb = load_bounds(d, s, jnn);
                     if (pend_j >= 0) {
                         bookkeep(beta, trust, pend_j, pend_b, pend_t, pend_y, pend_db, lin_c, sq_c, ab_c, nonzero_tb);
@@ -1214,7 +1405,9 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     // warps 1..: desc[buf ^ 1] (written by thread tb) is visible after this barrier
                     if (one_warp) named_barrier_all_but_warp0();
                     const ColDesc &nd = sh.desc[buf ^ 1];
-                    if (nd.staged) {
+                    // no early L1 copies of state that a narrow run will change first
+                    const bool gap = use_narrow && d.next_wide[j] != (j + 1 < J ? j + 1 : 0);
+                    if (nd.staged && !gap) {
                         if (F32)
                             prefetch_staged_state32(d, nd, sm.stage[buf ^ 1], &sh.bar[buf ^ 1],
                                                     (phase_bits >> (buf ^ 1)) & 1u);
@@ -1276,6 +1469,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
             status = sh.stop;
         }
         nonzero = sh.nonzero;
+        if (threadIdx.x == 0) nonzero += nonzero_nar;
     }
     if (!F32 && p.ho_nev && (status == kStOk || status == kStNotConverged)) {
         // Section 2.5: the held-out fold's predictive log-likelihood at the final beta, from the

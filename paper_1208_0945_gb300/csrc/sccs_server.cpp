@@ -91,7 +91,7 @@ size_t slot_bytes(const sccs::DevLayout &d, int max_cycles) {
     const size_t N1 = std::max<size_t>(N, 1);
     return al(8 * K) + al(8 * N) + al(4 * K) + al(8 * N) + 2 * al(8 * S * J) +
            al(16 * S * static_cast<size_t>(d.stash_stride)) + al(32 * S) + 2 * al(sizeof(sccs::FitOut)) +
-           al(8 * J) + al(8 * static_cast<size_t>(max_cycles + 1)) + 3 * al(4 * N1) + 2 * al(8 * J);
+           al(8 * J) + al(8 * static_cast<size_t>(max_cycles + 1)) + 3 * al(4 * N1) + 2 * al(8 * J) + al(256);
 }
 
 }  // namespace
@@ -184,6 +184,8 @@ FitSlot *make_slot(const sccs_handle *dataset, int max_cycles) {
     s->nev_w = reinterpret_cast<int32_t *>(take(4 * N1));
     s->ytx_w = reinterpret_cast<double *>(take(8 * J));
     s->nev_ho = reinterpret_cast<int32_t *>(take(4 * N1));
+    auto *nsync = reinterpret_cast<unsigned long long *>(take(256));
+    if (d.narrow) d.nar_sync = nsync;   // the slot's own narrow-run counters
     s->ytx_ho = reinterpret_cast<double *>(take(8 * J));
     d.abort_flag = &s->out_dev->abort_flag;
     if (cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess ||

@@ -364,3 +364,37 @@ def test_fp32_grad_path_and_tiny_config(P):
         r32 = m.fit(precision="fp32", tol_mode="rel_logpost", tol=1e-7, max_cycles=200)
     assert float(np.abs(r2["beta"] - ref2["beta"]).max()) <= 1e-8
     assert float(np.abs(r32["beta"] - ref2["beta"]).max()) <= 2e-4
+
+
+@pytest.mark.parametrize("prior,var", [("normal", 0.3), ("laplace", 0.1)])
+def test_narrow_columns_match_wide_path_and_oracle(P, prior, var):
+    """Columns run whole on one CTA (block-level sums) against the same fit with every column
+    on all CTAs, and against the oracle: a mix of narrow and wide columns, narrow runs at the
+    start and end of the cycle."""
+    sizes = np.array([5, 3000, 40, 7, 12000, 900, 2, 60, 25000, 15, 300, 8, 1])
+    d = make_dataset(n_patients=30000, eras=("geometric", 8), J=sizes.size, columns=("sizes", sizes),
+                     n_true=4, beta_sd=0.5, seed=21)
+    orc = oracle.Problem.from_data(d)
+    ref = orc.fit(prior=prior, variance=var, fixed_cycles=4)
+    out = {}
+    for thr in (-1, 1000, 0):
+        with gpu_model(P, d, num_shards=16, narrow_max_nnz=thr) as m:
+            info = m.info
+            m.set_prior(prior, var)
+            out[thr] = (m.fit(tol=-1.0, max_cycles=4, history=True), info["narrow_columns"])
+    assert out[-1][1] == 0 and 0 < out[1000][1] <= out[0][1] <= sizes.size
+    for thr in (-1, 1000, 0):
+        r = out[thr][0]
+        np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11, rtol=0)
+        np.testing.assert_allclose(r["history"], ref["history"], rtol=1e-12)
+        assert r["nonzero_steps"] == out[-1][0]["nonzero_steps"]
+
+
+def test_all_columns_narrow_and_converged(P):
+    d, fit = tiny_fit_config()
+    orc = oracle.Problem.from_data(d)
+    with gpu_model(P, d, num_shards=8, narrow_max_nnz=100000) as m:
+        assert m.info["narrow_columns"] == d.J
+        m.set_prior(fit["prior"], fit["variance"])
+        r = m.fit(tol_mode="rel_logpost", tol=1e-15, max_cycles=200)
+    compare_converged(r, orc, fit["prior"], fit["variance"], "rel_logpost", 1e-15)
