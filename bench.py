@@ -506,7 +506,8 @@ def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, 
     nf = 0 if folds_of is None else int(max(f.max() for f in folds_of)) + 1
     rows = []
     for ri, rate in enumerate(rates):
-        reqs = serving_requests(n_per_rate, rate, len(Js), seed=seed0 + ri, folds=nf)
+        n_req = n_per_rate if n_per_rate > 0 else int(min(192, max(32, 3.0 * rate)))
+        reqs = serving_requests(n_req, rate, len(Js), seed=seed0 + ri, folds=nf)
         masks = [fold_weights(folds_of[o], k - 1) if k > 0 else (None, None) for (_t, o, _p, _v, k) in reqs]
         with sccs.FitServer(device=device, max_inflight=max_inflight, hbm_budget_bytes=budget) as srv:
             tickets = []
@@ -529,8 +530,8 @@ def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, 
             t_end = time.perf_counter()
         lat = np.array([r["latency_ms"] for r in out])
         done_span = (t_end - t0)
-        rows.append({"rate_per_s": rate, "requests": n_per_rate,
-                     "fits_per_s": n_per_rate / done_span,
+        rows.append({"rate_per_s": rate, "requests": n_req,
+                     "fits_per_s": n_req / done_span,
                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                      "mean_queue_ms": float(np.mean([r["queue_ms"] for r in out])),
                      "failed": int(sum(1 for r in out if r["status"] < 0)),
@@ -596,7 +597,8 @@ def run_serving(args, rank, world, local):
                                    "requests = outcome x Normal/Laplace x variance grid "
                                    "{0.01..1} x fold 1..10 (fit on 9 folds, held-out predictive log-likelihood "
                                    "of the 10th returned), FP64 to rel |dP| < 1e-12; "
-                                   f"{args.requests} Poisson arrivals per rate",
+                                   + (f"{args.requests} Poisson arrivals per rate" if args.requests > 0 else
+                                      "3 s of Poisson arrivals per rate (32 to 192 requests)"),
                        "outcomes": args.outcomes, "eras": int(sum(i["rows_kept"] for i in infos)),
                        "nnz": int(sum(i["nnz_kept"] for i in infos)), "rates_per_s": rates,
                        "teams": {"min": int(min(teams)), "max": int(max(teams))},
@@ -635,7 +637,8 @@ def main():
     ap.add_argument("--outcomes", type=int, default=32, help="serving: resident outcomes")
     ap.add_argument("--max-eras", type=float, default=20e6, help="serving: largest outcome's eras")
     ap.add_argument("--rates", default="1,2,5,10,20,50,100,200", help="serving: arrival rates per second")
-    ap.add_argument("--requests", type=int, default=32, help="serving: requests per rate")
+    ap.add_argument("--requests", type=int, default=0,
+                    help="serving: requests per rate (0: 3 s of arrivals, at least 32 and at most 192)")
     ap.add_argument("--hbm-budget-gb", type=float, default=48.0, help="serving: fit-slot memory budget")
     args = ap.parse_args()
     rank, world, local = dist_env()
