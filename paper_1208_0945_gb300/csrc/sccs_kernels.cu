@@ -87,6 +87,11 @@ __device__ __forceinline__ void prefetch_l1(const void *p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// Into L2 only: L2 is where all SMs' writes meet, so an early copy there cannot go stale.
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // ------------------------------------------------------------------ bulk copies, mbarriers
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -1073,20 +1078,40 @@ __device__ bool wait_counter(const unsigned long long *ctr, unsigned long long t
 }
 
 // Static data of narrow column j into L1 ahead of use (segments and rows never change, so an
-// early copy cannot go stale).
-__device__ __forceinline__ void prefetch_narrow(const DevLayout &d, int j) {
+// early copy cannot go stale), spread over the `nthr` threads t0, t0 + 1, ... that call it.
+__device__ __forceinline__ void prefetch_narrow(const DevLayout &d, int j, int t, int nthr) {
     const long long a = d.nar_ptr[j], b = d.nar_ptr[j + 1];
     const long long nseg = b - a;
     if (nseg <= 0) return;
     const char *sp = reinterpret_cast<const char *>(d.nar_seg + a);
     const long long sbytes = nseg * static_cast<long long>(sizeof(int4));
-    for (long long o = static_cast<long long>(threadIdx.x) * 128; o < sbytes; o += static_cast<long long>(blockDim.x) * 128)
+    for (long long o = static_cast<long long>(t) * 128; o < sbytes; o += static_cast<long long>(nthr) * 128)
         prefetch_l1(sp + o);
     const int4 f = d.nar_seg[a], l = d.nar_seg[b - 1];
     const char *rp = reinterpret_cast<const char *>(d.nar_row + f.z);
     const long long rbytes = static_cast<long long>(l.z + l.y - f.z) * 4;
-    for (long long o = static_cast<long long>(threadIdx.x) * 128; o < rbytes; o += static_cast<long long>(blockDim.x) * 128)
+    for (long long o = static_cast<long long>(t) * 128; o < rbytes; o += static_cast<long long>(nthr) * 128)
         prefetch_l1(rp + o);
+}
+
+// The state narrow column j will read (E at its rows, D at its subjects) into L2, spread over
+// nthr threads.
+__device__ __forceinline__ void prefetch_narrow_state_l2(const DevLayout &d, int j, int t, int nthr) {
+    const long long a = d.nar_ptr[j];
+    const int nseg = static_cast<int>(d.nar_ptr[j + 1] - a);
+    for (int q = t; q < nseg; q += nthr) {
+        const int4 sg = d.nar_seg[a + q];
+        prefetch_l2(d.D + sg.x);
+        for (int u = 0; u < sg.y; ++u) prefetch_l2(d.E + d.nar_row[sg.z + u]);
+    }
+}
+
+// The state wide column j will read on shard s (E at the slice's rows, D at its subjects) into
+// L2, spread over nthr threads.
+__device__ __forceinline__ void prefetch_slice_state_l2(const DevLayout &d, int s, int j, int t, int nthr) {
+    const long long so = static_cast<long long>(s) * (d.J + 1) + j;
+    for (long long q = d.slice_row[so] + t; q < d.slice_row[so + 1]; q += nthr) prefetch_l2(d.E + d.rows[q]);
+    for (long long si = d.slice_seg[so] + t; si < d.slice_seg[so + 1]; si += nthr) prefetch_l2(d.D + d.segs[si].x);
 }
 
 // Narrow columns j0..j1-1 on this CTA (the team's CTA 0).  beta / trust: this CTA's copies;
@@ -1095,7 +1120,7 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
                                SharedState &sh, double *beta, double *trust, int &status, int &warn,
                                long long &nonzero) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    prefetch_narrow(d, j0);
+    prefetch_narrow(d, j0, threadIdx.x, blockDim.x);
     for (int j = j0; j < j1; ++j) {
         // the step's operands early, off the critical path
         double bj = 0.0, tj = 0.0, yj = 0.0;
@@ -1107,20 +1132,28 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
         const long long a = d.nar_ptr[j];
         const int nseg = static_cast<int>(d.nar_ptr[j + 1] - a);
         const int row0 = nseg > 0 ? d.nar_seg[a].z : 0;
-        if (j + 1 < j1) prefetch_narrow(d, j + 1);
+        // threads without a segment of this column fetch the next column's static data
+        if (j + 1 < j1) {
+            const int busy = nseg < static_cast<int>(blockDim.x) ? (nseg + 31) & ~31 : static_cast<int>(blockDim.x);
+            if (busy < static_cast<int>(blockDim.x) && threadIdx.x >= busy)
+                prefetch_narrow(d, j + 1, threadIdx.x - busy, blockDim.x - busy);
+            else if (busy == static_cast<int>(blockDim.x) && threadIdx.x == 0)
+                prefetch_narrow(d, j + 1, 0, 1);
+        }
         double G = 0.0, H = 0.0;
         bool bad = false, first = true;
         for (int q = threadIdx.x; q < nseg; q += blockDim.x) {
             const int4 sg = d.nar_seg[a + q];
+            const double Dv = d.D[sg.x];      // issued ahead of the row gathers
+            const int nv = d.nev[sg.x];
             double num = 0.0;
             for (int t = 0; t < sg.y; ++t) {
                 const double e = d.E[d.nar_row[sg.z + t]];
                 sm.est[sg.z - row0 + t] = e;
                 num += e;
             }
-            const double Dv = d.D[sg.x];
             double gl = 0.0, hl = 0.0;
-            segment_terms(num, Dv, d.nev[sg.x], gl, hl, bad);
+            segment_terms(num, Dv, nv, gl, hl, bad);
             sm.seg_stash[q] = make_double2(num, Dv);
             if (first) {
                 G = gl;
@@ -1165,6 +1198,9 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
                 sh.r = r;
                 sh.em1 = em1;
             }
+        } else if (j + 1 < j1) {
+            // while warp 0 takes the step: the next column's state into L2
+            prefetch_narrow_state_l2(d, j + 1, threadIdx.x - 32, blockDim.x - 32);
         }
         __syncthreads();
         const double db = sh.db;
@@ -1272,6 +1308,11 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                         if (threadIdx.x == 0) {
                             atomicAdd(&d.nar_sync[0], 1ull);
                             sh.ok = wait_counter(&d.nar_sync[16], run_id, d.abort_flag, timeout) ? 1 : 0;
+                        } else if (d.first_wide >= 0) {
+                            // while CTA 0 runs the narrow columns: the next wide column's state
+                            // on this shard into L2
+                            const int jw = d.next_wide[j1 - 1];
+                            prefetch_slice_state_l2(d, s, jw, threadIdx.x - 1, blockDim.x - 1);
                         }
                         __syncthreads();
                     } else {
