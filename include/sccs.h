@@ -311,6 +311,14 @@ int sccs_server_get_stats(sccs_server *srv, sccs_server_stats *stats);
 int sccs_server_destroy(sccs_server *srv);
 
 /*
+ * sccs_selftest_exp -- diagnostic for tests: the library's e^x, used for e^{Delta beta} in every
+ * coordinate step (Section 2.3's update of L x exp(X beta)), and CUDA's exp on the same n host
+ * values (x, ours, ref: host arrays of n doubles; the library copies them).  Errors:
+ * SCCS_E_INVAL (n < 0 or null arrays with n > 0), SCCS_E_NOMEM, SCCS_E_CUDA.
+ */
+int sccs_selftest_exp(int32_t device, const double *x, int64_t n, double *ours, double *ref);
+
+/*
  * sccs_check_wait_timeout -- self-test of the bounded device-side waits (failure detection).
  * Launches the gradient kernel on one CTA fewer than the all-reduce counts, so the last
  * partial is never written and every launched CTA's wait must run out after timeout_ms

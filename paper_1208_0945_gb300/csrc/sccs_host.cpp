@@ -386,7 +386,8 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
         int64_t rows_total = 0;
         for (int32_t j = 0; j < J; ++j) {
             const int64_t n = cptr[j + 1] - cptr[j];
-            const bool fits = n <= narrow_max && n <= sccs::kRowCap && nseg[j] <= sccs::kSegCap &&
+            // half the shared buffers each: the next column is gathered while this one steps
+            const bool fits = n <= narrow_max && n <= sccs::kRowCap / 2 && nseg[j] <= sccs::kSegCap / 2 &&
                               rows_total + n < (int64_t(1) << 31);
             hl.narrow[j] = fits ? 1 : 0;
             hl.nar_ptr[j + 1] = hl.nar_ptr[j] + (fits ? nseg[j] : 0);
@@ -1471,6 +1472,27 @@ int sccs_heldout_loglik(sccs_handle *h, const double *beta, const int32_t *weigh
     }
     h->seq = r.seq_end;
     *loglik = r.loglik;
+    return SCCS_OK;
+}
+
+int sccs_selftest_exp(int32_t device, const double *x, int64_t n, double *ours, double *ref) {
+    if (n < 0 || (n > 0 && (!x || !ours || !ref))) return fail(SCCS_E_INVAL, "bad arguments");
+    if (n == 0) return SCCS_OK;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    double *buf = nullptr;
+    const size_t b = sizeof(double) * static_cast<size_t>(n);
+    if (cudaMalloc(&buf, 3 * b) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(SCCS_E_NOMEM, "device buffers");
+    }
+    e = cudaMemcpy(buf, x, b, cudaMemcpyHostToDevice);
+    int le = e == cudaSuccess ? sccs::launch_exp_selftest(buf, n, buf + n, buf + 2 * n, nullptr) : static_cast<int>(e);
+    if (le == 0) e = cudaMemcpy(ours, buf + n, b, cudaMemcpyDeviceToHost);
+    if (le == 0 && e == cudaSuccess) e = cudaMemcpy(ref, buf + 2 * n, b, cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "exp self-test");
+    if (e != cudaSuccess) return cuda_fail(e, "exp self-test copies");
     return SCCS_OK;
 }
 

@@ -144,6 +144,8 @@ int launch_e_to_f32(const DevLayout &d, int threads, void *stream);
 int launch_build_row_index(const DevLayout &d, int64_t *row_ptr, int32_t *row_col, int32_t *cnt, int64_t *cursor,
                            int64_t *block_sums, void *stream);
 size_t row_index_scan_blocks(int64_t K);
+// Diagnostic: the coordinate step's e^x and CUDA's exp on n device values.
+int launch_exp_selftest(const double *x, long long n, double *ours, double *ref, void *stream);
 // Weighted counts of a fit with subject weights w_kept (device [N]): nev_w[i] = w_i n_i and
 // ytx_w[j] = sum over X_j's (subject, y) pairs of w_i y, both exact (integer sums).
 int launch_weighted_counts(const DevLayout &d, const int32_t *w_kept, int32_t *nev_w, double *ytx_w, void *stream);

@@ -277,6 +277,7 @@ struct SharedState {
     Fx wb[kMaxWarps];
     int wbad[kMaxWarps];
     double db, r, em1;
+    double nbj;             // a narrow column's new beta_j
     double G, H;
     double lin, sq, ab;     // cycle sums of b_j Y'X_j, b_j^2, |b_j| (from the bookkeeping thread)
     long long nonzero;
@@ -462,6 +463,48 @@ __device__ double newton_step(double g, double q, double b, const FitParams &p, 
         }
     }
     return fmin(fmax(dv, -trust), trust);
+}
+
+// ---- e^x for the coordinate step (on every coordinate's critical path, where FP64 issues at
+// 1/64 of the FP32 rate): Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989).
+// x = (32 m + j) ln2/32 + r with |r| <= ln2/64, e^x = 2^m 2^(j/32) e^r, e^r - 1 from its Taylor
+// series to r^6 (the next term is below 2^-60 relative).  Table: 2^(j/32) rounded to the nearest
+// double (from the exponential series at 60 digits); ln2/32 split so that n ln2/32 is exact in
+// two parts for |n| < 2^15.  |x| >= 700 (and NaN) go to exp().
+__constant__ double c_exp2_j32[32] = {
+    0x1.0000000000000p+0, 0x1.059b0d3158574p+0, 0x1.0b5586cf9890fp+0, 0x1.11301d0125b51p+0,
+    0x1.172b83c7d517bp+0, 0x1.1d4873168b9aap+0, 0x1.2387a6e756238p+0, 0x1.29e9df51fdee1p+0,
+    0x1.306fe0a31b715p+0, 0x1.371a7373aa9cbp+0, 0x1.3dea64c123422p+0, 0x1.44e086061892dp+0,
+    0x1.4bfdad5362a27p+0, 0x1.5342b569d4f82p+0, 0x1.5ab07dd485429p+0, 0x1.6247eb03a5585p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.71f75e8ec5f74p+0, 0x1.7a11473eb0187p+0, 0x1.82589994cce13p+0,
+    0x1.8ace5422aa0dbp+0, 0x1.93737b0cdc5e5p+0, 0x1.9c49182a3f090p+0, 0x1.a5503b23e255dp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b7f76f2fb5e47p+0, 0x1.c199bdd85529cp+0, 0x1.cb720dcef9069p+0,
+    0x1.d5818dcfba487p+0, 0x1.dfc97337b9b5fp+0, 0x1.ea4afa2a490dap+0, 0x1.f50765b6e4540p+0};
+
+__device__ __forceinline__ double exp_step(double x) {
+    if (!(fabs(x) < 700.0)) return exp(x);
+    constexpr double kInvL = 0x1.71547652b82fep+5;   // 32 / ln 2
+    constexpr double kL1 = 0x1.62e42fefa0000p-6;     // ln2/32, high 38 bits
+    constexpr double kL2 = 0x1.cf79abc9e3b3ap-45;    // ln2/32 - kL1
+    const double n = rint(x * kInvL);
+    const double r = fma(-n, kL2, fma(-n, kL1, x));
+    const int ni = static_cast<int>(n);
+    const int jj = ni & 31, m = (ni - jj) / 32;
+    double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+    q = fma(r, q, 1.0 / 24.0);
+    q = fma(r, q, 1.0 / 6.0);
+    q = fma(r, q, 0.5);
+    const double em1r = fma(r * r, q, r);            // e^r - 1
+    const double t = c_exp2_j32[jj];
+    return fma(t, em1r, t) * __longlong_as_double(static_cast<long long>(m + 1023) << 52);
+}
+
+// Classifications by bit pattern (integer ops; an FP64 compare costs as much as an FP64 add).
+__device__ __forceinline__ bool nan_bits(double v) {
+    return (static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool nonfinite_bits(double v) {
+    return (static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
 }
 
 // W_i from one segment, with the partials of Eqs. 7 and 9.  W_i is a share of D_i; rounding
@@ -1094,18 +1137,6 @@ __device__ __forceinline__ void prefetch_narrow(const DevLayout &d, int j, int t
         prefetch_l1(rp + o);
 }
 
-// The state narrow column j will read (E at its rows, D at its subjects) into L2, spread over
-// nthr threads.
-__device__ __forceinline__ void prefetch_narrow_state_l2(const DevLayout &d, int j, int t, int nthr) {
-    const long long a = d.nar_ptr[j];
-    const int nseg = static_cast<int>(d.nar_ptr[j + 1] - a);
-    for (int q = t; q < nseg; q += nthr) {
-        const int4 sg = d.nar_seg[a + q];
-        prefetch_l2(d.D + sg.x);
-        for (int u = 0; u < sg.y; ++u) prefetch_l2(d.E + d.nar_row[sg.z + u]);
-    }
-}
-
 // The state wide column j will read on shard s (E at the slice's rows, D at its subjects) into
 // L2, spread over nthr threads.
 __device__ __forceinline__ void prefetch_slice_state_l2(const DevLayout &d, int s, int j, int t, int nthr) {
@@ -1116,12 +1147,41 @@ __device__ __forceinline__ void prefetch_slice_state_l2(const DevLayout &d, int 
 
 // Narrow columns j0..j1-1 on this CTA (the team's CTA 0).  beta / trust: this CTA's copies;
 // every shard's copy of beta_j is written too.  Thread 0 carries status, warn, nonzero.
+//
+// Pipelined: while warp 0 takes column j's step, warps 1.. gather column j+1 (numerators, D,
+// the E values of its rows) into the other half of the shared buffers.  After column j's
+// updates each of column j+1's subjects re-reads D_i: a subject whose rows column j changed has
+// a changed D_i, and is gathered again; the W terms are then formed from data as current as a
+// gather made at that point.
+__device__ void narrow_gather(const DevLayout &d, int j, int t, int nthr, double *est, double2 *stash) {
+    const long long a = d.nar_ptr[j];
+    const int nseg = static_cast<int>(d.nar_ptr[j + 1] - a);
+    const int row0 = nseg > 0 ? d.nar_seg[a].z : 0;
+    for (int q = t; q < nseg; q += nthr) {
+        const int4 sg = d.nar_seg[a + q];
+        const double Dv = d.D[sg.x];
+        prefetch_l1(d.nev + sg.x);          // static: read after the step, when the terms are formed
+        double num = 0.0;
+        for (int u = 0; u < sg.y; ++u) {
+            const double e = d.E[d.nar_row[sg.z + u]];
+            est[sg.z - row0 + u] = e;
+            num += e;
+        }
+        stash[q] = make_double2(num, Dv);
+    }
+}
+
 __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, int j1, SmemLayout &sm,
                                SharedState &sh, double *beta, double *trust, int &status, int &warn,
                                long long &nonzero) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     prefetch_narrow(d, j0, threadIdx.x, blockDim.x);
+    bool gathered = false;     // column j's data was gathered during the previous step
+    double db_prev = 0.0;
     for (int j = j0; j < j1; ++j) {
+        const int half = (j - j0) & 1;
+        double *est = sm.est + half * (kRowCap / 2);
+        double2 *stash = sm.seg_stash + half * (kSegCap / 2);
         // the step's operands early, off the critical path
         double bj = 0.0, tj = 0.0, yj = 0.0;
         if (threadIdx.x == 0) {
@@ -1146,15 +1206,21 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
             const int4 sg = d.nar_seg[a + q];
             const double Dv = d.D[sg.x];      // issued ahead of the row gathers
             const int nv = d.nev[sg.x];
-            double num = 0.0;
-            for (int t = 0; t < sg.y; ++t) {
-                const double e = d.E[d.nar_row[sg.z + t]];
-                sm.est[sg.z - row0 + t] = e;
-                num += e;
+            double num;
+            const double2 st = gathered ? stash[q] : make_double2(0.0, 0.0);
+            if (gathered && (db_prev == 0.0 || __double_as_longlong(Dv) == __double_as_longlong(st.y))) {
+                num = st.x;                   // the subject's state is as gathered
+            } else {
+                num = 0.0;
+                for (int t = 0; t < sg.y; ++t) {
+                    const double e = d.E[d.nar_row[sg.z + t]];
+                    est[sg.z - row0 + t] = e;
+                    num += e;
+                }
             }
             double gl = 0.0, hl = 0.0;
             segment_terms(num, Dv, nv, gl, hl, bad);
-            sm.seg_stash[q] = make_double2(num, Dv);
+            stash[q] = make_double2(num, Dv);
             if (first) {
                 G = gl;
                 H = hl;
@@ -1184,37 +1250,44 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
                 if (cbad) ca = cb = __longlong_as_double(0x7ff8000000000000ll);
                 const double g = yj - ca, q = cb;
                 double db = newton_step(g, q, bj, p, tj, warn), r = 1.0, em1 = 0.0;
-                if (!(db == db) || isinf(db) || !(g == g) || !(q == q)) {
+                if (nonfinite_bits(db) || nan_bits(g) || nan_bits(q)) {
                     db = 0.0;
                     status = kStNumeric;
                 } else if (db != 0.0) {
-                    r = exp(db);
+                    r = exp_step(db);
                     em1 = r - 1.0;
                     ++nonzero;
                 }
-                beta[j] = bj + db;
-                trust[j] = fmax(2.0 * fabs(db), 0.5 * tj);
                 sh.db = db;
                 sh.r = r;
                 sh.em1 = em1;
+                sh.nbj = bj + db;
             }
         } else if (j + 1 < j1) {
-            // while warp 0 takes the step: the next column's state into L2
-            prefetch_narrow_state_l2(d, j + 1, threadIdx.x - 32, blockDim.x - 32);
+            // while warp 0 takes the step: gather the next column into the other half
+            const int nh = half ^ 1;
+            narrow_gather(d, j + 1, threadIdx.x - 32, blockDim.x - 32, sm.est + nh * (kRowCap / 2),
+                          sm.seg_stash + nh * (kSegCap / 2));
         }
         __syncthreads();
         const double db = sh.db;
+        if (threadIdx.x == 0) {      // bookkeeping, off the critical path
+            beta[j] = sh.nbj;
+            trust[j] = fmax(2.0 * fabs(db), 0.5 * tj);
+        }
         if (db != 0.0) {
             const double r = sh.r, em1 = sh.em1;
             for (int q = threadIdx.x; q < nseg; q += blockDim.x) {
                 const int4 sg = d.nar_seg[a + q];
-                for (int t = 0; t < sg.y; ++t) d.E[d.nar_row[sg.z + t]] = sm.est[sg.z - row0 + t] * r;
-                const double2 st = sm.seg_stash[q];
+                for (int t = 0; t < sg.y; ++t) d.E[d.nar_row[sg.z + t]] = est[sg.z - row0 + t] * r;
+                const double2 st = stash[q];
                 d.D[sg.x] = fma(em1, st.x, st.y);
             }
         }
-        const double nbj = beta[j];
+        const double nbj = sh.nbj;
         for (int t = threadIdx.x + 1; t < d.S; t += blockDim.x) d.beta_priv[static_cast<long long>(t) * d.J + j] = nbj;
+        gathered = true;
+        db_prev = db;
         __syncthreads();   // E and D as updated are what the next column reads
     }
 }
@@ -1428,12 +1501,12 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                         if (ok) {
                             const double g = yj - At, q = Bt;
                             db = newton_step(g, q, bj, p, tj, warn);
-                            if (!(db == db) || isinf(db) || !(g == g) || !(q == q)) {
+                            if (nonfinite_bits(db) || nan_bits(g) || nan_bits(q)) {
                                 db = 0.0;
                                 status = kStNumeric;
                             } else if (db != 0.0) {
                                 // e^db - 1 only scales the D update, whose rounding dominates
-                                r = exp(db);
+                                r = exp_step(db);
                                 em1 = r - 1.0;
                             }
                         }
@@ -1899,6 +1972,15 @@ __global__ void __launch_bounds__(256) row_sort_kernel(const int64_t *row_ptr, i
     }
 }
 
+// Diagnostic: the step's e^x against CUDA's exp, element by element.
+__global__ void exp_selftest_kernel(const double *x, long long n, double *ours, double *ref) {
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        ours[i] = exp_step(x[i]);
+        ref[i] = exp(x[i]);
+    }
+}
+
 int ensure_smem_attr() {
     const int bytes = static_cast<int>(sizeof(SmemLayout));
     cudaError_t e = cudaFuncSetAttribute(fit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1923,6 +2005,12 @@ int launch_init_state(const DevLayout &d, const double *beta0_dev, int threads, 
 
 int launch_e_to_f32(const DevLayout &d, int threads, void *stream) {
     e_to_f32_kernel<<<d.S, threads, 0, static_cast<cudaStream_t>(stream)>>>(d);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_exp_selftest(const double *x, long long n, double *ours, double *ref, void *stream) {
+    const int blocks = static_cast<int>(std::min<long long>(std::max<long long>((n + 255) / 256, 1), 1024));
+    exp_selftest_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, ours, ref);
     return static_cast<int>(cudaGetLastError());
 }
 

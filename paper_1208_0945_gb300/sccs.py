@@ -102,6 +102,7 @@ _SIGS = {
     "sccs_logpost": (ctypes.c_int, [_P, _dp, _dp, _dp]),
     "sccs_get_beta": (ctypes.c_int, [_P, _dp]),
     "sccs_heldout_loglik": (ctypes.c_int, [_P, _dp, _P, _dp]),
+    "sccs_selftest_exp": (ctypes.c_int, [ctypes.c_int32, _dp, ctypes.c_int64, _dp, _dp]),
     "sccs_check_wait_timeout": (ctypes.c_int, [_P, ctypes.c_double]),
     "sccs_grad_hess_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int64, _P, _P]),
     "sccs_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(sccs_server_opts)]),
@@ -258,6 +259,14 @@ def sccs_heldout_loglik(handle, weights=None, beta=None) -> float:
     _check(_lib.sccs_heldout_loglik(handle, _dptr(b), None if w is None else ctypes.c_void_p(w.ctypes.data),
                                     ctypes.byref(ll)), "sccs_heldout_loglik")
     return ll.value
+
+
+def sccs_selftest_exp(x, device=0):
+    """(the library's e^x used in the coordinate step, CUDA's exp) on the values x."""
+    xx = np.ascontiguousarray(x, np.float64)
+    ours, ref = np.empty_like(xx), np.empty_like(xx)
+    _check(_lib.sccs_selftest_exp(int(device), _dptr(xx), xx.size, _dptr(ours), _dptr(ref)), "sccs_selftest_exp")
+    return ours, ref
 
 
 def sccs_get_beta(handle, J: int) -> np.ndarray:

@@ -398,3 +398,24 @@ def test_all_columns_narrow_and_converged(P):
         m.set_prior(fit["prior"], fit["variance"])
         r = m.fit(tol_mode="rel_logpost", tol=1e-15, max_cycles=200)
     compare_converged(r, orc, fit["prior"], fit["variance"], "rel_logpost", 1e-15)
+
+
+def test_step_exponential_against_cuda_exp(P):
+    """The table-driven e^x of the coordinate step against CUDA's exp and the host's: within an
+    ulp of the host's everywhere (steps are small; the tails past |x| = 700 go to exp itself)."""
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.normal(0, 0.05, 200000), rng.uniform(-30, 30, 200000), rng.uniform(-699, 699, 50000),
+                        np.array([0.0, -0.0, 1e-300, -1e-300, 5e-17, -5e-17, 1.0, -1.0, 0.5 * np.log(2),
+                                  np.log(2) / 64, -np.log(2) / 64, 699.9, -699.9, 700.0, -700.0, 709.0,
+                                  -745.0, np.inf, -np.inf, np.nan])])
+    ours, ref = P.sccs.sccs_selftest_exp(x)
+    fin = np.isfinite(ref) & (ref > 0)
+    ulp = np.abs(ours[fin] - ref[fin]) / np.spacing(ref[fin])
+    with np.errstate(over="ignore"):
+        host = np.exp(x[fin])
+    ulp_host = np.abs(ours[fin] - host) / np.spacing(host)
+    assert ulp.max() <= 2.0, ulp.max()          # two approximations within 1 ulp each
+    assert ulp_host.max() <= 1.0, ulp_host.max()
+    assert np.mean(ulp == 0) > 0.5
+    assert ours[x == 0.0].tolist() == [1.0, 1.0]
+    assert np.isnan(ours[-1]) and ours[-2] == 0.0 and np.isinf(ours[-3])
