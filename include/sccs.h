@@ -53,7 +53,8 @@ extern "C" {
 /* ---- convergence tests, evaluated once per full cycle (Section 2.2) ------------------- */
 #define SCCS_TOL_ABS_LOGPOST 0   /* |P_t - P_{t-1}| < tol */
 #define SCCS_TOL_REL_LOGPOST 1   /* |P_t - P_{t-1}| / max(1, |P_t|) < tol */
-#define SCCS_TOL_GENKIN_XBETA 2  /* sum|Xb_t - Xb_{t-1}| / (1 + sum|Xb_t|) < tol (not on GPU yet) */
+#define SCCS_TOL_GENKIN_XBETA 2  /* sum|Xb_t - Xb_{t-1}| / (1 + sum|Xb_t|) < tol (Xb_k = log(E_k/l_k); FP64
+                                     state: SCCS_PREC_FP64, or the polish of SCCS_PREC_FP32_POLISH) */
 
 /* ---- arithmetic ----------------------------------------------------------------------- */
 #define SCCS_PREC_FP64 0         /* every step in FP64 */

@@ -582,6 +582,15 @@ int set_state(sccs_handle *h, const double *beta) {
     return run_init_state(h, h->beta_dev);
 }
 
+// E at the start of a cycle, for Genkin's X-beta convergence test (made on first use).
+int ensure_e_prev(sccs_handle *h) {
+    if (h->d.E_prev) return SCCS_OK;
+    auto *p = static_cast<double *>(h->arena.get(sizeof(double) * static_cast<size_t>(std::max<int64_t>(h->d.K, 1))));
+    if (!p) return fail(SCCS_E_NOMEM, "device memory for the X-beta test");
+    h->d.E_prev = p;
+    return SCCS_OK;
+}
+
 // ---- subject weights (Section 2.5)
 
 int ensure_weight_scratch(sccs_handle *h) {
@@ -1150,14 +1159,16 @@ int sccs_fit(sccs_handle *h, const sccs_fit_opts *opts, double *beta_out, sccs_f
         o = *opts;
     }
     if (o.max_cycles < 0) return fail(SCCS_E_INVAL, "max_cycles must be >= 0");
-    if (o.tol_mode == SCCS_TOL_GENKIN_XBETA)
-        return fail(SCCS_E_UNSUPPORTED, "the Genkin X-beta convergence test is not in this build");
-    if (o.tol_mode != SCCS_TOL_ABS_LOGPOST && o.tol_mode != SCCS_TOL_REL_LOGPOST)
+    if (o.tol_mode != SCCS_TOL_ABS_LOGPOST && o.tol_mode != SCCS_TOL_REL_LOGPOST &&
+        o.tol_mode != SCCS_TOL_GENKIN_XBETA)
         return fail(SCCS_E_INVAL, "unknown tol_mode");
     if (o.precision != SCCS_PREC_FP64 && o.precision != SCCS_PREC_FP32_POLISH && o.precision != SCCS_PREC_FP32)
         return fail(SCCS_E_INVAL, "unknown precision");
+    if (o.tol_mode == SCCS_TOL_GENKIN_XBETA && o.precision == SCCS_PREC_FP32)
+        return fail(SCCS_E_UNSUPPORTED, "the Genkin X-beta test needs the FP64 state (use FP64 or FP32 + polish)");
     int rc = set_device(h);
     if (rc) return rc;
+    if (o.tol_mode == SCCS_TOL_GENKIN_XBETA && (rc = ensure_e_prev(h))) return rc;
     if (o.subject_weights && (rc = prepare_weights(h, o.subject_weights))) return rc;
     CountsScope counts(h, o.subject_weights != nullptr);
 
@@ -1269,10 +1280,13 @@ int sccs_fit_batch(sccs_handle *const *handles, int32_t n, const sccs_fit_opts *
     }
     if (o.beta0) return fail(SCCS_E_INVAL, "sccs_fit_batch takes no beta0 (use warm_start)");
     if (o.max_cycles < 0) return fail(SCCS_E_INVAL, "max_cycles must be >= 0");
-    if (o.tol_mode != SCCS_TOL_ABS_LOGPOST && o.tol_mode != SCCS_TOL_REL_LOGPOST)
-        return fail(o.tol_mode == SCCS_TOL_GENKIN_XBETA ? SCCS_E_UNSUPPORTED : SCCS_E_INVAL, "unsupported tol_mode");
+    if (o.tol_mode != SCCS_TOL_ABS_LOGPOST && o.tol_mode != SCCS_TOL_REL_LOGPOST &&
+        o.tol_mode != SCCS_TOL_GENKIN_XBETA)
+        return fail(SCCS_E_INVAL, "unknown tol_mode");
     if (o.precision != SCCS_PREC_FP64 && o.precision != SCCS_PREC_FP32_POLISH && o.precision != SCCS_PREC_FP32)
         return fail(SCCS_E_INVAL, "unknown precision");
+    if (o.tol_mode == SCCS_TOL_GENKIN_XBETA && o.precision == SCCS_PREC_FP32)
+        return fail(SCCS_E_UNSUPPORTED, "the Genkin X-beta test needs the FP64 state (use FP64 or FP32 + polish)");
     for (int32_t k = 0; k < n; ++k) {
         if (!handles[k]) return fail(SCCS_E_INVAL, "null handle in batch");
         if (handles[k]->device != handles[0]->device) return fail(SCCS_E_INVAL, "handles on different devices");
@@ -1289,6 +1303,9 @@ int sccs_fit_batch(sccs_handle *const *handles, int32_t n, const sccs_fit_opts *
     if (rc) return rc;
     const int mode = o.precision == SCCS_PREC_FP64 ? sccs::kBatchFp64
                      : o.precision == SCCS_PREC_FP32 ? sccs::kBatchFp32 : sccs::kBatchFp32Polish;
+    if (o.tol_mode == SCCS_TOL_GENKIN_XBETA)
+        for (int32_t k = 0; k < n; ++k)
+            if ((rc = ensure_e_prev(handles[k]))) return rc;
     std::lock_guard<std::mutex> batch_lock(g_batch_mu);
     BatchPlan *plan = nullptr;
     if ((rc = get_batch_plan(handles, n, mode, &plan))) return rc;

@@ -67,6 +67,7 @@ struct DevLayout {
     const int32_t *ycnt;       //   sum of y over the column's rows of that subject
     // state
     double *E;                 // K: L x exp(Xb)
+    double *E_prev;            // K: E at the start of the cycle (Genkin's X-beta rule), or null
     double *D;                 // N: M[L x exp(Xb)]
     float *E32;                // K: L x exp(Xb) in the FP32 mode
     float2 *D32;               // N: M[L x exp(Xb)] as an FP32 (hi, lo) pair in the FP32 mode

@@ -1315,6 +1315,9 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
     double P_prev = 0.0, P = 0.0, conv = 0.0, loglik = 0.0, heldout = __longlong_as_double(0x7ff8000000000000ll);
     long long col = 0;          // wide columns processed: stage buffer = col & 1
     const bool use_narrow = !F32 && d.narrow != nullptr;
+    // Genkin's rule (the paper's Section 2.2 criterion): sum_k |d(Xb)_k| / (1 + sum_k |(Xb)_k|) over
+    // a cycle, with (Xb)_k = log(E_k / l_k) and d(Xb)_k = log(E_k / E_k at the cycle's start).
+    const bool genkin = !F32 && p.tol_mode == 2 && d.E_prev != nullptr;
     unsigned long long run_id = 0;   // narrow runs in this launch
     long long nonzero_nar = 0;       // thread 0 of CTA 0: narrow steps with db != 0
 
@@ -1357,6 +1360,8 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
         __syncthreads();
         status = sh.stop;
     }
+    if (genkin)
+        for (long long k = d.shard_row[s] + threadIdx.x; k < d.shard_row[s + 1]; k += blockDim.x) d.E_prev[k] = d.E[k];
     {
         // Bookkeeping of a finished column (beta, trust radius, the cycle's sums) is done by
         // thread tb at the start of the next column, off the critical path.
@@ -1566,13 +1571,30 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
             __syncthreads();
             if (!(F32 ? refresh_and_reduce32(d, s, seq++, timeout, sh) : refresh_and_reduce(d, s, seq++, timeout, sh)))
                 goto aborted;
+            const double nlogG = sh.G, nlogH = sh.H;   // the refresh's totals (sh.G/H are reused below)
+            double gk_d = 0.0, gk_a = 0.0;
+            if (genkin) {
+                double ds = 0.0, as = 0.0;
+                for (long long k = d.shard_row[s] + threadIdx.x; k < d.shard_row[s + 1]; k += blockDim.x) {
+                    const double e = d.E[k];
+                    ds += fabs(log(e / d.E_prev[k]));
+                    as += fabs(log(e / d.L[k]));
+                    d.E_prev[k] = e;
+                }
+                bool gbad = false;
+                const Fx fa = fx_from_double(ds, gbad), fb = fx_from_double(as, gbad);
+                if (!block_grid_reduce(d, s, seq++, timeout, sh, fa, fb, gbad)) goto aborted;
+                gk_d = sh.G;
+                gk_a = sh.H;
+            }
             if (threadIdx.x == 0) {
                 const double lp = p.prior == 1 ? -0.5 * sh.sq * p.inv_var : (p.prior == 2 ? -p.lambda * sh.ab : 0.0);
-                loglik = sh.lin - (sh.G - sh.H);
+                loglik = sh.lin - (nlogG - nlogH);
                 P = loglik + lp;
                 if (leader && p.record_history) hist[c] = P;
                 conv = fabs(P - P_prev);
                 if (p.tol_mode == 1) conv /= fmax(1.0, fabs(P));
+                if (genkin) conv = gk_d / (1.0 + gk_a);
                 cycles = c;
                 if (!(P == P) || isinf(P)) status = kStNumeric;
                 else if (status == kStNotConverged && p.tol >= 0.0 && conv < p.tol) status = kStOk;

@@ -91,7 +91,7 @@ size_t slot_bytes(const sccs::DevLayout &d, int max_cycles) {
     const size_t N1 = std::max<size_t>(N, 1);
     return al(8 * K) + al(8 * N) + al(4 * K) + al(8 * N) + 2 * al(8 * S * J) +
            al(16 * S * static_cast<size_t>(d.stash_stride)) + al(32 * S) + 2 * al(sizeof(sccs::FitOut)) +
-           al(8 * J) + al(8 * static_cast<size_t>(max_cycles + 1)) + 3 * al(4 * N1) + 2 * al(8 * J) + al(256);
+           al(8 * J) + al(8 * static_cast<size_t>(max_cycles + 1)) + 3 * al(4 * N1) + 2 * al(8 * J) + al(256) + al(8 * K);
 }
 
 }  // namespace
@@ -185,6 +185,7 @@ FitSlot *make_slot(const sccs_handle *dataset, int max_cycles) {
     s->ytx_w = reinterpret_cast<double *>(take(8 * J));
     s->nev_ho = reinterpret_cast<int32_t *>(take(4 * N1));
     auto *nsync = reinterpret_cast<unsigned long long *>(take(256));
+    d.E_prev = reinterpret_cast<double *>(take(8 * std::max<size_t>(K, 1)));   // Genkin's X-beta test
     if (d.narrow) d.nar_sync = nsync;   // the slot's own narrow-run counters
     s->ytx_ho = reinterpret_cast<double *>(take(8 * J));
     d.abort_flag = &s->out_dev->abort_flag;
@@ -517,8 +518,11 @@ int sccs_submit(sccs_server *sv, const sccs_request *req, uint64_t *ticket) {
         return sccs_set_error(SCCS_E_INVAL, "unknown prior type");
     if (req->prior_type != SCCS_PRIOR_NONE && !(req->variance > 0.0 && std::isfinite(req->variance)))
         return sccs_set_error(SCCS_E_INVAL, "prior variance must be positive and finite");
-    if (req->tol_mode != SCCS_TOL_ABS_LOGPOST && req->tol_mode != SCCS_TOL_REL_LOGPOST)
-        return sccs_set_error(SCCS_E_INVAL, "tol_mode must be SCCS_TOL_ABS_LOGPOST or SCCS_TOL_REL_LOGPOST");
+    if (req->tol_mode != SCCS_TOL_ABS_LOGPOST && req->tol_mode != SCCS_TOL_REL_LOGPOST &&
+        req->tol_mode != SCCS_TOL_GENKIN_XBETA)
+        return sccs_set_error(SCCS_E_INVAL, "unknown tol_mode");
+    if (req->tol_mode == SCCS_TOL_GENKIN_XBETA && req->precision == SCCS_PREC_FP32)
+        return sccs_set_error(SCCS_E_UNSUPPORTED, "the Genkin X-beta test needs the FP64 state");
     if (req->max_cycles < 0) return sccs_set_error(SCCS_E_INVAL, "max_cycles must be >= 0");
     if (req->precision != SCCS_PREC_FP64 && req->precision != SCCS_PREC_FP32_POLISH &&
         req->precision != SCCS_PREC_FP32)

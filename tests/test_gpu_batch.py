@@ -124,3 +124,17 @@ def test_destroyed_handle_drops_cached_plans(P):
         finally:
             for m in ms:
                 m.close()
+
+
+def test_batch_with_genkin_rule_equals_standalone(P):
+    ds = _datasets([5000, 20000], seed0=600)
+    ms = _models(P, ds, [2, 6], [("normal", 0.2), ("laplace", 0.1)])
+    try:
+        batch = P.sccs_fit_batch([m.handle for m in ms], [m.J for m in ms], tol_mode="genkin_xbeta", tol=1e-7,
+                                 max_cycles=100)
+        for m, b in zip(ms, batch):
+            r = m.fit(tol_mode="genkin_xbeta", tol=1e-7, max_cycles=100)
+            assert b["cycles"] == r["cycles"] and np.array_equal(r["beta"], b["beta"])
+    finally:
+        for m in ms:
+            m.close()

@@ -419,3 +419,37 @@ def test_step_exponential_against_cuda_exp(P):
     assert np.mean(ulp == 0) > 0.5
     assert ours[x == 0.0].tolist() == [1.0, 1.0]
     assert np.isnan(ours[-1]) and ours[-2] == 0.0 and np.isinf(ours[-3])
+
+
+def _genkin_stat(X, b_now, b_prev):
+    xb, xp = X @ b_now, X @ b_prev
+    return np.abs(xb - xp).sum() / (1.0 + np.abs(xb).sum())
+
+
+@pytest.mark.parametrize("tol", [5e-4, 1e-9])
+def test_genkin_xbeta_rule_against_oracle(P, tol):
+    """Genkin's relative change of X beta over a cycle (the paper's Section 2.2 criterion, tol
+    0.0005 there): the GPU stops at the first cycle whose statistic, computed from the oracle's
+    own trajectory with a dense X, is below tol; its beta is the oracle's at that cycle."""
+    from sccs_testlib import to_dense
+    d, fit = tiny_fit_config()
+    orc = oracle.Problem.from_data(d)
+    X = to_dense(d)
+    with gpu_model(P, d) as m:
+        m.set_prior("normal", 1.0)
+        r = m.fit(tol_mode="genkin_xbeta", tol=tol, max_cycles=500)
+        r32 = m.fit(tol_mode="genkin_xbeta", tol=tol, max_cycles=500, precision="fp32_polish")
+        with pytest.raises(P.SCCSError) as ei:
+            m.fit(tol_mode="genkin_xbeta", tol=tol, precision="fp32")
+        assert ei.value.code == P.sccs.E_UNSUPPORTED
+    c = r["cycles"]
+    assert r["rc"] == 0 and c >= 1 and r32["rc"] == 0
+    same = orc.fit(prior="normal", variance=1.0, fixed_cycles=c)
+    prev = orc.fit(prior="normal", variance=1.0, fixed_cycles=c - 1)
+    np.testing.assert_allclose(r["beta"], same["beta"], atol=1e-11, rtol=0)
+    assert _genkin_stat(X, same["beta"], prev["beta"]) < tol * (1 + 1e-6)
+    if c > 1:
+        pprev = orc.fit(prior="normal", variance=1.0, fixed_cycles=c - 2)
+        assert _genkin_stat(X, prev["beta"], pprev["beta"]) >= tol * (1 - 1e-6)
+    ocycles = orc.fit(prior="normal", variance=1.0, tol_mode="genkin_xbeta", tol=tol, max_cycles=500)["cycles"]
+    assert ocycles == c
