@@ -498,7 +498,8 @@ def run_batched(args, rank, world, local):
     return 0
 
 
-def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, budget, seed0, folds_of=None):
+def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, budget, seed0, folds_of=None,
+                 alts_of=None):
     """Submit each rate's Poisson arrivals to a fresh server and collect latencies.  With
     folds_of (per outcome, the fold of each input subject), a request with fold k fits on the
     other folds and returns the held-out predictive log-likelihood of fold k."""
@@ -518,7 +519,8 @@ def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, 
                     time.sleep(dt)
                 tickets.append(sccs.sccs_submit(srv.server, handles_of[o], prior=prior, variance=var,
                                                 tol_mode="rel_logpost", tol=1e-12, max_cycles=1000,
-                                                weights=wt, heldout_weights=wh))
+                                                weights=wt, heldout_weights=wh,
+                                                dataset_alt=None if alts_of is None else alts_of[o]))
             out = []
             for t, (ta, o, *_rest) in zip(tickets, reqs):
                 while True:
@@ -535,7 +537,8 @@ def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, 
                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                      "mean_queue_ms": float(np.mean([r["queue_ms"] for r in out])),
                      "failed": int(sum(1 for r in out if r["status"] < 0)),
-                     "heldout_evaluated": int(sum(1 for r in out if np.isfinite(r["heldout_loglik"])))})
+                     "heldout_evaluated": int(sum(1 for r in out if np.isfinite(r["heldout_loglik"]))),
+                     "on_full_device_team": int(sum(1 for r in out if r["team"] >= 100))})
     return rows
 
 
@@ -582,7 +585,7 @@ def run_serving(args, rank, world, local):
                      folds_of)
     with ClockSampler(local) as clk:
         ours = _serve_sweep(sccs, local, [m.handle for m in served], Js, rates, args.requests, 64, budget, 2000,
-                            folds_of)
+                            folds_of, alts_of=[m.handle for m in plain])
     clocks = clk.summary()
     one = _serve_sweep(sccs, local, [m.handle for m in plain], Js, rates, args.requests, 1, 0, 2000, folds_of)
     top = ours[-1]
@@ -596,7 +599,8 @@ def run_serving(args, rank, world, local):
                                    f"{args.max_eras / 1e6:g}M, 1000-5000 drugs, Zipf(1.2) columns up to eras/5; "
                                    "requests = outcome x Normal/Laplace x variance grid "
                                    "{0.01..1} x fold 1..10 (fit on 9 folds, held-out predictive log-likelihood "
-                                   "of the 10th returned), FP64 to rel |dP| < 1e-12; "
+                                   "of the 10th returned), FP64 to rel |dP| < 1e-12; each outcome resident with "
+                                   "an autotuned team and a full-device team, the server choosing per request; "
                                    + (f"{args.requests} Poisson arrivals per rate" if args.requests > 0 else
                                       "3 s of Poisson arrivals per rate (32 to 192 requests)"),
                        "outcomes": args.outcomes, "eras": int(sum(i["rows_kept"] for i in infos)),

@@ -256,7 +256,7 @@ typedef struct sccs_request {
     int32_t prior_type;        /* SCCS_PRIOR_* */
     sccs_handle *dataset;      /* from sccs_create; must outlive the request */
     double variance;           /* prior variance (Eq. 3) */
-    int32_t tol_mode;          /* SCCS_TOL_ABS_LOGPOST or SCCS_TOL_REL_LOGPOST */
+    int32_t tol_mode;          /* SCCS_TOL_* */
     int32_t max_cycles;
     double tol;
     int32_t precision;         /* SCCS_PREC_* */
@@ -268,13 +268,17 @@ typedef struct sccs_request {
     const int32_t *heldout_weights;  /* per input subject (copied at submit): after the fit,
                                   res->heldout_loglik = sccs_heldout_loglik at the fitted beta with
                                   these weights (the held-out fold's mask); NULL = not evaluated */
+    sccs_handle *dataset_alt;  /* NULL, or the same data created with another shard count: when the
+                                  device is idle and no other request waits, the request runs on
+                                  whichever of the two has the larger team (lower latency); otherwise
+                                  on the smaller (more fits side by side).  res->team says which. */
 } sccs_request;
 
 typedef struct sccs_result {
     int32_t status;            /* SCCS_OK, SCCS_NOT_CONVERGED or the fit's error */
     int32_t cycles;
     int32_t fp32_cycles;
-    int32_t reserved;
+    int32_t team;              /* shards (CTAs) of the handle the fit ran on (dataset or dataset_alt) */
     double logpost;
     double queue_ms;           /* submit -> start on the device */
     double latency_ms;         /* submit -> result ready */

@@ -61,7 +61,10 @@ struct FitSlot {
 
 struct Request {
     uint64_t ticket = 0;
-    sccs_handle *dataset = nullptr;
+    sccs_handle *dataset = nullptr;     // the handle the fit runs on (chosen at admission)
+    sccs_handle *small = nullptr;       // the smaller-team handle of the request (or its only one)
+    sccs_handle *large = nullptr;       // the larger-team handle, or null
+    int S_small = 0, S_large = 0;
     int prior = SCCS_PRIOR_NONE;
     double variance = 1.0;
     int tol_mode = SCCS_TOL_REL_LOGPOST;
@@ -382,8 +385,17 @@ void worker_main(sccs_server *sv) {
                     finish(sv, r, SCCS_E_INVAL);
                     continue;
                 }
+                // an idle device and nothing else waiting: the larger team, for latency
+                const bool go_large = r->large && sv->running.empty() && sv->pending.size() == 1;
+                r->dataset = go_large ? r->large : r->small;
+                r->S = go_large ? r->S_large : r->S_small;
                 if (sv->ctas_in_use + r->S > sv->capacity_ctas && !sv->running.empty()) break;
                 FitSlot *s = acquire_slot(sv, *r);
+                if (!s && go_large) {       // the larger team's state does not fit the budget
+                    r->dataset = r->small;
+                    r->S = r->S_small;
+                    s = acquire_slot(sv, *r);
+                }
                 if (!s) {
                     if (sv->running.empty()) {   // it will never fit
                         sv->pending.pop_front();
@@ -528,8 +540,29 @@ int sccs_submit(sccs_server *sv, const sccs_request *req, uint64_t *ticket) {
         req->precision != SCCS_PREC_FP32)
         return sccs_set_error(SCCS_E_INVAL, "unknown precision");
     if (v.d.S > sv->capacity_ctas) return sccs_set_error(SCCS_E_INVAL, "dataset has more shards than the device holds");
+    sccs::HandleView va{};
+    if (req->dataset_alt) {
+        if (!sccs_handle_view(req->dataset_alt, &va)) return sccs_set_error(SCCS_E_INVAL, "bad dataset_alt");
+        if (va.device != v.device || va.d.J != v.d.J || va.d.K != v.d.K || va.d.N != v.d.N ||
+            va.subjects_in != v.subjects_in)
+            return sccs_set_error(SCCS_E_INVAL, "dataset_alt does not hold the same data as dataset");
+        if (va.d.S > sv->capacity_ctas) return sccs_set_error(SCCS_E_INVAL, "dataset_alt has more shards than the device holds");
+    }
     Request *r = new Request();
     r->dataset = req->dataset;
+    r->small = req->dataset;
+    r->S_small = v.d.S;
+    if (req->dataset_alt && req->dataset_alt != req->dataset) {
+        if (va.d.S >= v.d.S) {
+            r->large = req->dataset_alt;
+            r->S_large = va.d.S;
+        } else {
+            r->large = req->dataset;
+            r->S_large = v.d.S;
+            r->small = req->dataset_alt;
+            r->S_small = va.d.S;
+        }
+    }
     r->prior = req->prior_type;
     r->variance = req->variance;
     r->tol_mode = req->tol_mode;
@@ -586,6 +619,7 @@ int sccs_poll(sccs_server *sv, uint64_t ticket, sccs_result *res) {
     Request *r = it->second;
     if (r->phase != 3) return SCCS_PENDING;
     res->status = r->status;
+    res->team = r->S;
     res->cycles = r->cycles;
     res->fp32_cycles = r->fp32_cycles;
     res->logpost = r->logpost;

@@ -70,12 +70,12 @@ class sccs_request(ctypes.Structure):
                 ("variance", ctypes.c_double), ("tol_mode", ctypes.c_int32), ("max_cycles", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("beta0", ctypes.POINTER(ctypes.c_double)), ("subject_weights", ctypes.POINTER(ctypes.c_int32)),
-                ("heldout_weights", ctypes.POINTER(ctypes.c_int32))]
+                ("heldout_weights", ctypes.POINTER(ctypes.c_int32)), ("dataset_alt", ctypes.c_void_p)]
 
 
 class sccs_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("cycles", ctypes.c_int32), ("fp32_cycles", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("logpost", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("team", ctypes.c_int32), ("logpost", ctypes.c_double), ("queue_ms", ctypes.c_double),
                 ("latency_ms", ctypes.c_double), ("beta", ctypes.POINTER(ctypes.c_double)),
                 ("heldout_loglik", ctypes.c_double)]
 
@@ -302,13 +302,14 @@ def sccs_server_create(device=0, max_inflight=64, queue_capacity=4096, hbm_budge
 
 
 def sccs_submit(server, dataset, prior="normal", variance=1.0, tol_mode="rel_logpost", tol=1e-12,
-                max_cycles=1000, precision="fp64", beta0=None, weights=None, heldout_weights=None) -> int:
+                max_cycles=1000, precision="fp64", beta0=None, weights=None, heldout_weights=None,
+                dataset_alt=None) -> int:
     b0 = None if beta0 is None else np.ascontiguousarray(beta0, np.float64)
     w, wh = _weights(weights), _weights(heldout_weights)
     r = sccs_request(struct_size=ctypes.sizeof(sccs_request), prior_type=PRIOR[prior], dataset=dataset,
                      variance=float(variance), tol_mode=TOL[tol_mode], max_cycles=int(max_cycles), tol=float(tol),
                      precision=PREC[precision], reserved=0, beta0=_dptr(b0), subject_weights=_iptr(w),
-                     heldout_weights=_iptr(wh))
+                     heldout_weights=_iptr(wh), dataset_alt=dataset_alt)
     t = ctypes.c_uint64()
     _check(_lib.sccs_submit(server, ctypes.byref(r), ctypes.byref(t)), "sccs_submit")
     return t.value
@@ -343,8 +344,9 @@ class FitServer:
         self.server = sccs_server_create(device, max_inflight, queue_capacity, hbm_budget_bytes)
         self._J = {}
 
-    def submit(self, model, **kw) -> int:
-        t = sccs_submit(self.server, model.handle, **kw)
+    def submit(self, model, alt=None, **kw) -> int:
+        """alt: another SCCSModel of the same data with a different shard count (see dataset_alt)."""
+        t = sccs_submit(self.server, model.handle, dataset_alt=None if alt is None else alt.handle, **kw)
         self._J[t] = model.J
         return t
 

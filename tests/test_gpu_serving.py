@@ -141,3 +141,32 @@ def test_destroy_with_requests_outstanding(P, models):
     m = models[0]
     m.set_prior("normal", 1.0)
     assert m.fit(tol=1e-10)["status"] == P.sccs.OK
+
+
+def test_alternative_team_at_low_and_high_load(P):
+    """A request naming two layouts of the same data runs on the larger team when the device is
+    idle and on the smaller one in a burst; each result equals the standalone fit on the handle
+    it ran on, bit for bit."""
+    d = _data(40000, 510)
+    small = P.SCCSModel(d, device=0, num_shards=6)
+    large = P.SCCSModel(d, device=0, num_shards=48)
+    try:
+        kw = dict(prior="normal", variance=0.2, tol=1e-12, max_cycles=200)
+        alone = {}
+        for m in (small, large):
+            m.set_prior("normal", 0.2)
+            alone[m.info["num_shards"]] = m.fit(tol=1e-12, max_cycles=200)
+        with P.FitServer(device=0, max_inflight=16) as srv:
+            quiet = [srv.wait(srv.submit(small, alt=large, **kw)) for _ in range(3)]
+            burst = [srv.submit(small, alt=large, **kw) for _ in range(12)]
+            burst = [srv.wait(t) for t in burst]
+        assert all(r["team"] == 48 for r in quiet)
+        assert any(r["team"] == 6 for r in burst)
+        for r in quiet + burst:
+            a = alone[r["team"]]
+            assert r["cycles"] == a["cycles"] and r["logpost"] == a["logpost"]
+            assert np.array_equal(r["beta"], a["beta"])
+        np.testing.assert_allclose(alone[6]["beta"], alone[48]["beta"], atol=1e-12, rtol=0)
+    finally:
+        small.close()
+        large.close()
