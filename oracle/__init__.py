@@ -82,6 +82,9 @@ def _bind(lib):
     lib.oracle_fit.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                ctypes.c_int, P, f64p, f64p, ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_raw_eval.restype = ctypes.c_int
+    lib.oracle_raw_eval.argtypes = [ctypes.c_int64, i64p, i32p, f64p, ctypes.c_int32, i64p, i32p, f64p,
+                                    ctypes.c_int32, i32p, ctypes.POINTER(ctypes.c_double), f64p, f64p]
     lib.oracle_subjects_in.restype = ctypes.c_int64
     lib.oracle_subjects_in.argtypes = [P]
     lib.oracle_loglik_w.restype = ctypes.c_double
@@ -201,3 +204,21 @@ class Problem:
         t = cyc.value
         return dict(status=rc, beta=beta, cycles=t, logpost=float(hist[t]), history=hist[:t + 1].copy(),
                     nonzero_steps=int(nz.value), warning=bool(warn.value))
+
+
+def raw_eval(d, beta, cols, lib=None):
+    """Eq. 2 and (g_j, h_j) of Eqs. 7-9 for the columns `cols`, straight from the input arrays of
+    dataset d (no canonical copy; for sampled checks of very large problems).
+    Returns (loglik, g array, h array)."""
+    lib = _load() if lib is None else lib
+    cols = np.ascontiguousarray(cols, np.int32)
+    g = np.zeros(cols.size)
+    h = np.zeros(cols.size)
+    ll = ctypes.c_double()
+    rc = lib.oracle_raw_eval(int(d.K), np.ascontiguousarray(d.patient_id, np.int64),
+                             np.ascontiguousarray(d.y, np.int32), np.ascontiguousarray(d.L, np.float64), int(d.J),
+                             np.ascontiguousarray(d.col_ptr, np.int64), np.ascontiguousarray(d.row_idx, np.int32),
+                             np.ascontiguousarray(beta, np.float64), int(cols.size), cols, ctypes.byref(ll), g, h)
+    if rc != OK:
+        raise OracleError(rc, "raw_eval")
+    return ll.value, g, h

@@ -478,3 +478,67 @@ int oracle_fit(const oracle_problem *p, int prior, double var, int tol_mode, dou
     return oracle_fit_w(p, prior, var, tol_mode, tol, max_cycles, beta0, NULL, beta_out, hist,
                         cycles_out, nonzero_steps_out, warn_out);
 }
+
+/* Eq. 2 and Eqs. 7-9 straight from the input arrays (no canonical copy: for sampled checks of
+ * very large problems).  One pass builds Xb per row from scratch, one the denominators and n_i
+ * per input subject (a run of equal patient_id; subjects with n_i = 0 contribute nothing, R8),
+ * then L(b) and, for each requested column, g_j = Y'X_j - sum_i n_i W_ij and
+ * h_j = -sum_i n_i W_ij (1 - W_ij).  Rows of a column may come in any order.  Returns ORC_OK,
+ * ORC_E_INVAL or ORC_E_NOMEM. */
+int oracle_raw_eval(int64_t K, const int64_t *patient_id, const int32_t *y, const double *L, int32_t J,
+                    const int64_t *col_ptr, const int32_t *row_idx, const double *beta, int32_t ncols,
+                    const int32_t *cols, double *loglik_out, double *g_out, double *h_out) {
+    if (K < 0 || J < 0 || ncols < 0) return ORC_E_INVAL;
+    for (int32_t c = 0; c < ncols; ++c)
+        if (cols[c] < 0 || cols[c] >= J) return ORC_E_INVAL;
+    double *xb = (double *)xcalloc((size_t)K, sizeof(double));
+    int64_t *sub = (int64_t *)xcalloc((size_t)K, sizeof(int64_t));
+    if (!xb || !sub) { free(xb); free(sub); return ORC_E_NOMEM; }
+    for (int32_t j = 0; j < J; ++j) {
+        if (beta[j] == 0.0) continue;
+        for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) xb[row_idx[e]] += beta[j];
+    }
+    int64_t nsub = 0;
+    for (int64_t k = 0; k < K; ++k) {
+        if (k == 0 || patient_id[k] != patient_id[k - 1]) nsub++;
+        sub[k] = nsub - 1;
+    }
+    double *D = (double *)xcalloc((size_t)nsub, sizeof(double));
+    double *num = (double *)xcalloc((size_t)nsub, sizeof(double));
+    int64_t *n = (int64_t *)xcalloc((size_t)nsub, sizeof(int64_t));
+    if (!D || !num || !n) { free(xb); free(sub); free(D); free(num); free(n); return ORC_E_NOMEM; }
+    double lin = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+        D[sub[k]] += L[k] * exp(xb[k]);
+        n[sub[k]] += y[k];
+        lin += (double)y[k] * xb[k];
+    }
+    double nlog = 0.0;
+    for (int64_t i = 0; i < nsub; ++i)
+        if (n[i] > 0) nlog += (double)n[i] * log(D[i]);
+    if (loglik_out) *loglik_out = lin - nlog;
+    for (int32_t c = 0; c < ncols; ++c) {
+        const int32_t j = cols[c];
+        int64_t ytx = 0;
+        for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) {
+            const int64_t k = row_idx[e];
+            num[sub[k]] += L[k] * exp(xb[k]);
+            if (n[sub[k]] > 0) ytx += y[k];
+        }
+        double nW = 0.0, nWW = 0.0;
+        for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) {
+            const int64_t i = sub[row_idx[e]];
+            if (num[i] == 0.0) continue;      /* this subject's term was taken already */
+            if (n[i] > 0) {
+                const double Wi = num[i] / D[i];
+                nW += (double)n[i] * Wi;
+                nWW += (double)n[i] * Wi * (1.0 - Wi);
+            }
+            num[i] = 0.0;
+        }
+        g_out[c] = (double)ytx - nW;
+        h_out[c] = -nWW;
+    }
+    free(xb); free(sub); free(D); free(num); free(n);
+    return ORC_OK;
+}

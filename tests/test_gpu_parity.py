@@ -453,3 +453,34 @@ def test_genkin_xbeta_rule_against_oracle(P, tol):
         assert _genkin_stat(X, prev["beta"], pprev["beta"]) >= tol * (1 - 1e-6)
     ocycles = orc.fit(prior="normal", variance=1.0, tol_mode="genkin_xbeta", tol=tol, max_cycles=500)["cycles"]
     assert ocycles == c
+
+
+@pytest.mark.slow
+def test_paper_scale_sampled_against_oracle(P):
+    """The paper-scale workload at full size (4M subjects, 5,000 drugs, ~1e9 nonzeros, Laplace) in
+    FP32 + FP64 polish, checked on sampled outputs the oracle computes straight from the input
+    arrays: L at the fitted beta, g_j and h_j of sampled columns (the largest, the smallest, the
+    largest effects, random ones), and the Laplace optimality conditions with the oracle's g_j."""
+    from synth import paper_scale_config
+    d, fit = paper_scale_config()
+    with gpu_model(P, d) as m:
+        m.set_prior(fit["prior"], fit["variance"])
+        r = m.fit(precision="fp32_polish", tol_mode="rel_logpost", tol=1e-15, max_cycles=60)
+        beta = r["beta"]
+        nnz = np.diff(d.col_ptr)
+        rng = np.random.default_rng(0)
+        cols = sorted({0, 1, int(np.argmax(nnz)), int(np.argmin(nnz)), *map(int, np.argsort(-np.abs(beta))[:3]),
+                       *map(int, rng.choice(d.J, 5, replace=False))})
+        gh = np.array([m.grad_hess(j, beta) for j in cols])
+        ll_gpu = m.logpost(beta)[1]
+    ll, g, h = oracle.raw_eval(d, beta, cols)
+    assert rel(ll_gpu, ll) <= 1e-12
+    scale = np.maximum(1.0, np.abs(h))
+    np.testing.assert_array_less(np.abs(gh[:, 0] - g), 1e-9 * scale)
+    np.testing.assert_array_less(np.abs(gh[:, 1] - h), 1e-9 * scale)
+    lam = np.sqrt(2.0 / fit["variance"])
+    b = beta[cols]
+    nzs = b != 0
+    np.testing.assert_array_less(np.abs(g[nzs] - lam * np.sign(b[nzs])), 1e-6 * scale[nzs])
+    np.testing.assert_array_less(np.abs(g[~nzs]), lam + 1e-6 * scale[~nzs])
+    assert nzs.sum() >= 3

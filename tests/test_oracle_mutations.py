@@ -30,6 +30,9 @@ MUTATIONS = [
     ("weights_ignored_in_n", "wn[i] = weight_of(p, w_in, i) * p->n[i];", "wn[i] = p->n[i];"),
     ("weights_ignored_in_loglik", "total += (double)weight_of(p, w_in, i) * (", "total += ("),
     ("weights_by_kept_subject", "return w_in ? w_in[p->sub_in[i]] : 1;", "return w_in ? w_in[i] : 1;"),
+    # the evaluation straight from the input arrays
+    ("raw_eval_unweighted_W", "nW += (double)n[i] * Wi;", "nW += Wi;"),
+    ("raw_eval_counts_zero_event_rows", "if (n[sub[k]] > 0) ytx += y[k];", "ytx += y[k] + (n[sub[k]] == 0);"),
 ]
 
 PIN_CASES = [
@@ -42,6 +45,7 @@ PIN_CASES = [
     (pins.test_laplace_kkt_certificate, dict(seed=1, var=0.2)),
     (wpins.test_weighted_fit_equals_replicated_dataset, dict(seed=0, prior="normal", var=0.5)),
     (wpins.test_fold_fit_and_heldout_loglik, dict(seed=0)),
+    (pins.test_raw_eval_equals_canonical_oracle, dict(seed=0)),
 ]
 
 

@@ -310,3 +310,22 @@ def test_input_validation():
     bad[0] = d.K
     with pytest.raises(oracle.OracleError):
         oracle.Problem(d.K, d.patient_id, d.y, d.L, d.J, d.col_ptr, bad)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_raw_eval_equals_canonical_oracle(seed):
+    """The evaluation straight from the input arrays (used for sampled checks at sizes too big
+    for the canonical copy) against the canonical oracle, with zero-event subjects and rows of
+    a column in shuffled order."""
+    d = random_tiny(seed, n_patients=25, J=5, with_zero_subjects=True, beta_scale=0.5)
+    rng = np.random.default_rng(seed)
+    for j in range(d.J):            # shuffle each column's rows
+        a, b = d.col_ptr[j], d.col_ptr[j + 1]
+        d.row_idx[a:b] = rng.permutation(d.row_idx[a:b])
+    beta = rng.normal(0, 0.6, size=d.J)
+    p = oracle.Problem.from_data(d, lib=ORACLE_LIB)
+    ll, g, h = oracle.raw_eval(d, beta, np.arange(d.J), lib=ORACLE_LIB)
+    assert ll == pytest.approx(p.loglik(beta), rel=1e-13, abs=1e-12)
+    for j in range(d.J):
+        gc, hc = p.grad_hess(j, beta)
+        assert g[j] == pytest.approx(gc, rel=1e-12, abs=1e-12) and h[j] == pytest.approx(hc, rel=1e-12, abs=1e-12)
