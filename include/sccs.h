@@ -84,7 +84,10 @@ typedef struct sccs_create_opts {
                                   subjects) run whole on one CTA of the team with block-level sums
                                   instead of a grid-wide reduction per coordinate (FP64 fits,
                                   4 or more shards): 0 = the default 1024; < 0 = never */
-    int32_t reserved;
+    int32_t narrow_group_max;  /* consecutive narrow columns whose subjects are pairwise disjoint
+                                  have their steps taken side by side, up to this many at a time
+                                  (the result is the sequential one): 0 = the default 8; 1 = one
+                                  at a time */
 } sccs_create_opts;
 
 typedef struct sccs_data_info {

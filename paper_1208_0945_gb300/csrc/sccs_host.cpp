@@ -210,9 +210,12 @@ struct HostLayout {
     std::vector<int64_t> nar_ptr;     // J+1
     std::vector<int4> nar_seg;        // {subject, rows, first row in nar_row, 0}
     std::vector<int32_t> nar_row;
+    std::vector<int32_t> nar_group;   // J: at a group's first column, its number of columns; else 0
+    int32_t narrow_groups = 0;
 };
 
 constexpr int32_t kNarrowDefault = 1024;
+using sccs::kNarrowGroupMax;
 constexpr int32_t kNarrowMinShards = 4;
 
 // Checks everything about the inputs that needs no GPU.
@@ -245,7 +248,8 @@ int validate_inputs(int64_t K, const int64_t *patient_id, const int32_t *y, cons
 }
 
 int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const double *Lin, int32_t J,
-                 const int64_t *col_ptr, const int32_t *row_idx, int32_t S, int32_t narrow_max, HostLayout &hl) {
+                 const int64_t *col_ptr, const int32_t *row_idx, int32_t S, int32_t narrow_max, int32_t group_max,
+                 HostLayout &hl) {
     // ---- subjects, n_i, dropping n_i = 0
     std::vector<int64_t> sub_start;
     std::vector<int64_t> sub_n;
@@ -412,6 +416,52 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
                 hl.nar_seg[q].y++;
                 hl.nar_row.push_back(r);
             }
+        }
+        // Groups: consecutive narrow columns with pairwise disjoint subjects.  Neither column of a
+        // pair reads what the other writes (their subjects' E and D), so their coordinate steps can
+        // be taken side by side and give exactly the sequential result.  A group fits half the
+        // shared buffers (rows, segments), like one narrow column.
+        hl.nar_group.assign(static_cast<size_t>(J), 0);
+        std::vector<uint8_t> mark(static_cast<size_t>(std::max<int64_t>(hl.N, 1)), 0);
+        std::vector<int32_t> marked;
+        auto subjects_of = [&](int32_t j, bool set, bool &clash) {
+            for (int64_t q = hl.nar_ptr[j]; q < hl.nar_ptr[j + 1]; ++q) {
+                const int32_t i = hl.nar_seg[q].x;
+                if (mark[i]) clash = true;
+                if (set && !mark[i]) {
+                    mark[i] = 1;
+                    marked.push_back(i);
+                }
+            }
+        };
+        int32_t j = 0;
+        while (j < J) {
+            if (!hl.narrow[j]) {
+                ++j;
+                continue;
+            }
+            int32_t m = 1;
+            int64_t segs = hl.nar_ptr[j + 1] - hl.nar_ptr[j];
+            int64_t rows = cptr[j + 1] - cptr[j];
+            bool clash = false;
+            subjects_of(j, true, clash);
+            while (j + m < J && hl.narrow[j + m] && m < group_max) {
+                const int32_t jn = j + m;
+                const int64_t sg = hl.nar_ptr[jn + 1] - hl.nar_ptr[jn], rw = cptr[jn + 1] - cptr[jn];
+                if (segs + sg > sccs::kSegCap / 2 || rows + rw > sccs::kRowCap / 2) break;
+                clash = false;
+                subjects_of(jn, false, clash);
+                if (clash) break;
+                subjects_of(jn, true, clash);
+                segs += sg;
+                rows += rw;
+                ++m;
+            }
+            for (int32_t i : marked) mark[i] = 0;
+            marked.clear();
+            hl.nar_group[j] = m;
+            hl.narrow_groups++;
+            j += m;
         }
     }
     for (int32_t j = 0; j < J; ++j)
@@ -959,7 +1009,10 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
 
     HostLayout hl;
     const int32_t narrow_max = o.narrow_max_nnz == 0 ? kNarrowDefault : o.narrow_max_nnz;
-    int rc = build_layout(K, patient_id, y, offset_L, J, col_ptr, row_idx, S, narrow_max, hl);
+    // every column of a group keeps at least two warps of the CTA
+    const int32_t group_cap = std::max(1, std::min(kNarrowGroupMax, threads / 64));
+    const int32_t group_max = o.narrow_group_max <= 0 ? group_cap : std::min(o.narrow_group_max, group_cap);
+    int rc = build_layout(K, patient_id, y, offset_L, J, col_ptr, row_idx, S, narrow_max, group_max, hl);
     if (rc != SCCS_OK) return rc;
 
     sccs_handle *h = new sccs_handle();
@@ -1080,7 +1133,7 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     }
     if (hl.narrow_count > 0) {
         uint8_t *nar;
-        int32_t *nxt, *nrow;
+        int32_t *nxt, *nrow, *ngrp;
         int64_t *nptr;
         int4 *nseg;
         unsigned long long *nsync;
@@ -1089,6 +1142,7 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
             (rc = upload(h, &nptr, hl.nar_ptr.data(), hl.nar_ptr.size())) ||
             (rc = upload(h, &nseg, hl.nar_seg.data(), hl.nar_seg.size())) ||
             (rc = upload(h, &nrow, hl.nar_row.data(), hl.nar_row.size())) ||
+            (rc = upload(h, &ngrp, hl.nar_group.data(), hl.nar_group.size())) ||
             (rc = alloc_zero(h, &nsync, static_cast<size_t>(32))))
             return bail(rc);
         d.narrow = nar;
@@ -1097,6 +1151,7 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
         d.nar_ptr = nptr;
         d.nar_seg = nseg;
         d.nar_row = nrow;
+        d.nar_group = ngrp;
         d.nar_sync = nsync;
     }
     if ((rc = run_init_state(h, nullptr))) return bail(rc);

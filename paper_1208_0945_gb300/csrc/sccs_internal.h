@@ -29,6 +29,7 @@ constexpr int kWarp = 32;
 constexpr int kSegCap = 2048;              // segments per staged slice
 constexpr int kRowCap = 4096;              // nonzeros per staged slice
 constexpr int kGrpCap = kSegCap / 32;      // groups per staged slice
+constexpr int kNarrowGroupMax = 8;         // narrow columns whose steps are taken side by side
 // Global arrays read by bulk copies are padded by this many bytes past their end, so a copy
 // rounded out to 16-byte boundaries stays inside the allocation.
 constexpr int kCopyPad = 32;
@@ -59,6 +60,7 @@ struct DevLayout {
     const int64_t *nar_ptr;    // J+1: a narrow column's segments in nar_seg
     const int4 *nar_seg;       //   {subject, rows, first row in nar_row, 0}, subjects ascending
     const int32_t *nar_row;    //   rows of each segment, ascending
+    const int32_t *nar_group;  // J: columns in the group starting at j (0 inside a group)
     unsigned long long *nar_sync;  // per fit state: [0] CTAs arrived at a narrow run, [16] runs done
     const int64_t *row_ptr;    // K+1: row -> columns index (built on the device at create)
     const int32_t *row_col;    //   the columns of each row, ascending

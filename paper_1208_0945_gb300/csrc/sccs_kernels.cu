@@ -278,6 +278,10 @@ struct SharedState {
     int wbad[kMaxWarps];
     double db, r, em1;
     double nbj;             // a narrow column's new beta_j
+    // a group of narrow columns: per column step results, and the group's flags
+    double gdb[kNarrowGroupMax], gr[kNarrowGroupMax], gem1[kNarrowGroupMax], gnbj[kNarrowGroupMax],
+        gtrust[kNarrowGroupMax];
+    int gnumeric, gwarn, gnonzero, gchanged;
     double G, H;
     double lin, sq, ab;     // cycle sums of b_j Y'X_j, b_j^2, |b_j| (from the bookkeeping thread)
     long long nonzero;
@@ -1120,23 +1124,6 @@ __device__ bool wait_counter(const unsigned long long *ctr, unsigned long long t
     }
 }
 
-// Static data of narrow column j into L1 ahead of use (segments and rows never change, so an
-// early copy cannot go stale), spread over the `nthr` threads t0, t0 + 1, ... that call it.
-__device__ __forceinline__ void prefetch_narrow(const DevLayout &d, int j, int t, int nthr) {
-    const long long a = d.nar_ptr[j], b = d.nar_ptr[j + 1];
-    const long long nseg = b - a;
-    if (nseg <= 0) return;
-    const char *sp = reinterpret_cast<const char *>(d.nar_seg + a);
-    const long long sbytes = nseg * static_cast<long long>(sizeof(int4));
-    for (long long o = static_cast<long long>(t) * 128; o < sbytes; o += static_cast<long long>(nthr) * 128)
-        prefetch_l1(sp + o);
-    const int4 f = d.nar_seg[a], l = d.nar_seg[b - 1];
-    const char *rp = reinterpret_cast<const char *>(d.nar_row + f.z);
-    const long long rbytes = static_cast<long long>(l.z + l.y - f.z) * 4;
-    for (long long o = static_cast<long long>(t) * 128; o < rbytes; o += static_cast<long long>(nthr) * 128)
-        prefetch_l1(rp + o);
-}
-
 // The state wide column j will read on shard s (E at the slice's rows, D at its subjects) into
 // L2, spread over nthr threads.
 __device__ __forceinline__ void prefetch_slice_state_l2(const DevLayout &d, int s, int j, int t, int nthr) {
@@ -1145,22 +1132,23 @@ __device__ __forceinline__ void prefetch_slice_state_l2(const DevLayout &d, int 
     for (long long si = d.slice_seg[so] + t; si < d.slice_seg[so + 1]; si += nthr) prefetch_l2(d.D + d.segs[si].x);
 }
 
-// Narrow columns j0..j1-1 on this CTA (the team's CTA 0).  beta / trust: this CTA's copies;
-// every shard's copy of beta_j is written too.  Thread 0 carries status, warn, nonzero.
+// Narrow columns j0..j1-1 on this CTA (the team's CTA 0), a group at a time: the columns of a
+// group touch pairwise disjoint subjects, so each takes its step on its own warps, side by side,
+// with the sequential result.  beta / trust: this CTA's copies; every shard's copy of beta_j is
+// written too.  Thread 0 carries status, warn, nonzero.
 //
-// Pipelined: while warp 0 takes column j's step, warps 1.. gather column j+1 (numerators, D,
-// the E values of its rows) into the other half of the shared buffers.  After column j's
-// updates each of column j+1's subjects re-reads D_i: a subject whose rows column j changed has
-// a changed D_i, and is gathered again; the W terms are then formed from data as current as a
-// gather made at that point.
-__device__ void narrow_gather(const DevLayout &d, int j, int t, int nthr, double *est, double2 *stash) {
-    const long long a = d.nar_ptr[j];
-    const int nseg = static_cast<int>(d.nar_ptr[j + 1] - a);
-    const int row0 = nseg > 0 ? d.nar_seg[a].z : 0;
+// Pipelined: while the groups' first warps take the steps, the other warps gather the next group
+// (numerators, D, the E values of its rows) into the other half of the shared buffers.  After
+// this group's updates each subject of the next group re-reads D_i: a subject whose rows this
+// group changed has a changed D_i and is gathered again; the W terms are formed then.
+__device__ void narrow_gather(const DevLayout &d, int j, int m, int t, int nthr, double *est, double2 *stash) {
+    const long long ga = d.nar_ptr[j], gb = d.nar_ptr[j + m];
+    const int nseg = static_cast<int>(gb - ga);
+    const int row0 = nseg > 0 ? d.nar_seg[ga].z : 0;
     for (int q = t; q < nseg; q += nthr) {
-        const int4 sg = d.nar_seg[a + q];
+        const int4 sg = d.nar_seg[ga + q];
         const double Dv = d.D[sg.x];
-        prefetch_l1(d.nev + sg.x);          // static: read after the step, when the terms are formed
+        prefetch_l1(d.nev + sg.x);          // static: read after the steps, when the terms are formed
         double num = 0.0;
         for (int u = 0; u < sg.y; ++u) {
             const double e = d.E[d.nar_row[sg.z + u]];
@@ -1175,59 +1163,64 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
                                SharedState &sh, double *beta, double *trust, int &status, int &warn,
                                long long &nonzero) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    prefetch_narrow(d, j0, threadIdx.x, blockDim.x);
-    bool gathered = false;     // column j's data was gathered during the previous step
-    double db_prev = 0.0;
-    for (int j = j0; j < j1; ++j) {
-        const int half = (j - j0) & 1;
+    bool gathered = false;     // this group was gathered during the previous group's steps
+    bool changed = true;       // ... and a step since then may have changed its subjects' state
+    int half = 0;
+    for (int j = j0; j < j1;) {
+        const int m = d.nar_group[j] > 0 ? d.nar_group[j] : 1;
+        const int wpc = nwarps / m;                 // warps per column
+        const int c = warp / wpc;                   // this warp's column (c >= m: a spare warp)
+        const int wi = warp - c * wpc;
+        const bool mine = c < m;
+        const int jc = j + (mine ? c : 0);
         double *est = sm.est + half * (kRowCap / 2);
         double2 *stash = sm.seg_stash + half * (kSegCap / 2);
+        const long long ga = d.nar_ptr[j];
+        const int grow0 = d.nar_ptr[j + m] > ga ? d.nar_seg[ga].z : 0;
+        if (threadIdx.x == 0) sh.gnumeric = sh.gwarn = sh.gnonzero = sh.gchanged = 0;
         // the step's operands early, off the critical path
+        const bool stepper = mine && wi == 0 && lane == 0;
         double bj = 0.0, tj = 0.0, yj = 0.0;
-        if (threadIdx.x == 0) {
-            bj = beta[j];
-            tj = trust[j];
-            yj = d.ytx[j];
-        }
-        const long long a = d.nar_ptr[j];
-        const int nseg = static_cast<int>(d.nar_ptr[j + 1] - a);
-        const int row0 = nseg > 0 ? d.nar_seg[a].z : 0;
-        // threads without a segment of this column fetch the next column's static data
-        if (j + 1 < j1) {
-            const int busy = nseg < static_cast<int>(blockDim.x) ? (nseg + 31) & ~31 : static_cast<int>(blockDim.x);
-            if (busy < static_cast<int>(blockDim.x) && threadIdx.x >= busy)
-                prefetch_narrow(d, j + 1, threadIdx.x - busy, blockDim.x - busy);
-            else if (busy == static_cast<int>(blockDim.x) && threadIdx.x == 0)
-                prefetch_narrow(d, j + 1, 0, 1);
+        if (stepper) {
+            bj = beta[jc];
+            tj = trust[jc];
+            yj = d.ytx[jc];
         }
         double G = 0.0, H = 0.0;
         bool bad = false, first = true;
-        for (int q = threadIdx.x; q < nseg; q += blockDim.x) {
-            const int4 sg = d.nar_seg[a + q];
-            const double Dv = d.D[sg.x];      // issued ahead of the row gathers
-            const int nv = d.nev[sg.x];
-            double num;
-            const double2 st = gathered ? stash[q] : make_double2(0.0, 0.0);
-            if (gathered && (db_prev == 0.0 || __double_as_longlong(Dv) == __double_as_longlong(st.y))) {
-                num = st.x;                   // the subject's state is as gathered
-            } else {
-                num = 0.0;
-                for (int t = 0; t < sg.y; ++t) {
-                    const double e = d.E[d.nar_row[sg.z + t]];
-                    est[sg.z - row0 + t] = e;
-                    num += e;
+        long long a = 0;
+        int nseg = 0, so = 0;
+        if (mine) {
+            a = d.nar_ptr[jc];
+            nseg = static_cast<int>(d.nar_ptr[jc + 1] - a);
+            so = static_cast<int>(a - ga);          // the column's first slot in the group's buffers
+            for (int q = wi * 32 + lane; q < nseg; q += wpc * 32) {
+                const int4 sg = d.nar_seg[a + q];
+                const double Dv = d.D[sg.x];      // issued ahead of the row gathers
+                const int nv = d.nev[sg.x];
+                const double2 st = gathered ? stash[so + q] : make_double2(0.0, 0.0);
+                double num;
+                if (gathered && (!changed || __double_as_longlong(Dv) == __double_as_longlong(st.y))) {
+                    num = st.x;                   // the subject's state is as gathered
+                } else {
+                    num = 0.0;
+                    for (int t = 0; t < sg.y; ++t) {
+                        const double e = d.E[d.nar_row[sg.z + t]];
+                        est[sg.z - grow0 + t] = e;
+                        num += e;
+                    }
                 }
-            }
-            double gl = 0.0, hl = 0.0;
-            segment_terms(num, Dv, nv, gl, hl, bad);
-            stash[q] = make_double2(num, Dv);
-            if (first) {
-                G = gl;
-                H = hl;
-                first = false;
-            } else {
-                G += gl;
-                H += hl;
+                double gl = 0.0, hl = 0.0;
+                segment_terms(num, Dv, nv, gl, hl, bad);
+                stash[so + q] = make_double2(num, Dv);
+                if (first) {
+                    G = gl;
+                    H = hl;
+                    first = false;
+                } else {
+                    G += gl;
+                    H += hl;
+                }
             }
         }
         const Fx fa = fx_warp_sum(fx_from_double(G, bad));
@@ -1239,56 +1232,72 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
             sh.wbad[warp] = wbad;
         }
         __syncthreads();
-        if (warp == 0) {
-            Fx ta = lane < nwarps ? sh.wa[lane] : fx_zero();
-            Fx tbx = lane < nwarps ? sh.wb[lane] : fx_zero();
-            const bool cbad = __any_sync(kFull, lane < nwarps ? sh.wbad[lane] != 0 : false);
+        if (mine && wi == 0) {
+            // the column's sums over its warps, then its step
+            Fx ta = lane < wpc ? sh.wa[c * wpc + lane] : fx_zero();
+            Fx tbx = lane < wpc ? sh.wb[c * wpc + lane] : fx_zero();
+            const bool cbad = __any_sync(kFull, lane < wpc ? sh.wbad[c * wpc + lane] != 0 : false);
             ta = fx_warp_sum(ta);
             tbx = fx_warp_sum(tbx);
             if (lane == 0) {
                 double ca = fx_to_double(ta), cb = fx_to_double(tbx);
                 if (cbad) ca = cb = __longlong_as_double(0x7ff8000000000000ll);
                 const double g = yj - ca, q = cb;
-                double db = newton_step(g, q, bj, p, tj, warn), r = 1.0, em1 = 0.0;
+                int wl = 0;
+                double db = newton_step(g, q, bj, p, tj, wl), r = 1.0, em1 = 0.0;
                 if (nonfinite_bits(db) || nan_bits(g) || nan_bits(q)) {
                     db = 0.0;
-                    status = kStNumeric;
+                    atomicExch(&sh.gnumeric, 1);
                 } else if (db != 0.0) {
                     r = exp_step(db);
                     em1 = r - 1.0;
-                    ++nonzero;
+                    atomicAdd(&sh.gnonzero, 1);
+                    atomicExch(&sh.gchanged, 1);
                 }
-                sh.db = db;
-                sh.r = r;
-                sh.em1 = em1;
-                sh.nbj = bj + db;
+                if (wl) atomicOr(&sh.gwarn, wl);
+                sh.gdb[c] = db;
+                sh.gr[c] = r;
+                sh.gem1[c] = em1;
+                sh.gnbj[c] = bj + db;
+                sh.gtrust[c] = fmax(2.0 * fabs(db), 0.5 * tj);
             }
-        } else if (j + 1 < j1) {
-            // while warp 0 takes the step: gather the next column into the other half
+        } else if (j + m < j1) {
+            // the other warps: gather the next group into the other half of the buffers
+            const int fw = mine ? warp - (c + 1) : warp - m;
             const int nh = half ^ 1;
-            narrow_gather(d, j + 1, threadIdx.x - 32, blockDim.x - 32, sm.est + nh * (kRowCap / 2),
-                          sm.seg_stash + nh * (kSegCap / 2));
+            narrow_gather(d, j + m, d.nar_group[j + m] > 0 ? d.nar_group[j + m] : 1, fw * 32 + lane,
+                          (nwarps - m) * 32, sm.est + nh * (kRowCap / 2), sm.seg_stash + nh * (kSegCap / 2));
         }
         __syncthreads();
-        const double db = sh.db;
-        if (threadIdx.x == 0) {      // bookkeeping, off the critical path
-            beta[j] = sh.nbj;
-            trust[j] = fmax(2.0 * fabs(db), 0.5 * tj);
+        if (threadIdx.x == 0) {
+            if (sh.gnumeric) status = kStNumeric;
+            warn |= sh.gwarn;
+            nonzero += sh.gnonzero;
         }
-        if (db != 0.0) {
-            const double r = sh.r, em1 = sh.em1;
-            for (int q = threadIdx.x; q < nseg; q += blockDim.x) {
-                const int4 sg = d.nar_seg[a + q];
-                for (int t = 0; t < sg.y; ++t) d.E[d.nar_row[sg.z + t]] = est[sg.z - row0 + t] * r;
-                const double2 st = stash[q];
-                d.D[sg.x] = fma(em1, st.x, st.y);
+        if (mine) {
+            const double db = sh.gdb[c];
+            if (db != 0.0) {
+                const double r = sh.gr[c], em1 = sh.gem1[c];
+                for (int q = wi * 32 + lane; q < nseg; q += wpc * 32) {
+                    const int4 sg = d.nar_seg[a + q];
+                    for (int t = 0; t < sg.y; ++t) d.E[d.nar_row[sg.z + t]] = est[sg.z - grow0 + t] * r;
+                    const double2 st = stash[so + q];
+                    d.D[sg.x] = fma(em1, st.x, st.y);
+                }
             }
+            // bookkeeping, and every shard's copy of beta_jc
+            const double nb = sh.gnbj[c];
+            if (wi == 0 && lane == 0) {
+                beta[jc] = nb;
+                trust[jc] = sh.gtrust[c];
+            }
+            for (int t = wi * 32 + lane + 1; t < d.S; t += wpc * 32) d.beta_priv[static_cast<long long>(t) * d.J + jc] = nb;
         }
-        const double nbj = sh.nbj;
-        for (int t = threadIdx.x + 1; t < d.S; t += blockDim.x) d.beta_priv[static_cast<long long>(t) * d.J + j] = nbj;
-        gathered = true;
-        db_prev = db;
-        __syncthreads();   // E and D as updated are what the next column reads
+        changed = sh.gchanged != 0;
+        gathered = j + m < j1;
+        half ^= 1;
+        j += m;
+        __syncthreads();   // E and D as updated are what the next group reads
     }
 }
 

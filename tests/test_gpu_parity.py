@@ -377,13 +377,14 @@ def test_narrow_columns_match_wide_path_and_oracle(P, prior, var):
     orc = oracle.Problem.from_data(d)
     ref = orc.fit(prior=prior, variance=var, fixed_cycles=4)
     out = {}
-    for thr in (-1, 1000, 0):
-        with gpu_model(P, d, num_shards=16, narrow_max_nnz=thr) as m:
+    for thr, gmax in ((-1, 0), (1000, 1), (1000, 0), (0, 0)):
+        with gpu_model(P, d, num_shards=16, narrow_max_nnz=thr, narrow_group_max=gmax) as m:
             info = m.info
             m.set_prior(prior, var)
-            out[thr] = (m.fit(tol=-1.0, max_cycles=4, history=True), info["narrow_columns"])
+            out[thr if gmax == 0 else (thr, gmax)] = (m.fit(tol=-1.0, max_cycles=4, history=True),
+                                                      info["narrow_columns"])
     assert out[-1][1] == 0 and 0 < out[1000][1] <= out[0][1] <= sizes.size
-    for thr in (-1, 1000, 0):
+    for thr in (-1, 1000, 0, (1000, 1)):
         r = out[thr][0]
         np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11, rtol=0)
         np.testing.assert_allclose(r["history"], ref["history"], rtol=1e-12)
@@ -484,3 +485,22 @@ def test_paper_scale_sampled_against_oracle(P):
     np.testing.assert_array_less(np.abs(g[nzs] - lam * np.sign(b[nzs])), 1e-6 * scale[nzs])
     np.testing.assert_array_less(np.abs(g[~nzs]), lam + 1e-6 * scale[~nzs])
     assert nzs.sum() >= 3
+
+
+def test_narrow_groups_of_independent_columns(P):
+    """Many small narrow columns over many subjects: most neighbours touch disjoint subjects and
+    share a group; the grouped fit equals the one-at-a-time narrow fit and the oracle."""
+    d = make_dataset(n_patients=200000, eras=("geometric", 5), J=60, columns=("sizes", np.full(60, 40)),
+                     n_true=6, beta_sd=0.5, seed=33)
+    orc = oracle.Problem.from_data(d)
+    ref = orc.fit(prior="normal", variance=0.4, fixed_cycles=3)
+    res = []
+    for gmax in (1, 0, 3):
+        with gpu_model(P, d, num_shards=32, narrow_group_max=gmax) as m:
+            assert m.info["narrow_columns"] == d.J
+            m.set_prior("normal", 0.4)
+            res.append(m.fit(tol=-1.0, max_cycles=3, history=True))
+    for r in res:
+        np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11, rtol=0)
+        np.testing.assert_allclose(r["history"], ref["history"], rtol=1e-12)
+        assert r["nonzero_steps"] == res[0]["nonzero_steps"]
