@@ -327,6 +327,14 @@ int sccs_server_destroy(sccs_server *srv);
 int sccs_selftest_exp(int32_t device, const double *x, int64_t n, double *ours, double *ref);
 
 /*
+ * sccs_selftest_div -- diagnostic for tests: the library's quotient a/b, used for W_i = num_i/D_i
+ * (Eq. 8) and the Newton step (Eq. 4) in every coordinate step, and CUDA's IEEE division on the
+ * same n pairs (a, b, ours, ref: host arrays of n doubles; the library copies them).  Errors:
+ * SCCS_E_INVAL (n < 0 or null arrays with n > 0), SCCS_E_NOMEM, SCCS_E_CUDA.
+ */
+int sccs_selftest_div(int32_t device, const double *a, const double *b, int64_t n, double *ours, double *ref);
+
+/*
  * sccs_check_wait_timeout -- self-test of the bounded device-side waits (failure detection).
  * Launches the gradient kernel on one CTA fewer than the all-reduce counts, so the last
  * partial is never written and every launched CTA's wait must run out after timeout_ms

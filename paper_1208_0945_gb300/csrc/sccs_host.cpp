@@ -208,7 +208,7 @@ struct HostLayout {
     std::vector<uint8_t> narrow;      // J
     std::vector<int32_t> next_wide;   // J
     std::vector<int64_t> nar_ptr;     // J+1
-    std::vector<int4> nar_seg;        // {subject, rows, first row in nar_row, 0}
+    std::vector<int4> nar_seg;        // {subject, rows, first row in nar_row, the step it waits on}
     std::vector<int32_t> nar_row;
     std::vector<int32_t> nar_group;   // J: at a group's first column, its number of columns; else 0
     int32_t narrow_groups = 0;
@@ -462,6 +462,35 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             hl.nar_group[j] = m;
             hl.narrow_groups++;
             j += m;
+        }
+        // A group's state is gathered before the step ahead of it has written E and D: the run's
+        // first group while the wide column before the run is still being applied on the other
+        // shards, a later group while the previous group steps.  Each segment records the one
+        // step that can change its subject: w = c + 1 if the subject is in column c of the
+        // previous group, kNarrowAfterWide if the run's preceding wide column touches it, else 0.
+        // The kernel gathers a segment again when that step was not zero.
+        std::vector<int64_t> tag(static_cast<size_t>(std::max<int64_t>(hl.N, 1)), -1);
+        int64_t pass = 0;
+        for (int32_t g = 0; g < J;) {
+            if (!hl.narrow[g]) {
+                ++g;
+                continue;
+            }
+            const int32_t m = hl.nar_group[g];
+            const bool run_start = g == 0 || !hl.narrow[g - 1];
+            if (run_start) {
+                ++pass;
+                if (g > 0)
+                    for (int64_t e = cptr[g - 1]; e < cptr[g]; ++e) tag[row_pat[crow[e]]] = pass * 16 + 15;
+            }
+            for (int64_t q = hl.nar_ptr[g]; q < hl.nar_ptr[g + m]; ++q) {
+                const int64_t t = tag[hl.nar_seg[q].x];
+                hl.nar_seg[q].w = t >= 0 && t / 16 == pass ? (t % 16 == 15 ? sccs::kNarrowAfterWide : static_cast<int>(t % 16) + 1) : 0;
+            }
+            ++pass;
+            for (int32_t c = 0; c < m; ++c)
+                for (int64_t q = hl.nar_ptr[g + c]; q < hl.nar_ptr[g + c + 1]; ++q) tag[hl.nar_seg[q].x] = pass * 16 + c;
+            g += m;
         }
     }
     for (int32_t j = 0; j < J; ++j)
@@ -1565,6 +1594,29 @@ int sccs_selftest_exp(int32_t device, const double *x, int64_t n, double *ours, 
     cudaFree(buf);
     if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "exp self-test");
     if (e != cudaSuccess) return cuda_fail(e, "exp self-test copies");
+    return SCCS_OK;
+}
+
+int sccs_selftest_div(int32_t device, const double *a, const double *b, int64_t n, double *ours, double *ref) {
+    if (n < 0 || (n > 0 && (!a || !b || !ours || !ref))) return fail(SCCS_E_INVAL, "bad arguments");
+    if (n == 0) return SCCS_OK;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    double *buf = nullptr;
+    const size_t bytes = sizeof(double) * static_cast<size_t>(n);
+    if (cudaMalloc(&buf, 4 * bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(SCCS_E_NOMEM, "device buffers");
+    }
+    e = cudaMemcpy(buf, a, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(buf + n, b, bytes, cudaMemcpyHostToDevice);
+    int le = e == cudaSuccess ? sccs::launch_div_selftest(buf, buf + n, n, buf + 2 * n, buf + 3 * n, nullptr)
+                              : static_cast<int>(e);
+    if (le == 0) e = cudaMemcpy(ours, buf + 2 * n, bytes, cudaMemcpyDeviceToHost);
+    if (le == 0 && e == cudaSuccess) e = cudaMemcpy(ref, buf + 3 * n, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "division self-test");
+    if (e != cudaSuccess) return cuda_fail(e, "division self-test copies");
     return SCCS_OK;
 }
 

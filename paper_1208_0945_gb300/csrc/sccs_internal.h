@@ -30,6 +30,7 @@ constexpr int kSegCap = 2048;              // segments per staged slice
 constexpr int kRowCap = 4096;              // nonzeros per staged slice
 constexpr int kGrpCap = kSegCap / 32;      // groups per staged slice
 constexpr int kNarrowGroupMax = 8;         // narrow columns whose steps are taken side by side
+constexpr int kNarrowAfterWide = kNarrowGroupMax + 1;  // segment mark: waits on the wide column before the run
 // Global arrays read by bulk copies are padded by this many bytes past their end, so a copy
 // rounded out to 16-byte boundaries stays inside the allocation.
 constexpr int kCopyPad = 32;
@@ -149,6 +150,7 @@ int launch_build_row_index(const DevLayout &d, int64_t *row_ptr, int32_t *row_co
 size_t row_index_scan_blocks(int64_t K);
 // Diagnostic: the coordinate step's e^x and CUDA's exp on n device values.
 int launch_exp_selftest(const double *x, long long n, double *ours, double *ref, void *stream);
+int launch_div_selftest(const double *a, const double *b, long long n, double *ours, double *ref, void *stream);
 // Weighted counts of a fit with subject weights w_kept (device [N]): nev_w[i] = w_i n_i and
 // ytx_w[j] = sum over X_j's (subject, y) pairs of w_i y, both exact (integer sums).
 int launch_weighted_counts(const DevLayout &d, const int32_t *w_kept, int32_t *nev_w, double *ytx_w, void *stream);

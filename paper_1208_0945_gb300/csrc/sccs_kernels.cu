@@ -281,7 +281,7 @@ struct SharedState {
     // a group of narrow columns: per column step results, and the group's flags
     double gdb[kNarrowGroupMax], gr[kNarrowGroupMax], gem1[kNarrowGroupMax], gnbj[kNarrowGroupMax],
         gtrust[kNarrowGroupMax];
-    int gnumeric, gwarn, gnonzero, gchanged;
+    int gnumeric, gwarn, gnonzero;
     double G, H;
     double lin, sq, ab;     // cycle sums of b_j Y'X_j, b_j^2, |b_j| (from the bookkeeping thread)
     long long nonzero;
@@ -294,10 +294,30 @@ struct SharedState {
     unsigned long long run_seq;   // the all-reduce sequence number it ended at
 };
 
-struct SmemLayout {
-    StageBuf stage[2];
+// One narrow group's gathered data (half of the narrow buffers).
+struct NarrowBuf {
+    double est[kRowCap / 2];             // E per row
+    double2 stash[kSegCap / 2];          // (numerator, D) per segment
+    int4 info[kSegCap / 2];              // {subject, rows | mark << 16, first row, n_i} per segment
+    int rows[kRowCap / 2];               // index into E per row
+    int m;                               // columns in the group
+    int col_off[kNarrowGroupMax + 1];    // each column's first segment
+};
+
+// A wide column's gathered state between its phases A and C.
+struct WideBuf {
     double est[kRowCap];             // E gathered in phase A, per row position
     double2 seg_stash[kSegCap];      // (num, D) per segment
+};
+
+// Wide columns and narrow runs never hold gathered state at the same time (CTA 0 finishes a
+// wide column's phase C before a narrow run starts, and the run before the next phase A).
+struct SmemLayout {
+    StageBuf stage[2];
+    union {
+        WideBuf wide;
+        NarrowBuf nar[2];            // narrow groups: the stepping one and the next
+    };
 };
 
 // ------------------------------------------------------------------ grid all-reduce
@@ -415,6 +435,57 @@ __device__ bool block_grid_reduce(const DevLayout &d, int me, unsigned long long
 
 // ------------------------------------------------------------------ the coordinate step
 
+// FP64 issues at 1/64 of the FP32 rate on this part (a warp's FP64 instruction holds its SM
+// partition's unit for about 64 clocks, however many lanes are active), so the helpers below
+// keep FP64 instructions off the coordinate path where integer or FP32 work can stand in.
+
+__device__ __forceinline__ bool nan_bits_u(unsigned long long b) { return (b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull; }
+
+// a / b: a reciprocal seed from FP32 (b's leading 24 bits, the hardware's approximate
+// reciprocal), one Newton-Raphson refinement of the reciprocal and one correction of the
+// quotient, both by FMA (P. Markstein, IBM J. Res. Dev. 34(1), 1990).  Five FP64 operations;
+// the seed's error (about 2^-22) squares to about 2^-44 in the reciprocal, and the correction
+// leaves the quotient within an ulp (faithful; the correctly rounded one in practice).  |b|
+// outside [2^-120, 2^121), |a| outside [2^-900, 2^901), zeros, infinities and NaNs take the
+// IEEE division.
+__device__ __forceinline__ double quot(double a, double b) {
+    const unsigned long long ab = static_cast<unsigned long long>(__double_as_longlong(a));
+    const unsigned long long bb = static_cast<unsigned long long>(__double_as_longlong(b));
+    const unsigned ea = static_cast<unsigned>((ab >> 52) & 0x7ff), eb = static_cast<unsigned>((bb >> 52) & 0x7ff);
+    if (eb - (1023u - 120u) > 240u || ea - (1023u - 900u) > 1800u) return a / b;
+    const float bf = __int_as_float(static_cast<int>(((eb - 896u) << 23) | static_cast<unsigned>((bb >> 29) & 0x7fffff)));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(bf));
+    const unsigned rb = static_cast<unsigned>(__float_as_int(rf));
+    const double y0 = __longlong_as_double(static_cast<long long>(
+        (static_cast<unsigned long long>(((rb >> 23) & 0xffu) + 896u) << 52) |
+        (static_cast<unsigned long long>(rb & 0x7fffffu) << 29) | (bb & 0x8000000000000000ull)));
+    const double e = fma(-b, y0, 1.0);
+    const double y1 = fma(y0, e, y0);
+    const double q0 = a * y1;
+    const double r = fma(-b, q0, a);
+    return fma(r, y1, q0);
+}
+
+// An unsigned 32-bit integer as a double, assembled from its bits (exact).
+__device__ __forceinline__ double u32_to_double(unsigned v) {
+    if (v == 0u) return 0.0;
+    const int e = 31 - __clz(v);
+    return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(1023 + e) << 52) |
+                                                       ((static_cast<unsigned long long>(v) << (52 - e)) & 0xfffffffffffffull)));
+}
+
+// The Genkin trust radius after a step: max(2 |db|, t / 2) (t > 0), exact, by bit patterns;
+// radii within a factor 2 of the subnormal range take the FP64 expression.
+__device__ __forceinline__ double trust_update(double db, double t) {
+    const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(db)) & 0x7fffffffffffffffull;
+    const unsigned long long tb = static_cast<unsigned long long>(__double_as_longlong(t));
+    if ((tb >> 52) - 2ull > 0x7fcull || (a >> 52) >= 0x7feull) return fmax(2.0 * fabs(db), 0.5 * t);
+    const unsigned long long a2 = a == 0ull ? 0ull : ((a >> 52) == 0ull ? (a << 1) : a + (1ull << 52));
+    const unsigned long long t2 = tb - (1ull << 52);
+    return __longlong_as_double(static_cast<long long>(a2 > t2 ? a2 : t2));
+}
+
 // Newton step of Eq. 4 under the prior of Eq. 3, clamped to the Genkin trust region (one
 // lane).  q = -h >= 0.  Laplace: soft threshold at 0, and a step that would change the sign
 // of a nonzero b stops at 0.  q = 0 with no finite minimiser takes the trust bound and
@@ -422,16 +493,16 @@ __device__ bool block_grid_reduce(const DevLayout &d, int me, unsigned long long
 __device__ double newton_step(double g, double q, double b, const FitParams &p, double trust, int &warn) {
     double dv;
     if (p.prior == 1) {
-        dv = fma(-b, p.inv_var, g) / (q + p.inv_var);
+        dv = quot(fma(-b, p.inv_var, g), q + p.inv_var);
     } else if (p.prior == 2) {
         const double lambda = p.lambda;
         if (q > 0.0) {
             if (b == 0.0) {
                 const double gu = g - lambda, gd = g + lambda;
-                dv = gu > 0.0 ? gu / q : (gd < 0.0 ? gd / q : 0.0);
+                dv = gu > 0.0 ? quot(gu, q) : (gd < 0.0 ? quot(gd, q) : 0.0);
             } else {
                 const double s = b > 0.0 ? 1.0 : -1.0;
-                dv = (g - lambda * s) / q;
+                dv = quot(g - lambda * s, q);
                 const double nb = b + dv;
                 const double ns = nb > 0.0 ? 1.0 : (nb < 0.0 ? -1.0 : 0.0);
                 if (ns != s) dv = -b;
@@ -458,7 +529,7 @@ __device__ double newton_step(double g, double q, double b, const FitParams &p, 
         }
     } else {
         if (q > 0.0) {
-            dv = g / q;
+            dv = quot(g, q);
         } else if (g != 0.0) {
             dv = g > 0.0 ? trust : -trust;
             warn |= 1;
@@ -466,15 +537,23 @@ __device__ double newton_step(double g, double q, double b, const FitParams &p, 
             dv = 0.0;
         }
     }
-    return fmin(fmax(dv, -trust), trust);
+    // clamp to [-trust, trust] by bit patterns (trust >= 0; NaN goes to -trust, as fmin/fmax do)
+    const unsigned long long db = static_cast<unsigned long long>(__double_as_longlong(dv));
+    const unsigned long long tb = static_cast<unsigned long long>(__double_as_longlong(trust));
+    if ((db & 0x7fffffffffffffffull) > tb)
+        dv = __longlong_as_double(static_cast<long long>(tb | (nan_bits_u(db) ? 0x8000000000000000ull : (db & 0x8000000000000000ull))));
+    return dv;
 }
 
-// ---- e^x for the coordinate step (on every coordinate's critical path, where FP64 issues at
-// 1/64 of the FP32 rate): Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989).
+// ---- e^x and e^x - 1 for the coordinate step (on every coordinate's critical path).
+// |x| < 2^-10: e^x - 1 from its Taylor series to x^5 (the next term is below 2^-59 relative),
+// e^x = 1 + that.  Otherwise Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989):
 // x = (32 m + j) ln2/32 + r with |r| <= ln2/64, e^x = 2^m 2^(j/32) e^r, e^r - 1 from its Taylor
-// series to r^6 (the next term is below 2^-60 relative).  Table: 2^(j/32) rounded to the nearest
-// double (from the exponential series at 60 digits); ln2/32 split so that n ln2/32 is exact in
-// two parts for |n| < 2^15.  |x| >= 700 (and NaN) go to exp().
+// series to r^6 (the next term is below 2^-60 relative).  n = 32 m + j is x 32/ln2 rounded to
+// the nearest integer by adding 1.5 2^52 in one FMA (the sum's low word holds n); 2^m goes into
+// the table value's exponent field.  Table: 2^(j/32) rounded to the nearest double (from the
+// exponential series at 60 digits); ln2/32 split so that n ln2/32 is exact in two parts for
+// |n| < 2^15.  |x| >= 700 (and NaN) go to exp().
 __constant__ double c_exp2_j32[32] = {
     0x1.0000000000000p+0, 0x1.059b0d3158574p+0, 0x1.0b5586cf9890fp+0, 0x1.11301d0125b51p+0,
     0x1.172b83c7d517bp+0, 0x1.1d4873168b9aap+0, 0x1.2387a6e756238p+0, 0x1.29e9df51fdee1p+0,
@@ -485,22 +564,41 @@ __constant__ double c_exp2_j32[32] = {
     0x1.ae89f995ad3adp+0, 0x1.b7f76f2fb5e47p+0, 0x1.c199bdd85529cp+0, 0x1.cb720dcef9069p+0,
     0x1.d5818dcfba487p+0, 0x1.dfc97337b9b5fp+0, 0x1.ea4afa2a490dap+0, 0x1.f50765b6e4540p+0};
 
-__device__ __forceinline__ double exp_step(double x) {
-    if (!(fabs(x) < 700.0)) return exp(x);
+struct ExpStep {
+    double r;     // e^x
+    double em1;   // e^x - 1
+};
+
+__device__ __forceinline__ ExpStep exp_step(double x) {
+    const unsigned long long ax = static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+    if (ax < 0x3f50000000000000ull) {                // |x| < 2^-10
+        double p = fma(x, 1.0 / 120.0, 1.0 / 24.0);
+        p = fma(x, p, 1.0 / 6.0);
+        p = fma(x, p, 0.5);
+        const double em1 = fma(x * x, p, x);
+        return ExpStep{1.0 + em1, em1};
+    }
+    if (ax >= 0x4085e00000000000ull) {               // |x| >= 700, inf, NaN
+        const double r = exp(x);
+        return ExpStep{r, r - 1.0};
+    }
     constexpr double kInvL = 0x1.71547652b82fep+5;   // 32 / ln 2
     constexpr double kL1 = 0x1.62e42fefa0000p-6;     // ln2/32, high 38 bits
     constexpr double kL2 = 0x1.cf79abc9e3b3ap-45;    // ln2/32 - kL1
-    const double n = rint(x * kInvL);
+    constexpr double kShift = 0x1.8p52;
+    const double sh = fma(x, kInvL, kShift);
+    const int ni = static_cast<int>(__double2loint(sh));
+    const double n = sh - kShift;
     const double r = fma(-n, kL2, fma(-n, kL1, x));
-    const int ni = static_cast<int>(n);
-    const int jj = ni & 31, m = (ni - jj) / 32;
+    const int jj = ni & 31, m = ni >> 5;             // n = 32 m + jj (arithmetic shift: floor)
     double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
     q = fma(r, q, 1.0 / 24.0);
     q = fma(r, q, 1.0 / 6.0);
     q = fma(r, q, 0.5);
     const double em1r = fma(r * r, q, r);            // e^r - 1
-    const double t = c_exp2_j32[jj];
-    return fma(t, em1r, t) * __longlong_as_double(static_cast<long long>(m + 1023) << 52);
+    const double t = __longlong_as_double(__double_as_longlong(c_exp2_j32[jj]) + (static_cast<long long>(m) << 52));
+    const double e = fma(t, em1r, t);
+    return ExpStep{e, e - 1.0};
 }
 
 // Classifications by bit pattern (integer ops; an FP64 compare costs as much as an FP64 add).
@@ -517,10 +615,10 @@ __device__ __forceinline__ void segment_terms(double num, double Dv, int nv, dou
     const unsigned long long bd = static_cast<unsigned long long>(__double_as_longlong(Dv));
     const unsigned long long bn = static_cast<unsigned long long>(__double_as_longlong(num));
     if (bd == 0ull || bd >= 0x7ff0000000000000ull || bn >= 0x7ff0000000000000ull) bad = true;
-    double w = num / Dv;
+    double w = quot(num, Dv);
     if (static_cast<unsigned long long>(__double_as_longlong(w)) > 0x3ff0000000000000ull) w = 1.0;
-    gl = static_cast<double>(nv) * w;
-    hl = gl * (1.0 - w);
+    gl = u32_to_double(static_cast<unsigned>(nv)) * w;
+    hl = fma(-gl, w, gl);                             // gl (1 - w), one rounding
 }
 
 // ------------------------------------------------------------------ column phases
@@ -563,7 +661,7 @@ __device__ void phase_a_staged(const DevLayout &d, const ColDesc &cd, const Stag
                 if (t0 + u < maxlen) {       // warp-uniform: skip the FP64 add on empty diagonals
                     if (k[u] >= 0) {
                         num += e[u];
-                        sm.est[pos[u]] = e[u];
+                        sm.wide.est[pos[u]] = e[u];
                     }
                 }
             }
@@ -571,7 +669,7 @@ __device__ void phase_a_staged(const DevLayout &d, const ColDesc &cd, const Stag
         double gl = 0.0, hl = 0.0;
         if (valid) {
             segment_terms(num, Dv, nv, gl, hl, bad);
-            sm.seg_stash[si] = make_double2(num, Dv);
+            sm.wide.seg_stash[si] = make_double2(num, Dv);
         }
         if (first) {
             G = gl;
@@ -656,9 +754,9 @@ __device__ void phase_c_staged(const DevLayout &d, const ColDesc &cd, const Stag
                                double r, double em1) {
     const int2 *sseg = sb.segs + cd.seg_off;
     const int32_t *srow = sb.rows + cd.row_off;
-    for (int p = threadIdx.x; p < cd.nnz; p += blockDim.x) d.E[srow[p]] = sm.est[p] * r;
+    for (int p = threadIdx.x; p < cd.nnz; p += blockDim.x) d.E[srow[p]] = sm.wide.est[p] * r;
     for (int si = threadIdx.x; si < cd.nseg; si += blockDim.x) {
-        const double2 st = sm.seg_stash[si];
+        const double2 st = sm.wide.seg_stash[si];
         d.D[sseg[si].x] = fma(em1, st.x, st.y);
     }
 }
@@ -770,8 +868,8 @@ __device__ void phase_a_staged32(const DevLayout &d, const ColDesc &cd, const St
     const int2 *sseg = sb.segs + cd.seg_off;
     const int32_t *srow = sb.rows + cd.row_off;
     const long long *sgrp = sb.grp + cd.grp_off;
-    float *est = reinterpret_cast<float *>(sm.est);
-    float4 *stash = reinterpret_cast<float4 *>(sm.seg_stash);
+    float *est = reinterpret_cast<float *>(sm.wide.est);
+    float4 *stash = reinterpret_cast<float4 *>(sm.wide.seg_stash);
     for (int g = warp; g < cd.ngrp; g += nwarps) {
         const int si = 32 * g + lane;
         const bool valid = si < cd.nseg;
@@ -870,8 +968,8 @@ __device__ void phase_c_staged32(const DevLayout &d, const ColDesc &cd, const St
                                  float r, float em1) {
     const int2 *sseg = sb.segs + cd.seg_off;
     const int32_t *srow = sb.rows + cd.row_off;
-    const float *est = reinterpret_cast<const float *>(sm.est);
-    const float4 *stash = reinterpret_cast<const float4 *>(sm.seg_stash);
+    const float *est = reinterpret_cast<const float *>(sm.wide.est);
+    const float4 *stash = reinterpret_cast<const float4 *>(sm.wide.seg_stash);
     for (int p = threadIdx.x; p < cd.nnz; p += blockDim.x) d.E32[srow[p]] = est[p] * r;
     for (int si = threadIdx.x; si < cd.nseg; si += blockDim.x) {
         const float4 st = stash[si];
@@ -1092,7 +1190,7 @@ __device__ __forceinline__ void bookkeep(double *beta, double *trust, int j, dou
                                          double &lin, double &sq, double &ab, long long &nonzero) {
     const double nbj = b + db;
     beta[j] = nbj;
-    trust[j] = fmax(2.0 * fabs(db), 0.5 * t);
+    trust[j] = trust_update(db, t);
     lin = fma(nbj, y, lin);
     sq = fma(nbj, nbj, sq);
     ab += fabs(nbj);
@@ -1138,24 +1236,36 @@ __device__ __forceinline__ void prefetch_slice_state_l2(const DevLayout &d, int 
 // written too.  Thread 0 carries status, warn, nonzero.
 //
 // Pipelined: while the groups' first warps take the steps, the other warps gather the next group
-// (numerators, D, the E values of its rows) into the other half of the shared buffers.  After
-// this group's updates each subject of the next group re-reads D_i: a subject whose rows this
-// group changed has a changed D_i and is gathered again; the W terms are formed then.
-__device__ void narrow_gather(const DevLayout &d, int j, int m, int t, int nthr, double *est, double2 *stash) {
+// into the other half of the shared buffers: its size and column offsets, per segment the
+// subject, rows, mark and n_i, per row its index into E, and the state (E per row; numerator
+// and D per segment).  The run's first group is gathered while CTA 0 waits for the other CTAs.
+// A gathered segment is used as it is unless the one step that can have changed its subject
+// since (its mark, set on the host: a column of the previous group, or the wide column before
+// the run) was not zero; then its state is gathered again.  The W terms are formed after that.
+__device__ void narrow_gather(const DevLayout &d, int j, int t, int nthr, NarrowBuf &nb) {
+    const int m = d.nar_group[j] > 0 ? d.nar_group[j] : 1;
     const long long ga = d.nar_ptr[j], gb = d.nar_ptr[j + m];
     const int nseg = static_cast<int>(gb - ga);
     const int row0 = nseg > 0 ? d.nar_seg[ga].z : 0;
+    if (t <= m) {
+        if (t == 0) nb.m = m;
+        nb.col_off[t] = static_cast<int>(d.nar_ptr[j + t] - ga);
+    }
     for (int q = t; q < nseg; q += nthr) {
         const int4 sg = d.nar_seg[ga + q];
         const double Dv = d.D[sg.x];
-        prefetch_l1(d.nev + sg.x);          // static: read after the steps, when the terms are formed
+        const int nv = d.nev[sg.x];
+        const int r0 = sg.z - row0;
         double num = 0.0;
         for (int u = 0; u < sg.y; ++u) {
-            const double e = d.E[d.nar_row[sg.z + u]];
-            est[sg.z - row0 + u] = e;
+            const int row = d.nar_row[sg.z + u];
+            const double e = d.E[row];
+            nb.rows[r0 + u] = row;
+            nb.est[r0 + u] = e;
             num += e;
         }
-        stash[q] = make_double2(num, Dv);
+        nb.stash[q] = make_double2(num, Dv);
+        nb.info[q] = make_int4(sg.x, sg.y | (sg.w << 16), r0, nv);
     }
 }
 
@@ -1163,21 +1273,16 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
                                SharedState &sh, double *beta, double *trust, int &status, int &warn,
                                long long &nonzero) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    bool gathered = false;     // this group was gathered during the previous group's steps
-    bool changed = true;       // ... and a step since then may have changed its subjects' state
     int half = 0;
     for (int j = j0; j < j1;) {
-        const int m = d.nar_group[j] > 0 ? d.nar_group[j] : 1;
+        NarrowBuf &nb = sm.nar[half];
+        const int m = nb.m;
         const int wpc = nwarps / m;                 // warps per column
         const int c = warp / wpc;                   // this warp's column (c >= m: a spare warp)
         const int wi = warp - c * wpc;
         const bool mine = c < m;
         const int jc = j + (mine ? c : 0);
-        double *est = sm.est + half * (kRowCap / 2);
-        double2 *stash = sm.seg_stash + half * (kSegCap / 2);
-        const long long ga = d.nar_ptr[j];
-        const int grow0 = d.nar_ptr[j + m] > ga ? d.nar_seg[ga].z : 0;
-        if (threadIdx.x == 0) sh.gnumeric = sh.gwarn = sh.gnonzero = sh.gchanged = 0;
+        if (threadIdx.x == 0) sh.gnumeric = sh.gwarn = sh.gnonzero = 0;
         // the step's operands early, off the critical path
         const bool stepper = mine && wi == 0 && lane == 0;
         double bj = 0.0, tj = 0.0, yj = 0.0;
@@ -1188,31 +1293,34 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
         }
         double G = 0.0, H = 0.0;
         bool bad = false, first = true;
-        long long a = 0;
         int nseg = 0, so = 0;
         if (mine) {
-            a = d.nar_ptr[jc];
-            nseg = static_cast<int>(d.nar_ptr[jc + 1] - a);
-            so = static_cast<int>(a - ga);          // the column's first slot in the group's buffers
+            so = nb.col_off[c];                     // the column's first slot in the group's buffers
+            nseg = nb.col_off[c + 1] - so;
             for (int q = wi * 32 + lane; q < nseg; q += wpc * 32) {
-                const int4 sg = d.nar_seg[a + q];
-                const double Dv = d.D[sg.x];      // issued ahead of the row gathers
-                const int nv = d.nev[sg.x];
-                const double2 st = gathered ? stash[so + q] : make_double2(0.0, 0.0);
-                double num;
-                if (gathered && (!changed || __double_as_longlong(Dv) == __double_as_longlong(st.y))) {
-                    num = st.x;                   // the subject's state is as gathered
+                const int4 in = nb.info[so + q];
+                const int mark = in.y >> 16;
+                // the step this segment waits on: a column of the previous group, or the wide
+                // column before the run (sh.db still holds its step)
+                const bool moved = mark != 0 && (mark <= kNarrowGroupMax ? sh.gdb[mark - 1] : sh.db) != 0.0;
+                double num, Dv;
+                if (!moved) {
+                    const double2 st = nb.stash[so + q];   // the subject's state is as gathered
+                    num = st.x;
+                    Dv = st.y;
                 } else {
+                    Dv = d.D[in.x];
                     num = 0.0;
-                    for (int t = 0; t < sg.y; ++t) {
-                        const double e = d.E[d.nar_row[sg.z + t]];
-                        est[sg.z - grow0 + t] = e;
+                    const int len = in.y & 0xffff;
+                    for (int u = 0; u < len; ++u) {
+                        const double e = d.E[nb.rows[in.z + u]];
+                        nb.est[in.z + u] = e;
                         num += e;
                     }
+                    nb.stash[so + q] = make_double2(num, Dv);
                 }
                 double gl = 0.0, hl = 0.0;
-                segment_terms(num, Dv, nv, gl, hl, bad);
-                stash[so + q] = make_double2(num, Dv);
+                segment_terms(num, Dv, in.w, gl, hl, bad);
                 if (first) {
                     G = gl;
                     H = hl;
@@ -1249,24 +1357,22 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
                     db = 0.0;
                     atomicExch(&sh.gnumeric, 1);
                 } else if (db != 0.0) {
-                    r = exp_step(db);
-                    em1 = r - 1.0;
+                    const ExpStep es = exp_step(db);
+                    r = es.r;
+                    em1 = es.em1;
                     atomicAdd(&sh.gnonzero, 1);
-                    atomicExch(&sh.gchanged, 1);
                 }
                 if (wl) atomicOr(&sh.gwarn, wl);
                 sh.gdb[c] = db;
                 sh.gr[c] = r;
                 sh.gem1[c] = em1;
                 sh.gnbj[c] = bj + db;
-                sh.gtrust[c] = fmax(2.0 * fabs(db), 0.5 * tj);
+                sh.gtrust[c] = trust_update(db, tj);
             }
         } else if (j + m < j1) {
             // the other warps: gather the next group into the other half of the buffers
             const int fw = mine ? warp - (c + 1) : warp - m;
-            const int nh = half ^ 1;
-            narrow_gather(d, j + m, d.nar_group[j + m] > 0 ? d.nar_group[j + m] : 1, fw * 32 + lane,
-                          (nwarps - m) * 32, sm.est + nh * (kRowCap / 2), sm.seg_stash + nh * (kSegCap / 2));
+            narrow_gather(d, j + m, fw * 32 + lane, (nwarps - m) * 32, sm.nar[half ^ 1]);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1279,22 +1385,21 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
             if (db != 0.0) {
                 const double r = sh.gr[c], em1 = sh.gem1[c];
                 for (int q = wi * 32 + lane; q < nseg; q += wpc * 32) {
-                    const int4 sg = d.nar_seg[a + q];
-                    for (int t = 0; t < sg.y; ++t) d.E[d.nar_row[sg.z + t]] = est[sg.z - grow0 + t] * r;
-                    const double2 st = stash[so + q];
-                    d.D[sg.x] = fma(em1, st.x, st.y);
+                    const int4 in = nb.info[so + q];
+                    const int len = in.y & 0xffff;
+                    for (int u = 0; u < len; ++u) d.E[nb.rows[in.z + u]] = nb.est[in.z + u] * r;
+                    const double2 st = nb.stash[so + q];
+                    d.D[in.x] = fma(em1, st.x, st.y);
                 }
             }
             // bookkeeping, and every shard's copy of beta_jc
-            const double nb = sh.gnbj[c];
+            const double nbj = sh.gnbj[c];
             if (wi == 0 && lane == 0) {
-                beta[jc] = nb;
+                beta[jc] = nbj;
                 trust[jc] = sh.gtrust[c];
             }
-            for (int t = wi * 32 + lane + 1; t < d.S; t += wpc * 32) d.beta_priv[static_cast<long long>(t) * d.J + jc] = nb;
+            for (int t = wi * 32 + lane + 1; t < d.S; t += wpc * 32) d.beta_priv[static_cast<long long>(t) * d.J + jc] = nbj;
         }
-        changed = sh.gchanged != 0;
-        gathered = j + m < j1;
         half ^= 1;
         j += m;
         __syncthreads();   // E and D as updated are what the next group reads
@@ -1403,9 +1508,13 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                         }
                         __syncthreads();
                     } else {
+                        // while thread 0 waits for the other CTAs, warps 1.. gather the run's first
+                        // group (checked against D once they have all arrived)
                         if (threadIdx.x == 0)
                             sh.ok = wait_counter(&d.nar_sync[0], run_id * static_cast<unsigned long long>(d.S - 1),
                                                  d.abort_flag, timeout) ? 1 : 0;
+                        else if (warp >= 1)
+                            narrow_gather(d, j, threadIdx.x - 32, blockDim.x - 32, sm.nar[0]);
                         __syncthreads();
                         if (sh.ok) {
                             narrow_columns(d, p, j, j1, sm, sh, beta, trust, status, warn, nonzero_nar);
@@ -1519,9 +1628,9 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                                 db = 0.0;
                                 status = kStNumeric;
                             } else if (db != 0.0) {
-                                // e^db - 1 only scales the D update, whose rounding dominates
-                                r = exp_step(db);
-                                em1 = r - 1.0;
+                                const ExpStep es = exp_step(db);
+                                r = es.r;
+                                em1 = es.em1;
                             }
                         }
                         sh.ok = ok;
@@ -2007,8 +2116,17 @@ __global__ void __launch_bounds__(256) row_sort_kernel(const int64_t *row_ptr, i
 __global__ void exp_selftest_kernel(const double *x, long long n, double *ours, double *ref) {
     for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        ours[i] = exp_step(x[i]);
+        ours[i] = exp_step(x[i]).r;
         ref[i] = exp(x[i]);
+    }
+}
+
+// Diagnostic: the coordinate path's quotient against the IEEE division, element by element.
+__global__ void div_selftest_kernel(const double *a, const double *b, long long n, double *ours, double *ref) {
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        ours[i] = quot(a[i], b[i]);
+        ref[i] = a[i] / b[i];
     }
 }
 
@@ -2042,6 +2160,12 @@ int launch_e_to_f32(const DevLayout &d, int threads, void *stream) {
 int launch_exp_selftest(const double *x, long long n, double *ours, double *ref, void *stream) {
     const int blocks = static_cast<int>(std::min<long long>(std::max<long long>((n + 255) / 256, 1), 1024));
     exp_selftest_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, ours, ref);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_div_selftest(const double *a, const double *b, long long n, double *ours, double *ref, void *stream) {
+    const int blocks = static_cast<int>(std::min<long long>(std::max<long long>((n + 255) / 256, 1), 1024));
+    div_selftest_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(a, b, n, ours, ref);
     return static_cast<int>(cudaGetLastError());
 }
 

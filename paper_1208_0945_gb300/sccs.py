@@ -103,6 +103,7 @@ _SIGS = {
     "sccs_get_beta": (ctypes.c_int, [_P, _dp]),
     "sccs_heldout_loglik": (ctypes.c_int, [_P, _dp, _P, _dp]),
     "sccs_selftest_exp": (ctypes.c_int, [ctypes.c_int32, _dp, ctypes.c_int64, _dp, _dp]),
+    "sccs_selftest_div": (ctypes.c_int, [ctypes.c_int32, _dp, _dp, ctypes.c_int64, _dp, _dp]),
     "sccs_check_wait_timeout": (ctypes.c_int, [_P, ctypes.c_double]),
     "sccs_grad_hess_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int64, _P, _P]),
     "sccs_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(sccs_server_opts)]),
@@ -266,6 +267,18 @@ def sccs_selftest_exp(x, device=0):
     xx = np.ascontiguousarray(x, np.float64)
     ours, ref = np.empty_like(xx), np.empty_like(xx)
     _check(_lib.sccs_selftest_exp(int(device), _dptr(xx), xx.size, _dptr(ours), _dptr(ref)), "sccs_selftest_exp")
+    return ours, ref
+
+
+def sccs_selftest_div(a, b, device=0):
+    """(the library's quotient a/b used in the coordinate step, CUDA's IEEE division)."""
+    aa = np.ascontiguousarray(a, np.float64)
+    bb = np.ascontiguousarray(b, np.float64)
+    if aa.shape != bb.shape:
+        raise ValueError("a and b must have the same shape")
+    ours, ref = np.empty_like(aa), np.empty_like(aa)
+    _check(_lib.sccs_selftest_div(int(device), _dptr(aa), _dptr(bb), aa.size, _dptr(ours), _dptr(ref)),
+           "sccs_selftest_div")
     return ours, ref
 
 

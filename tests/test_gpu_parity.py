@@ -405,7 +405,11 @@ def test_step_exponential_against_cuda_exp(P):
     """The table-driven e^x of the coordinate step against CUDA's exp and the host's: within an
     ulp of the host's everywhere (steps are small; the tails past |x| = 700 go to exp itself)."""
     rng = np.random.default_rng(3)
+    small = 2.0 ** -10
     x = np.concatenate([rng.normal(0, 0.05, 200000), rng.uniform(-30, 30, 200000), rng.uniform(-699, 699, 50000),
+                        rng.uniform(-small, small, 100000), rng.normal(0, 1e-7, 20000),
+                        np.nextafter(small, 0) * np.array([1, -1]), small * np.array([1, -1]),
+                        np.nextafter(small, 1) * np.array([1, -1]),
                         np.array([0.0, -0.0, 1e-300, -1e-300, 5e-17, -5e-17, 1.0, -1.0, 0.5 * np.log(2),
                                   np.log(2) / 64, -np.log(2) / 64, 699.9, -699.9, 700.0, -700.0, 709.0,
                                   -745.0, np.inf, -np.inf, np.nan])])
@@ -420,6 +424,37 @@ def test_step_exponential_against_cuda_exp(P):
     assert np.mean(ulp == 0) > 0.5
     assert ours[x == 0.0].tolist() == [1.0, 1.0]
     assert np.isnan(ours[-1]) and ours[-2] == 0.0 and np.isinf(ours[-3])
+
+
+def test_step_quotient_against_ieee_division(P):
+    """The coordinate path's quotient (FP32 reciprocal seed, Newton-Raphson refinement) against
+    CUDA's IEEE division: within an ulp everywhere, the same bits nearly always, and the IEEE
+    result itself for zeros, infinities, NaNs and magnitudes outside the seed's range."""
+    rng = np.random.default_rng(11)
+    n = 400000
+    D = 10.0 ** rng.uniform(-6, 12, n)                    # W = num / D with 0 < num <= D
+    num = D * rng.uniform(0, 1, n)
+    g = rng.normal(0, 1e4, n)                               # Newton steps g / q
+    q = 10.0 ** rng.uniform(-8, 8, n)
+    specials_a = np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan, 1.0, 1.0, 1e-310, 1e300, 2.0 ** -901,
+                           2.0 ** -900, 3.0, 5e-324, 1.0])
+    specials_b = np.array([3.0, 3.0, 0.0, -0.0, 2.0, 2.0, 2.0, np.inf, np.nan, 3.0, 1e-10, 1.0, 1.0, 2.0 ** 121,
+                           1.0, 2.0 ** -121])
+    a = np.concatenate([num, g, specials_a])
+    b = np.concatenate([D, q, specials_b])
+    ours, ref = P.sccs.sccs_selftest_div(a, b)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isnan(ours), np.isnan(ref))
+    assert np.array_equal(ours[~fin & ~np.isnan(ref)], ref[~fin & ~np.isnan(ref)])
+    nz = fin & (ref != 0)
+    ulp = np.abs(ours[nz] - ref[nz]) / np.spacing(np.abs(ref[nz]))
+    assert ulp.max() <= 1.0, ulp.max()
+    assert np.mean(ours[fin] == ref[fin]) > 0.999
+    k = len(specials_a)
+    sa, so = ref[-k:], ours[-k:]
+    same = (sa == so) | (np.isnan(sa) & np.isnan(so))
+    assert same.all(), (sa, so)
+    assert np.array_equal(np.signbit(so[:2]), np.signbit(sa[:2]))   # signed zeros kept
 
 
 def _genkin_stat(X, b_now, b_prev):
