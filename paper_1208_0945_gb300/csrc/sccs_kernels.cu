@@ -292,6 +292,7 @@ struct SharedState {
     int run_status;         // a finished run_fit's status (thread 0 writes it)
     int drained;            // its staging copies all landed (thread blockDim - 32 writes it)
     unsigned long long run_seq;   // the all-reduce sequence number it ended at
+    int nar_pre;            // CTA 0: the narrow run whose first group's static data is in nar_hi
 };
 
 // One narrow group's gathered data (half of the narrow buffers).
@@ -311,13 +312,17 @@ struct WideBuf {
 };
 
 // Wide columns and narrow runs never hold gathered state at the same time (CTA 0 finishes a
-// wide column's phase C before a narrow run starts, and the run before the next phase A).
+// wide column's phase C before a narrow run starts, and the run before the next phase A), so
+// one narrow buffer shares space with the wide one.  The other (nar_hi) takes a run's first
+// group, whose static data is gathered while the wide column before the run is still live.
 struct SmemLayout {
     StageBuf stage[2];
     union {
         WideBuf wide;
-        NarrowBuf nar[2];            // narrow groups: the stepping one and the next
+        NarrowBuf nar_lo;
     };
+    NarrowBuf nar_hi;
+    __device__ NarrowBuf &nar(int half) { return half ? nar_hi : nar_lo; }
 };
 
 // ------------------------------------------------------------------ grid all-reduce
@@ -328,9 +333,11 @@ struct SmemLayout {
 // so a reader can tell a fresh value from a stale one without a separate flag.  A CTA can
 // not run two rounds ahead of a reader, because the round after next needs the reader's
 // own contribution.  The totals are exact fixed-point sums rounded once, so every CTA
-// holds the same bits.
+// holds the same bits.  With `sync` the round is also a release/acquire: each CTA's writes
+// before its contribution (ordered by a CTA barrier before the call) are visible to every
+// CTA after the call (and, after a CTA barrier, to all its threads).
 __device__ bool grid_allreduce2(const DevLayout &d, int me, unsigned long long seq, double a, double b, double &A,
-                                double &B, long long timeout_ns) {
+                                double &B, long long timeout_ns, bool sync = false) {
     const int lane = threadIdx.x & 31;
     const unsigned long long phase = ((seq >> 1) & 1ull) ^ 1ull;
     unsigned long long *buf = d.slots + (seq & 1ull) * 2ull * static_cast<unsigned long long>(d.S);
@@ -339,6 +346,7 @@ __device__ bool grid_allreduce2(const DevLayout &d, int me, unsigned long long s
                                        0x7fffffffffffffffull) | (phase << 63);
         const unsigned long long eb = (static_cast<unsigned long long>(__double_as_longlong(b)) &
                                        0x7fffffffffffffffull) | (phase << 63);
+        if (sync) __threadfence();                    // release: the CTA's writes before the slot
         st_relaxed_v2(buf + 2 * me, ea, eb);
     }
     const long long deadline = now_ns() + timeout_ns;
@@ -385,6 +393,7 @@ __device__ bool grid_allreduce2(const DevLayout &d, int me, unsigned long long s
             return false;
         }
     }
+    if (sync) __threadfence();                        // acquire: after reading every slot
     sa = fx_warp_sum(sa);
     sb = fx_warp_sum(sb);
     const bool any_bad = __any_sync(kFull, bad);
@@ -422,7 +431,7 @@ __device__ bool block_grid_reduce(const DevLayout &d, int me, unsigned long long
         ca = __shfl_sync(kFull, ca, 0);
         cbv = __shfl_sync(kFull, cbv, 0);
         double At = 0.0, Bt = 0.0;
-        const bool ok = grid_allreduce2(d, me, seq, ca, cbv, At, Bt, timeout_ns);
+        const bool ok = grid_allreduce2(d, me, seq, ca, cbv, At, Bt, timeout_ns, true);
         if (lane == 0) {
             sh.ok = ok;
             sh.G = At;
@@ -642,7 +651,8 @@ __device__ void phase_a_staged(const DevLayout &d, const ColDesc &cd, const Stag
         int base = static_cast<int>(sgrp[g] - cd.row0);
         const int maxlen = __shfl_sync(kFull, sg.y, 0);  // segments are sorted longest first
         double num = 0.0;
-        for (int t0 = 0; t0 < maxlen; t0 += kBatch) {
+        // one batch of diagonals; the first batch's first diagonal starts the sums (no FP64 add)
+        auto batch = [&](int t0, bool init) {
             int pos[kBatch];
             int32_t k[kBatch];
 #pragma unroll
@@ -660,12 +670,15 @@ __device__ void phase_a_staged(const DevLayout &d, const ColDesc &cd, const Stag
             for (int u = 0; u < kBatch; ++u) {
                 if (t0 + u < maxlen) {       // warp-uniform: skip the FP64 add on empty diagonals
                     if (k[u] >= 0) {
-                        num += e[u];
+                        if (init && u == 0) num = e[u];
+                        else num += e[u];
                         sm.wide.est[pos[u]] = e[u];
                     }
                 }
             }
-        }
+        };
+        batch(0, true);
+        for (int t0 = kBatch; t0 < maxlen; t0 += kBatch) batch(t0, false);
         double gl = 0.0, hl = 0.0;
         if (valid) {
             segment_terms(num, Dv, nv, gl, hl, bad);
@@ -716,7 +729,7 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, double &G, doub
         const int nv = valid ? d.nev[sg.x] : 0;
         const int maxlen = __shfl_sync(kFull, sg.y, 0);
         double num = 0.0;
-        for (int t0 = 0; t0 < maxlen; t0 += kBatch) {
+        auto batch = [&](int t0, bool init) {
             int32_t k[kBatch];
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
@@ -729,9 +742,15 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, double &G, doub
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? d.E[k[u]] : 0.0;
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u)
-                if (t0 + u < maxlen && k[u] >= 0) num += e[u];
-        }
+            for (int u = 0; u < kBatch; ++u) {
+                if (t0 + u < maxlen && k[u] >= 0) {
+                    if (init && u == 0) num = e[u];
+                    else num += e[u];
+                }
+            }
+        };
+        if (maxlen > 0) batch(0, true);
+        for (int t0 = kBatch; t0 < maxlen; t0 += kBatch) batch(t0, false);
         double gl = 0.0, hl = 0.0;
         if (valid) {
             segment_terms(num, Dv, nv, gl, hl, bad);
@@ -1214,10 +1233,12 @@ __device__ bool wait_counter(const unsigned long long *ctr, unsigned long long t
         unsigned long long v;
         asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
         if (v >= target) return true;
-        if (*reinterpret_cast<const volatile int *>(abort_flag)) return false;
-        if ((it & 15u) == 15u && now_ns() - t0 > timeout_ns) {
-            atomicExch(const_cast<int *>(abort_flag), 1);
-            return false;
+        if ((it & 15u) == 15u) {
+            if (*reinterpret_cast<const volatile int *>(abort_flag)) return false;
+            if (now_ns() - t0 > timeout_ns) {
+                atomicExch(const_cast<int *>(abort_flag), 1);
+                return false;
+            }
         }
     }
 }
@@ -1242,6 +1263,45 @@ __device__ __forceinline__ void prefetch_slice_state_l2(const DevLayout &d, int 
 // A gathered segment is used as it is unless the one step that can have changed its subject
 // since (its mark, set on the host: a column of the previous group, or the wide column before
 // the run) was not zero; then its state is gathered again.  The W terms are formed after that.
+// The static part of a group's data (sizes, segment info, row indices); thread t of nthr takes
+// segments t, t + nthr, ...
+__device__ void narrow_gather_static(const DevLayout &d, int j, int t, int nthr, NarrowBuf &nb) {
+    const int m = d.nar_group[j] > 0 ? d.nar_group[j] : 1;
+    const long long ga = d.nar_ptr[j], gb = d.nar_ptr[j + m];
+    const int nseg = static_cast<int>(gb - ga);
+    const int row0 = nseg > 0 ? d.nar_seg[ga].z : 0;
+    if (t <= m) {
+        if (t == 0) nb.m = m;
+        nb.col_off[t] = static_cast<int>(d.nar_ptr[j + t] - ga);
+    }
+    for (int q = t; q < nseg; q += nthr) {
+        const int4 sg = d.nar_seg[ga + q];
+        const int r0 = sg.z - row0;
+        nb.info[q] = make_int4(sg.x, sg.y | (sg.w << 16), r0, d.nev[sg.x]);
+        for (int u = 0; u < sg.y; ++u) nb.rows[r0 + u] = d.nar_row[sg.z + u];
+    }
+}
+
+// The state part (numerator, D, E per row) for the same segments as narrow_gather_static with
+// the same t and nthr; that call's writes must be visible (a barrier since, or this thread's).
+__device__ void narrow_gather_state(const DevLayout &d, int t, int nthr, NarrowBuf &nb) {
+    const int nseg = nb.col_off[nb.m];
+    for (int q = t; q < nseg; q += nthr) {
+        const int4 in = nb.info[q];
+        const double Dv = d.D[in.x];
+        const int len = in.y & 0xffff;
+        double num = d.E[nb.rows[in.z]];
+        nb.est[in.z] = num;
+        for (int u = 1; u < len; ++u) {
+            const double e = d.E[nb.rows[in.z + u]];
+            nb.est[in.z + u] = e;
+            num += e;
+        }
+        nb.stash[q] = make_double2(num, Dv);
+    }
+}
+
+// Both parts at once.
 __device__ void narrow_gather(const DevLayout &d, int j, int t, int nthr, NarrowBuf &nb) {
     const int m = d.nar_group[j] > 0 ? d.nar_group[j] : 1;
     const long long ga = d.nar_ptr[j], gb = d.nar_ptr[j + m];
@@ -1256,9 +1316,12 @@ __device__ void narrow_gather(const DevLayout &d, int j, int t, int nthr, Narrow
         const double Dv = d.D[sg.x];
         const int nv = d.nev[sg.x];
         const int r0 = sg.z - row0;
-        double num = 0.0;
-        for (int u = 0; u < sg.y; ++u) {
-            const int row = d.nar_row[sg.z + u];
+        int row = d.nar_row[sg.z];                   // every segment has a row
+        double num = d.E[row];
+        nb.rows[r0] = row;
+        nb.est[r0] = num;
+        for (int u = 1; u < sg.y; ++u) {
+            row = d.nar_row[sg.z + u];
             const double e = d.E[row];
             nb.rows[r0 + u] = row;
             nb.est[r0 + u] = e;
@@ -1273,14 +1336,16 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
                                SharedState &sh, double *beta, double *trust, int &status, int &warn,
                                long long &nonzero) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    int half = 0;
+    int half = 1;                                   // the first group is in nar_hi
     for (int j = j0; j < j1;) {
-        NarrowBuf &nb = sm.nar[half];
+        NarrowBuf &nb = sm.nar(half);
         const int m = nb.m;
+        // warps interleaved over the columns (warp w works for column w mod m), so the group's
+        // steppers (warps 0..m-1) sit in different SM partitions and their FP64 chains overlap
         const int wpc = nwarps / m;                 // warps per column
-        const int c = warp / wpc;                   // this warp's column (c >= m: a spare warp)
-        const int wi = warp - c * wpc;
-        const bool mine = c < m;
+        const int c = warp % m;
+        const int wi = warp / m;
+        const bool mine = wi < wpc;                 // warps past m * wpc are spare
         const int jc = j + (mine ? c : 0);
         if (threadIdx.x == 0) sh.gnumeric = sh.gwarn = sh.gnonzero = 0;
         // the step's operands early, off the critical path
@@ -1310,9 +1375,10 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
                     Dv = st.y;
                 } else {
                     Dv = d.D[in.x];
-                    num = 0.0;
                     const int len = in.y & 0xffff;
-                    for (int u = 0; u < len; ++u) {
+                    num = d.E[nb.rows[in.z]];
+                    nb.est[in.z] = num;
+                    for (int u = 1; u < len; ++u) {
                         const double e = d.E[nb.rows[in.z + u]];
                         nb.est[in.z + u] = e;
                         num += e;
@@ -1342,9 +1408,9 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
         __syncthreads();
         if (mine && wi == 0) {
             // the column's sums over its warps, then its step
-            Fx ta = lane < wpc ? sh.wa[c * wpc + lane] : fx_zero();
-            Fx tbx = lane < wpc ? sh.wb[c * wpc + lane] : fx_zero();
-            const bool cbad = __any_sync(kFull, lane < wpc ? sh.wbad[c * wpc + lane] != 0 : false);
+            Fx ta = lane < wpc ? sh.wa[c + m * lane] : fx_zero();
+            Fx tbx = lane < wpc ? sh.wb[c + m * lane] : fx_zero();
+            const bool cbad = __any_sync(kFull, lane < wpc ? sh.wbad[c + m * lane] != 0 : false);
             ta = fx_warp_sum(ta);
             tbx = fx_warp_sum(tbx);
             if (lane == 0) {
@@ -1371,8 +1437,7 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
             }
         } else if (j + m < j1) {
             // the other warps: gather the next group into the other half of the buffers
-            const int fw = mine ? warp - (c + 1) : warp - m;
-            narrow_gather(d, j + m, fw * 32 + lane, (nwarps - m) * 32, sm.nar[half ^ 1]);
+            narrow_gather(d, j + m, (warp - m) * 32 + lane, (nwarps - m) * 32, sm.nar(half ^ 1));
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1448,6 +1513,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
         sh.desc[1].staged = 0;
         sh.nonzero = 0;
         sh.drained = 1;
+        sh.nar_pre = -1;
     }
     __syncthreads();
     // staging (copies, pending set, next bounds) belongs to the last warp's lane 0
@@ -1494,10 +1560,12 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     int j1 = j + 1;
                     while (j1 < J && d.narrow[j1]) ++j1;
                     ++run_id;
-                    __threadfence();   // this thread's E and D writes, before the arrival below
                     __syncthreads();
                     if (s != 0) {
                         if (threadIdx.x == 0) {
+                            // after the barrier, thread 0's fence orders the whole CTA's E and D
+                            // writes before the arrival (cumulativity)
+                            __threadfence();
                             atomicAdd(&d.nar_sync[0], 1ull);
                             sh.ok = wait_counter(&d.nar_sync[16], run_id, d.abort_flag, timeout) ? 1 : 0;
                         } else if (d.first_wide >= 0) {
@@ -1513,14 +1581,17 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                         if (threadIdx.x == 0)
                             sh.ok = wait_counter(&d.nar_sync[0], run_id * static_cast<unsigned long long>(d.S - 1),
                                                  d.abort_flag, timeout) ? 1 : 0;
-                        else if (warp >= 1)
-                            narrow_gather(d, j, threadIdx.x - 32, blockDim.x - 32, sm.nar[0]);
+                        else if (warp >= 1) {
+                            if (sh.nar_pre == j)
+                                narrow_gather_state(d, threadIdx.x - 32, blockDim.x - 32, sm.nar_hi);
+                            else
+                                narrow_gather(d, j, threadIdx.x - 32, blockDim.x - 32, sm.nar_hi);
+                        }
                         __syncthreads();
                         if (sh.ok) {
                             narrow_columns(d, p, j, j1, sm, sh, beta, trust, status, warn, nonzero_nar);
-                            __threadfence();
                             __syncthreads();
-                            if (threadIdx.x == 0)
+                            if (threadIdx.x == 0)   // a release after the barrier covers the CTA's writes
                                 asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&d.nar_sync[16]), "l"(run_id)
                                              : "memory");
                         }
@@ -1618,7 +1689,10 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     cb = __shfl_sync(kFull, cb, 0);
                     // grid all-reduce, then the step in lane 0 (no extra barrier)
                     double At = 0.0, Bt = 0.0;
-                    const bool ok = grid_allreduce2(d, s, seq, ca, cb, At, Bt, timeout);
+                    // before a narrow run, a release/acquire round: CTA 0 then reads every
+                    // shard's E and D as of this column's start (the run's first gather)
+                    const bool before_run = use_narrow && d.next_wide[j] != (j + 1 < J ? j + 1 : 0);
+                    const bool ok = grid_allreduce2(d, s, seq, ca, cb, At, Bt, timeout, before_run);
                     if (lane == 0) {
                         double db = 0.0, r = 1.0, em1 = 0.0;
                         if (ok) {
@@ -1644,6 +1718,12 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     const ColDesc &nd = sh.desc[buf ^ 1];
                     // no early L1 copies of state that a narrow run will change first
                     const bool gap = use_narrow && d.next_wide[j] != (j + 1 < J ? j + 1 : 0);
+                    if (gap && s == 0 && j + 1 < J) {
+                        // the next narrow run's first group: its static data, while the
+                        // all-reduce runs (E and D are read once the other CTAs arrive)
+                        narrow_gather_static(d, j + 1, threadIdx.x - 32, blockDim.x - 32, sm.nar_hi);
+                        if (threadIdx.x == 32) sh.nar_pre = j + 1;
+                    }
                     if (nd.staged && !gap) {
                         if (F32)
                             prefetch_staged_state32(d, nd, sm.stage[buf ^ 1], &sh.bar[buf ^ 1],
