@@ -469,6 +469,8 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
         // step that can change its subject: w = c + 1 if the subject is in column c of the
         // previous group, kNarrowAfterWide if the run's preceding wide column touches it, else 0.
         // The kernel gathers a segment again when that step was not zero.
+        // (the wide column's subjects by binary search: its rows are ascending, a subject's rows
+        // are [pat_ptr[i], pat_ptr[i+1]))
         std::vector<int64_t> tag(static_cast<size_t>(std::max<int64_t>(hl.N, 1)), -1);
         int64_t pass = 0;
         for (int32_t g = 0; g < J;) {
@@ -478,16 +480,21 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             }
             const int32_t m = hl.nar_group[g];
             const bool run_start = g == 0 || !hl.narrow[g - 1];
-            if (run_start) {
-                ++pass;
-                if (g > 0)
-                    for (int64_t e = cptr[g - 1]; e < cptr[g]; ++e) tag[row_pat[crow[e]]] = pass * 16 + 15;
-            }
-            for (int64_t q = hl.nar_ptr[g]; q < hl.nar_ptr[g + m]; ++q) {
-                const int64_t t = tag[hl.nar_seg[q].x];
-                hl.nar_seg[q].w = t >= 0 && t / 16 == pass ? (t % 16 == 15 ? sccs::kNarrowAfterWide : static_cast<int>(t % 16) + 1) : 0;
-            }
             ++pass;
+            for (int64_t q = hl.nar_ptr[g]; q < hl.nar_ptr[g + m]; ++q) {
+                const int32_t i = hl.nar_seg[q].x;
+                int w = 0;
+                if (run_start) {
+                    if (g > 0) {
+                        const int32_t *b = crow.data() + cptr[g - 1], *e = crow.data() + cptr[g];
+                        const int32_t *f = std::lower_bound(b, e, static_cast<int32_t>(hl.pat_ptr[i]));
+                        if (f != e && *f < hl.pat_ptr[i + 1]) w = sccs::kNarrowAfterWide;
+                    }
+                } else if (tag[i] >= 0 && tag[i] / 16 == pass - 1) {
+                    w = static_cast<int>(tag[i] % 16) + 1;
+                }
+                hl.nar_seg[q].w = w;
+            }
             for (int32_t c = 0; c < m; ++c)
                 for (int64_t q = hl.nar_ptr[g + c]; q < hl.nar_ptr[g + c + 1]; ++q) tag[hl.nar_seg[q].x] = pass * 16 + c;
             g += m;
