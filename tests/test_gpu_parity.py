@@ -391,6 +391,36 @@ def test_narrow_columns_match_wide_path_and_oracle(P, prior, var):
         assert r["nonzero_steps"] == out[-1][0]["nonzero_steps"]
 
 
+@pytest.mark.parametrize("prior,var", [("normal", 0.2), ("laplace", 0.05)])
+def test_many_narrow_runs_between_wide_columns(P, prior, var):
+    """400 columns: wide columns over a fifth of the subjects alternate with short runs of tiny
+    columns, so most runs start on subjects the wide column before them has just changed (the
+    run's first gather is speculative and must re-read exactly those).  Six fixed cycles of the
+    narrow path, the all-wide path and the oracle agree to rounding."""
+    rng = np.random.default_rng(77)
+    sizes = []
+    while len(sizes) < 400:
+        sizes.append(int(rng.integers(2000, 6000)))                 # wide
+        sizes.extend(int(x) for x in rng.integers(1, 80, size=int(rng.integers(1, 5))))   # a run
+    sizes = np.array(sizes[:400])
+    d = make_dataset(n_patients=20000, eras=("geometric", 6), J=sizes.size, columns=("sizes", sizes),
+                     n_true=10, beta_sd=0.4, seed=78)
+    orc = oracle.Problem.from_data(d)
+    ref = orc.fit(prior=prior, variance=var, fixed_cycles=6)
+    res = {}
+    for thr in (0, -1):
+        with gpu_model(P, d, num_shards=16, narrow_max_nnz=thr) as m:
+            if thr == 0:
+                assert m.info["narrow_columns"] > 150
+            m.set_prior(prior, var)
+            res[thr] = m.fit(tol=-1.0, max_cycles=6, history=True)
+    for thr in (0, -1):
+        np.testing.assert_allclose(res[thr]["beta"], ref["beta"], atol=1e-11, rtol=0)
+        np.testing.assert_allclose(res[thr]["history"], ref["history"], rtol=1e-12)
+    np.testing.assert_allclose(res[0]["beta"], res[-1]["beta"], atol=1e-12, rtol=0)
+    assert res[0]["nonzero_steps"] == res[-1]["nonzero_steps"]
+
+
 def test_all_columns_narrow_and_converged(P):
     d, fit = tiny_fit_config()
     orc = oracle.Problem.from_data(d)
