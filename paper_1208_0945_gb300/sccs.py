@@ -424,6 +424,7 @@ class SCCSModel:
             col_ptr, row_idx = data.col_ptr, data.row_idx
         st = _torch_stream() if stream == "torch" else stream
         self.J = int(J)
+        self.device = int(device)
         self.handle = sccs_create(K, patient_id, y, L, J, col_ptr, row_idx, x_values, device=device, stream=st,
                                   num_shards=num_shards, threads_per_block=threads_per_block,
                                   narrow_max_nnz=narrow_max_nnz, narrow_group_max=narrow_group_max)
