@@ -79,6 +79,15 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p) {
 }
 
 // Barrier 1 among warps 1..n-1 (warp 0 is busy with the all-reduce).
+// 4-byte asynchronous global -> shared copies (no registers held while in flight).
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ void named_barrier_all_but_warp0() {
     asm volatile("bar.sync 1, %0;" ::"r"(static_cast<int>(blockDim.x) - 32) : "memory");
 }
@@ -305,11 +314,13 @@ struct NarrowBuf {
     int col_off[kNarrowGroupMax + 1];    // each column's first segment
 };
 
-// A wide column's gathered state between its phases A and C.
+// A wide column's gathered state between its phases A and C (for a slice too big to stage, the
+// row-index ring of phase_a_global: 2 x 32 x kBatch ints per warp).
 struct WideBuf {
     double est[kRowCap];             // E gathered in phase A, per row position
     double2 seg_stash[kSegCap];      // (num, D) per segment
 };
+static_assert(kMaxWarps * 2 * 32 * kBatch * sizeof(int) <= sizeof(WideBuf), "row ring exceeds the wide buffer");
 
 // Wide columns and narrow runs never hold gathered state at the same time (CTA 0 finishes a
 // wide column's phase C before a narrow run starts, and the run before the next phase A), so
@@ -695,8 +706,14 @@ __device__ void phase_a_staged(const DevLayout &d, const ColDesc &cd, const Stag
     }
 }
 
-// Phase A over a slice read straight from global memory (slices too big to stage).
-__device__ void phase_a_global(const DevLayout &d, int s, int j, double &G, double &H, bool &bad) {
+// Phase A over a slice read straight from global memory (slices too big to stage).  Each warp
+// walks its groups with a software pipeline: the group descriptors two groups ahead, and the row
+// indices of the next group's first kBatch diagonals copied asynchronously into the warp's half
+// of a ring in shared memory (the wide buffer, idle while the slice is not staged), so a group's
+// E gathers start from rows already on chip instead of behind a dependent load.  Without a ring
+// (kRing false: a kernel with no room for it) the rows are read from global memory in place.
+template <bool kPipe>
+__device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, double &G, double &H, bool &bad) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
@@ -705,37 +722,64 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, double &G, doub
     const long long grp0 = d.slice_grp[so];
     const int ngrp = static_cast<int>(d.slice_grp[so + 1] - grp0);
     double *stash = d.stash + 2 * static_cast<long long>(s) * d.stash_stride;
+    constexpr int kRing = 32 * kBatch;              // rows of a group's first kBatch diagonals, at most
+    int *ring = kPipe ? ring_all + warp * (2 * kRing) : nullptr;
+    auto desc = [&](int g, int2 &sg, long long &base) {
+        sg = make_int2(0, 0);
+        base = 0;
+        if (g < ngrp) {
+            const long long si = seg0 + 32 * static_cast<long long>(g) + lane;
+            if (si < seg1) sg = d.segs[si];
+            base = d.grp_base[grp0 + g];
+        }
+    };
+    // the rows of a group's first kBatch diagonals are contiguous from its base (segments are
+    // longest first, diagonal after diagonal); every lane commits a copy group, empty or not
+    auto stage_rows = [&](const int2 &sg, long long base, int half) {
+        if (!kPipe) return;
+        int R = 0;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) R += __popc(__ballot_sync(kFull, sg.y > u));
+        int *dst = ring + half * kRing;
+        for (int q = lane; q < R; q += 32) cp_async4(dst + q, d.rows + base + q);
+        cp_async_commit();
+    };
     bool first = true;
-    // the next group's descriptors are loaded one group ahead
-    int2 sg_next = make_int2(0, 0);
-    long long base_next = 0;
-    if (warp < ngrp) {
-        const long long si = seg0 + 32 * static_cast<long long>(warp) + lane;
-        sg_next = si < seg1 ? d.segs[si] : make_int2(0, 0);
-        base_next = d.grp_base[grp0 + warp];
-    }
+    int2 sg_cur, sg_n1;
+    long long base_cur, base_n1;
+    desc(warp, sg_cur, base_cur);
+    desc(warp + nwarps, sg_n1, base_n1);
+    if (warp < ngrp) stage_rows(sg_cur, base_cur, 0);
+    int half = 0;
     for (int g = warp; g < ngrp; g += nwarps) {
         const long long si = seg0 + 32 * static_cast<long long>(g) + lane;
         const bool valid = si < seg1;
-        const int2 sg = sg_next;
-        long long base = base_next;
-        const int gn = g + nwarps;
-        if (gn < ngrp) {
-            const long long sn = seg0 + 32 * static_cast<long long>(gn) + lane;
-            sg_next = sn < seg1 ? d.segs[sn] : make_int2(0, 0);
-            base_next = d.grp_base[grp0 + gn];
-        }
+        const int2 sg = sg_cur;
+        const long long gbase = base_cur;
+        int2 sg_n2;
+        long long base_n2;
+        desc(g + 2 * nwarps, sg_n2, base_n2);
+        const bool has_next = g + nwarps < ngrp;     // warp-uniform
+        if (has_next) stage_rows(sg_n1, base_n1, half ^ 1);
         const double Dv = valid ? d.D[sg.x] : 1.0;
         const int nv = valid ? d.nev[sg.x] : 0;
+        // this group's rows have landed (every copy group but the newest), for every lane
+        if (kPipe) {
+            if (has_next) cp_async_wait<1>();
+            else cp_async_wait<0>();
+            __syncwarp();
+        }
+        const int *rr = kPipe ? ring + half * kRing : nullptr;
         const int maxlen = __shfl_sync(kFull, sg.y, 0);
+        long long base = gbase;
         double num = 0.0;
-        auto batch = [&](int t0, bool init) {
+        auto batch = [&](int t0, bool init, bool staged) {
             int32_t k[kBatch];
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 const bool act = sg.y > t0 + u;
                 const unsigned m = __ballot_sync(kFull, act);
-                k[u] = act ? d.rows[base + lane] : -1;
+                k[u] = act ? (staged ? rr[static_cast<int>(base - gbase) + lane] : d.rows[base + lane]) : -1;
                 base += __popc(m);
             }
             double e[kBatch];
@@ -749,8 +793,8 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, double &G, doub
                 }
             }
         };
-        if (maxlen > 0) batch(0, true);
-        for (int t0 = kBatch; t0 < maxlen; t0 += kBatch) batch(t0, false);
+        if (maxlen > 0) batch(0, true, kPipe);
+        for (int t0 = kBatch; t0 < maxlen; t0 += kBatch) batch(t0, false, false);
         double gl = 0.0, hl = 0.0;
         if (valid) {
             segment_terms(num, Dv, nv, gl, hl, bad);
@@ -765,6 +809,12 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, double &G, doub
             G += gl;
             H += hl;
         }
+        if (kPipe) __syncwarp();                      // every lane is done with this half
+        sg_cur = sg_n1;
+        base_cur = base_n1;
+        sg_n1 = sg_n2;
+        base_n1 = base_n2;
+        half ^= 1;
     }
 }
 
@@ -1652,7 +1702,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                 } else {
                     double G = 0.0, H = 0.0;
                     if (cd.staged) phase_a_staged(d, cd, sm.stage[buf], sm, G, H, bad);
-                    else phase_a_global(d, s, j, G, H, bad);
+                    else phase_a_global<true>(d, s, j, reinterpret_cast<int *>(&sm.wide), G, H, bad);
                     ga = fx_from_double(G, bad);
                     ha = fx_from_double(H, bad);
                 }
@@ -2035,7 +2085,7 @@ __global__ void __launch_bounds__(512, 1) grad_hess_kernel(DevLayout d, int j, F
     {
         double G = 0.0, H = 0.0;
         bool bad = false;
-        phase_a_global(d, blockIdx.x, j, G, H, bad);
+        phase_a_global<false>(d, blockIdx.x, j, nullptr, G, H, bad);
         const Fx fg = fx_from_double(G, bad), fh = fx_from_double(H, bad);
         if (!block_grid_reduce(d, blockIdx.x, seq++, timeout, sh, fg, fh, bad)) goto aborted;
         if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -421,6 +421,24 @@ def test_many_narrow_runs_between_wide_columns(P, prior, var):
     assert res[0]["nonzero_steps"] == res[-1]["nonzero_steps"]
 
 
+@pytest.mark.parametrize("shards", [2, 5])
+def test_unstaged_slices_pipelined_gather(P, shards):
+    """Columns far larger than a staged slice on few shards: phase A walks dozens of 32-segment
+    groups per warp from global memory, the next group's row indices copied ahead into shared
+    memory; segments up to 30 rows long also take the unstaged later diagonals.  Three fixed
+    cycles against the oracle."""
+    sizes = np.array([300000, 150000, 60000, 9000, 500, 20])
+    d = make_dataset(n_patients=40000, eras=("uniform", 1, 30), J=sizes.size, columns=("sizes", sizes),
+                     n_true=3, beta_sd=0.3, seed=95)
+    orc = oracle.Problem.from_data(d)
+    ref = orc.fit(prior="normal", variance=0.5, fixed_cycles=3)
+    with gpu_model(P, d, num_shards=shards) as m:
+        m.set_prior("normal", 0.5)
+        r = m.fit(tol=-1.0, max_cycles=3, history=True)
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11, rtol=0)
+    np.testing.assert_allclose(r["history"], ref["history"], rtol=1e-12)
+
+
 def test_all_columns_narrow_and_converged(P):
     d, fit = tiny_fit_config()
     orc = oracle.Problem.from_data(d)
