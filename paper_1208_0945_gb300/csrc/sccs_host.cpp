@@ -197,6 +197,7 @@ struct HostLayout {
     std::vector<int64_t> grp_base;
     std::vector<int64_t> slice_row, slice_seg, slice_grp;  // S*(J+1)
     int64_t stash_stride = 1;
+    int64_t estash_stride = 1;
     int64_t segments = 0;
     int64_t max_col = 0;
     int64_t subjects_in = 0;
@@ -553,7 +554,7 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     hl.slice_seg.assign(static_cast<size_t>(SJ), 0);
     hl.slice_grp.assign(static_cast<size_t>(SJ), 0);
     int64_t tr = 0, ts = 0, tg = 0;
-    int64_t max_seg = 1;
+    int64_t max_seg = 1, max_rows = 1;
     for (int32_t s = 0; s < S; ++s) {
         for (int32_t j = 0; j <= J; ++j) {
             const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
@@ -565,10 +566,12 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
                 ts += s_seg[idx];
                 tg += (s_seg[idx] + 31) / 32;
                 max_seg = std::max<int64_t>(max_seg, s_seg[idx]);
+                max_rows = std::max<int64_t>(max_rows, s_nnz[idx]);
             }
         }
     }
     hl.stash_stride = max_seg;
+    hl.estash_stride = max_rows;
     hl.segments = ts;
     hl.rows.assign(static_cast<size_t>(tr), 0);
     hl.segs.assign(static_cast<size_t>(ts), int2{0, 0});
@@ -1189,6 +1192,15 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
         d.nar_row = nrow;
         d.nar_group = ngrp;
         d.nar_sync = nsync;
+    }
+    {
+        // E per row of an unstaged slice between its phases A and C (allocated last: the arrays
+        // above keep their measured placement)
+        double *estash = nullptr;
+        if ((rc = alloc_zero(h, &estash, static_cast<size_t>(S) * static_cast<size_t>(hl.estash_stride))))
+            return bail(rc);
+        d.estash = estash;
+        d.estash_stride = hl.estash_stride;
     }
     if ((rc = run_init_state(h, nullptr))) return bail(rc);
     ce = cudaStreamSynchronize(h->stream);

@@ -78,6 +78,8 @@ struct DevLayout {
     double *trust_priv;        // S*J: each CTA's private trust radii
     double *stash;             // S*stash_stride*2: (num, D) per segment of slices too big to stage
     int64_t stash_stride;      // segments per shard
+    double *estash;            // S*estash_stride: E per row of slices too big to stage, phase A -> C
+    int64_t estash_stride;     // rows per shard (the largest slice)
     // grid all-reduce slots: 2 buffers x S slots x {a, b}; sign bit carries the phase
     unsigned long long *slots;
     int *abort_flag;           // set by a CTA that gives up; every wait checks it (lives in FitOut)

@@ -724,6 +724,10 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, 
     double *stash = d.stash + 2 * static_cast<long long>(s) * d.stash_stride;
     constexpr int kRing = 32 * kBatch;              // rows of a group's first kBatch diagonals, at most
     int *ring = kPipe ? ring_all + warp * (2 * kRing) : nullptr;
+    // with the ring (the fit kernel), every gathered E also goes to the slice's E stash at its row
+    // position, for phase C
+    const long long row0 = d.slice_row[so];
+    double *estash = kPipe ? d.estash + static_cast<long long>(s) * d.estash_stride : nullptr;
     auto desc = [&](int g, int2 &sg, long long &base) {
         sg = make_int2(0, 0);
         base = 0;
@@ -775,6 +779,7 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, 
         double num = 0.0;
         auto batch = [&](int t0, bool init, bool staged) {
             int32_t k[kBatch];
+            long long pb = base;                      // the batch's first row (stash positions)
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 const bool act = sg.y > t0 + u;
@@ -787,9 +792,14 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, 
             for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? d.E[k[u]] : 0.0;
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
-                if (t0 + u < maxlen && k[u] >= 0) {
-                    if (init && u == 0) num = e[u];
-                    else num += e[u];
+                if (t0 + u < maxlen) {                // warp-uniform
+                    const unsigned m = __ballot_sync(kFull, sg.y > t0 + u);
+                    if (k[u] >= 0) {
+                        if (init && u == 0) num = e[u];
+                        else num += e[u];
+                        if (kPipe) estash[pb - row0 + lane] = e[u];
+                    }
+                    pb += __popc(m);
                 }
             }
         };
@@ -836,22 +846,22 @@ __device__ void phase_c_global(const DevLayout &d, int s, int j, double r, doubl
     const long long row0 = d.slice_row[so], row1 = d.slice_row[so + 1];
     const long long seg0 = d.slice_seg[so], seg1 = d.slice_seg[so + 1];
     const double *stash = d.stash + 2 * static_cast<long long>(s) * d.stash_stride;
+    // E as phase A gathered it, at each row's position in the slice (coalesced, no gather)
+    const double *estash = d.estash + static_cast<long long>(s) * d.estash_stride - row0;
     const long long T = blockDim.x;
     long long p = row0 + threadIdx.x;
     for (; p + 3 * T < row1; p += 4 * T) {
         int32_t k[4];
         double e[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) k[u] = d.rows[p + u * T];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = d.E[k[u]];
+        for (int u = 0; u < 4; ++u) {
+            k[u] = d.rows[p + u * T];
+            e[u] = estash[p + u * T];
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) d.E[k[u]] = e[u] * r;
     }
-    for (; p < row1; p += T) {
-        const int32_t k = d.rows[p];
-        d.E[k] *= r;
-    }
+    for (; p < row1; p += T) d.E[d.rows[p]] = estash[p] * r;
     for (long long si = seg0 + threadIdx.x; si < seg1; si += T) {
         const double num = stash[2 * (si - seg0)], Dv = stash[2 * (si - seg0) + 1];
         d.D[d.segs[si].x] = fma(em1, num, Dv);

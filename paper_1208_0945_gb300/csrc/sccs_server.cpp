@@ -94,7 +94,8 @@ size_t slot_bytes(const sccs::DevLayout &d, int max_cycles) {
     const size_t N1 = std::max<size_t>(N, 1);
     return al(8 * K) + al(8 * N) + al(4 * K) + al(8 * N) + 2 * al(8 * S * J) +
            al(16 * S * static_cast<size_t>(d.stash_stride)) + al(32 * S) + 2 * al(sizeof(sccs::FitOut)) +
-           al(8 * J) + al(8 * static_cast<size_t>(max_cycles + 1)) + 3 * al(4 * N1) + 2 * al(8 * J) + al(256) + al(8 * K);
+           al(8 * J) + al(8 * static_cast<size_t>(max_cycles + 1)) + 3 * al(4 * N1) + 2 * al(8 * J) + al(256) + al(8 * K) +
+           al(8 * S * static_cast<size_t>(d.estash_stride));
 }
 
 }  // namespace
@@ -191,6 +192,7 @@ FitSlot *make_slot(const sccs_handle *dataset, int max_cycles) {
     d.E_prev = reinterpret_cast<double *>(take(8 * std::max<size_t>(K, 1)));   // Genkin's X-beta test
     if (d.narrow) d.nar_sync = nsync;   // the slot's own narrow-run counters
     s->ytx_ho = reinterpret_cast<double *>(take(8 * J));
+    d.estash = reinterpret_cast<double *>(take(8 * S * static_cast<size_t>(d.estash_stride)));
     d.abort_flag = &s->out_dev->abort_flag;
     if (cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&s->out_host, sizeof(sccs::FitOut)) != cudaSuccess ||
