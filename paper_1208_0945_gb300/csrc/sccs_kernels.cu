@@ -988,7 +988,10 @@ __device__ void phase_a_staged32(const DevLayout &d, const ColDesc &cd, const St
     }
 }
 
-__device__ void phase_a_global32(const DevLayout &d, int s, int j, Fx &ga, Fx &ha, bool &bad) {
+// The FP32 counterpart of phase_a_global<true>: the same per-warp pipeline (descriptors two groups
+// ahead, the next group's first rows copied into the warp's ring), and every gathered E32 kept in
+// the slice's E stash (as floats) for phase C.
+__device__ void phase_a_global32(const DevLayout &d, int s, int j, int *ring_all, Fx &ga, Fx &ha, bool &bad) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
@@ -997,49 +1000,89 @@ __device__ void phase_a_global32(const DevLayout &d, int s, int j, Fx &ga, Fx &h
     const long long grp0 = d.slice_grp[so];
     const int ngrp = static_cast<int>(d.slice_grp[so + 1] - grp0);
     float4 *stash = reinterpret_cast<float4 *>(d.stash + 2 * static_cast<long long>(s) * d.stash_stride);
-    int2 sg_next = make_int2(0, 0);
-    long long base_next = 0;
-    if (warp < ngrp) {
-        const long long si = seg0 + 32 * static_cast<long long>(warp) + lane;
-        sg_next = si < seg1 ? d.segs[si] : make_int2(0, 0);
-        base_next = d.grp_base[grp0 + warp];
-    }
+    constexpr int kRing = 32 * kBatch;
+    int *ring = ring_all + warp * (2 * kRing);
+    const long long row0 = d.slice_row[so];
+    float *estash = reinterpret_cast<float *>(d.estash + static_cast<long long>(s) * d.estash_stride);
+    auto desc = [&](int g, int2 &sg, long long &base) {
+        sg = make_int2(0, 0);
+        base = 0;
+        if (g < ngrp) {
+            const long long si = seg0 + 32 * static_cast<long long>(g) + lane;
+            if (si < seg1) sg = d.segs[si];
+            base = d.grp_base[grp0 + g];
+        }
+    };
+    auto stage_rows = [&](const int2 &sg, long long base, int half) {
+        int R = 0;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) R += __popc(__ballot_sync(kFull, sg.y > u));
+        int *dst = ring + half * kRing;
+        for (int q = lane; q < R; q += 32) cp_async4(dst + q, d.rows + base + q);
+        cp_async_commit();
+    };
+    int2 sg_cur, sg_n1;
+    long long base_cur, base_n1;
+    desc(warp, sg_cur, base_cur);
+    desc(warp + nwarps, sg_n1, base_n1);
+    if (warp < ngrp) stage_rows(sg_cur, base_cur, 0);
+    int half = 0;
     for (int g = warp; g < ngrp; g += nwarps) {
         const long long si = seg0 + 32 * static_cast<long long>(g) + lane;
         const bool valid = si < seg1;
-        const int2 sg = sg_next;
-        long long base = base_next;
-        const int gn = g + nwarps;
-        if (gn < ngrp) {
-            const long long sn = seg0 + 32 * static_cast<long long>(gn) + lane;
-            sg_next = sn < seg1 ? d.segs[sn] : make_int2(0, 0);
-            base_next = d.grp_base[grp0 + gn];
-        }
+        const int2 sg = sg_cur;
+        const long long gbase = base_cur;
+        int2 sg_n2;
+        long long base_n2;
+        desc(g + 2 * nwarps, sg_n2, base_n2);
+        const bool has_next = g + nwarps < ngrp;     // warp-uniform
+        if (has_next) stage_rows(sg_n1, base_n1, half ^ 1);
         const float2 Dv = valid ? d.D32[sg.x] : make_float2(1.0f, 0.0f);
         const int nv = valid ? d.nev[sg.x] : 0;
+        if (has_next) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncwarp();
+        const int *rr = ring + half * kRing;
         const int maxlen = __shfl_sync(kFull, sg.y, 0);
+        long long base = gbase;
         float sum = 0.0f, comp = 0.0f;
         for (int t0 = 0; t0 < maxlen; t0 += kBatch) {
+            const bool staged = t0 == 0;
             int32_t k[kBatch];
+            long long pb = base;
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 const bool act = sg.y > t0 + u;
                 const unsigned m = __ballot_sync(kFull, act);
-                k[u] = act ? d.rows[base + lane] : -1;
+                k[u] = act ? (staged ? rr[static_cast<int>(base - gbase) + lane] : d.rows[base + lane]) : -1;
                 base += __popc(m);
             }
             float e[kBatch];
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? d.E32[k[u]] : 0.0f;
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u)
-                if (k[u] >= 0) kahan_add(sum, comp, e[u]);
+            for (int u = 0; u < kBatch; ++u) {
+                if (t0 + u < maxlen) {                // warp-uniform
+                    const unsigned m = __ballot_sync(kFull, sg.y > t0 + u);
+                    if (k[u] >= 0) {
+                        kahan_add(sum, comp, e[u]);
+                        estash[pb - row0 + lane] = e[u];
+                    }
+                    pb += __popc(m);
+                }
+            }
         }
         if (valid) {
             const float num = sum - comp;
             segment_terms32(num, Dv.x, nv, ga, ha, bad);
             stash[si - seg0] = make_float4(num, Dv.x, Dv.y, 0.0f);
         }
+        __syncwarp();                                 // every lane is done with this half
+        sg_cur = sg_n1;
+        base_cur = base_n1;
+        sg_n1 = sg_n2;
+        base_n1 = base_n2;
+        half ^= 1;
     }
 }
 
@@ -1061,22 +1104,22 @@ __device__ void phase_c_global32(const DevLayout &d, int s, int j, float r, floa
     const long long row0 = d.slice_row[so], row1 = d.slice_row[so + 1];
     const long long seg0 = d.slice_seg[so], seg1 = d.slice_seg[so + 1];
     const float4 *stash = reinterpret_cast<const float4 *>(d.stash + 2 * static_cast<long long>(s) * d.stash_stride);
+    // E32 as phase A gathered it, at each row's position in the slice
+    const float *estash = reinterpret_cast<const float *>(d.estash + static_cast<long long>(s) * d.estash_stride) - row0;
     const long long T = blockDim.x;
     long long p = row0 + threadIdx.x;
     for (; p + 3 * T < row1; p += 4 * T) {
         int32_t k[4];
         float e[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) k[u] = d.rows[p + u * T];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = d.E32[k[u]];
+        for (int u = 0; u < 4; ++u) {
+            k[u] = d.rows[p + u * T];
+            e[u] = estash[p + u * T];
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) d.E32[k[u]] = e[u] * r;
     }
-    for (; p < row1; p += T) {
-        const int32_t k = d.rows[p];
-        d.E32[k] *= r;
-    }
+    for (; p < row1; p += T) d.E32[d.rows[p]] = estash[p] * r;
     for (long long si = seg0 + threadIdx.x; si < seg1; si += T) {
         const float4 st = stash[si - seg0];
         d.D32[d.segs[si].x] = pair_add(make_float2(st.y, st.z), em1 * st.x);
@@ -1708,7 +1751,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     if (threadIdx.x == 0) atomicExch(d.abort_flag, 1);
                 } else if (F32) {
                     if (cd.staged) phase_a_staged32(d, cd, sm.stage[buf], sm, ga, ha, bad);
-                    else phase_a_global32(d, s, j, ga, ha, bad);
+                    else phase_a_global32(d, s, j, reinterpret_cast<int *>(&sm.wide), ga, ha, bad);
                 } else {
                     double G = 0.0, H = 0.0;
                     if (cd.staged) phase_a_staged(d, cd, sm.stage[buf], sm, G, H, bad);
