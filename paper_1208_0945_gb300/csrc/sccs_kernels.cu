@@ -797,7 +797,7 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, 
                     if (k[u] >= 0) {
                         if (init && u == 0) num = e[u];
                         else num += e[u];
-                        if (kPipe) estash[pb - row0 + lane] = e[u];
+                        if (kPipe) __stcs(estash + (pb - row0 + lane), e[u]);   // streaming: E stays in L2
                     }
                     pb += __popc(m);
                 }
@@ -856,12 +856,12 @@ __device__ void phase_c_global(const DevLayout &d, int s, int j, double r, doubl
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             k[u] = d.rows[p + u * T];
-            e[u] = estash[p + u * T];
+            e[u] = __ldcs(estash + p + u * T);   // streaming: read once
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) d.E[k[u]] = e[u] * r;
     }
-    for (; p < row1; p += T) d.E[d.rows[p]] = estash[p] * r;
+    for (; p < row1; p += T) d.E[d.rows[p]] = __ldcs(estash + p) * r;
     for (long long si = seg0 + threadIdx.x; si < seg1; si += T) {
         const double num = stash[2 * (si - seg0)], Dv = stash[2 * (si - seg0) + 1];
         d.D[d.segs[si].x] = fma(em1, num, Dv);
@@ -1066,7 +1066,7 @@ __device__ void phase_a_global32(const DevLayout &d, int s, int j, int *ring_all
                     const unsigned m = __ballot_sync(kFull, sg.y > t0 + u);
                     if (k[u] >= 0) {
                         kahan_add(sum, comp, e[u]);
-                        estash[pb - row0 + lane] = e[u];
+                        __stcs(estash + (pb - row0 + lane), e[u]);
                     }
                     pb += __popc(m);
                 }
@@ -1114,12 +1114,12 @@ __device__ void phase_c_global32(const DevLayout &d, int s, int j, float r, floa
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             k[u] = d.rows[p + u * T];
-            e[u] = estash[p + u * T];
+            e[u] = __ldcs(estash + p + u * T);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) d.E32[k[u]] = e[u] * r;
     }
-    for (; p < row1; p += T) d.E32[d.rows[p]] = estash[p] * r;
+    for (; p < row1; p += T) d.E32[d.rows[p]] = __ldcs(estash + p) * r;
     for (long long si = seg0 + threadIdx.x; si < seg1; si += T) {
         const float4 st = stash[si - seg0];
         d.D32[d.segs[si].x] = pair_add(make_float2(st.y, st.z), em1 * st.x);
