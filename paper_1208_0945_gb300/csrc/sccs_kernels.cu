@@ -286,7 +286,6 @@ struct SharedState {
     Fx wb[kMaxWarps];
     int wbad[kMaxWarps];
     double db, r, em1;
-    double nbj;             // a narrow column's new beta_j
     // a group of narrow columns: per column step results, and the group's flags
     double gdb[kNarrowGroupMax], gr[kNarrowGroupMax], gem1[kNarrowGroupMax], gnbj[kNarrowGroupMax],
         gtrust[kNarrowGroupMax];
@@ -1680,7 +1679,9 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                         __syncthreads();
                     } else {
                         // while thread 0 waits for the other CTAs, warps 1.. gather the run's first
-                        // group (checked against D once they have all arrived)
+                        // group: every write before the previous wide column is visible (its
+                        // all-reduce was a release/acquire round); what that column itself changes
+                        // on other shards, the segments' marks send back for a second read
                         if (threadIdx.x == 0)
                             sh.ok = wait_counter(&d.nar_sync[0], run_id * static_cast<unsigned long long>(d.S - 1),
                                                  d.abort_flag, timeout) ? 1 : 0;
