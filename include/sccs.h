@@ -159,8 +159,8 @@ const char *sccs_last_error(const sccs_handle *h);
  *   x_values     NULL for an indicator matrix, else [col_ptr[J]] values that must all be 1
  *                (the Hessian form of Eq. 9 needs x_kj^2 = x_kj)
  *   opts         NULL for defaults
- * Subjects with n_i = 0 contribute nothing (Section 2.1) and are removed here.  Errors:
- * SCCS_E_INVAL, SCCS_E_UNSORTED, SCCS_E_NONBINARY, SCCS_E_DUPLICATE, SCCS_E_NOMEM,
+ * Subjects with n_i = 0 contribute nothing (Section 2.1) and are removed here; data with no
+ * event at all (K = 0 included) is rejected with SCCS_E_INVAL.  Errors: SCCS_E_INVAL, SCCS_E_UNSORTED, SCCS_E_NONBINARY, SCCS_E_DUPLICATE, SCCS_E_NOMEM,
  * SCCS_E_CUDA.  On success *out owns device memory until sccs_destroy.  The prior starts as
  * SCCS_PRIOR_NONE and beta as 0.
  */

@@ -233,11 +233,15 @@ int validate_inputs(int64_t K, const int64_t *patient_id, const int32_t *y, cons
     for (int64_t k = 1; k < K; ++k)
         if (patient_id[k] < patient_id[k - 1])
             return fail(SCCS_E_UNSORTED, "patient_id decreases at row " + std::to_string(k));
+    bool any_event = false;
     for (int64_t k = 0; k < K; ++k) {
         if (y[k] < 0) return fail(SCCS_E_INVAL, "negative event count at row " + std::to_string(k));
         if (!(Lin[k] > 0.0) || !std::isfinite(Lin[k]))
             return fail(SCCS_E_INVAL, "offset must be positive and finite at row " + std::to_string(k));
+        any_event = any_event || y[k] > 0;
     }
+    // every n_i = 0: no subject contributes to Eq. 2, so there is nothing to fit
+    if (!any_event) return fail(SCCS_E_INVAL, "no events: every subject has n_i = 0");
     for (int64_t e = 0; e < nnz_in; ++e)
         if (row_idx[e] < 0 || static_cast<int64_t>(row_idx[e]) >= K)
             return fail(SCCS_E_INVAL, "row index out of range at nonzero " + std::to_string(e));

@@ -55,7 +55,7 @@ def _tiny():
 
 @pytest.mark.parametrize("mutate,code", [
     ("unsorted", -2), ("neg_y", -1), ("zero_L", -1), ("nan_L", -1), ("row_oob", -1),
-    ("col_ptr_decreasing", -1), ("col_ptr_start", -1), ("nonbinary", -3),
+    ("col_ptr_decreasing", -1), ("col_ptr_start", -1), ("nonbinary", -3), ("no_events", -1),
 ])
 def test_validation_errors_need_no_gpu(lib, mutate, code):
     pid, y, L, cp, rows = _tiny()
@@ -76,6 +76,8 @@ def test_validation_errors_need_no_gpu(lib, mutate, code):
         cp = np.array([1, 2, 3], np.int64)
     elif mutate == "nonbinary":
         xv = np.array([1.0, 2.0, 1.0])
+    elif mutate == "no_events":
+        y[:] = 0
     with pytest.raises(lib.SCCSError) as ei:
         lib.sccs_create(5, pid, y, L, 2, cp, rows, xv)
     assert ei.value.code == code
