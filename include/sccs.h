@@ -43,7 +43,7 @@ extern "C" {
 #define SCCS_E_NUMERIC (-7)      /* non-finite gradient, Hessian, step or log-posterior */
 #define SCCS_E_BUSY (-8)         /* serving: queue full */
 #define SCCS_E_DUPLICATE (-9)    /* a row appears twice in one column */
-#define SCCS_E_UNSUPPORTED (-10) /* option not available in this build */
+#define SCCS_E_UNSUPPORTED (-10) /* option not supported by this library or device */
 
 /* ---- priors (Eq. 3: Normal(0, s2) or Laplace(0, s2), s2 the variance) ----------------- */
 #define SCCS_PRIOR_NONE 0

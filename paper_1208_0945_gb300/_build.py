@@ -1,7 +1,7 @@
 """Build the in-tree shared library libsccs.so for sm_103a with nvcc (no cmake, no torch).
 
 The two translation units compile in parallel; the library links the CUDA runtime
-statically, so it loads on any host with the driver and needs no library path.
+statically, so it loads on any host with the NVIDIA driver and needs no library path.
 """
 from __future__ import annotations
 

@@ -869,7 +869,7 @@ __device__ void phase_c_global(const DevLayout &d, int s, int j, double r, doubl
 
 // ------------------------------------------------------------------ FP32 column phases
 //
-// FP32 mode (spec precision variant): E in FP32, each segment's numerator a Kahan
+// FP32 mode (the single-precision variant): E in FP32, each segment's numerator a Kahan
 // (compensated) FP32 sum, D_i an FP32 (hi, lo) pair updated with an error-free two-sum, W_i and
 // its two terms in FP32; the per-subject terms then enter the same exact fixed-point sums, so
 // the cross-subject reductions stay exact.  The scalar step stays in FP64.
