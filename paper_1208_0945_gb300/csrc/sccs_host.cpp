@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -62,6 +63,30 @@ void parallel_for(int64_t n, F f) {
         });
     for (auto &th : pool) th.join();
 }
+
+// Split [0, n) into `parts` contiguous chunks (the same cuts for the same n and parts) and run
+// f(chunk, lo, hi) for each on the thread pool.
+template <class F>
+void parallel_chunks(int64_t n, int64_t parts, F f) {
+    parts = std::max<int64_t>(1, parts);
+    parallel_for(parts, [&](int64_t c) { f(c, n * c / parts, n * (c + 1) / parts); });
+}
+
+int64_t host_threads() {
+    const unsigned hw = std::thread::hardware_concurrency();
+    return hw ? static_cast<int64_t>(hw) : 4;
+}
+
+// A host array left uninitialised (every element is written before it is read).
+template <class T>
+struct HostBuf {
+    std::unique_ptr<T[]> p;
+    explicit HostBuf(size_t n) : p(new T[n > 0 ? n : 1]) {}
+    T &operator[](size_t i) { return p[i]; }
+    const T &operator[](size_t i) const { return p[i]; }
+    T *data() { return p.get(); }
+    T *begin() { return p.get(); }
+};
 
 struct DeviceArena {
     sccs_alloc_fn alloc = nullptr;
@@ -255,29 +280,51 @@ int validate_inputs(int64_t K, const int64_t *patient_id, const int32_t *y, cons
 int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const double *Lin, int32_t J,
                  const int64_t *col_ptr, const int32_t *row_idx, int32_t S, int32_t narrow_max, int32_t group_max,
                  HostLayout &hl) {
-    // ---- subjects, n_i, dropping n_i = 0
-    std::vector<int64_t> sub_start;
-    std::vector<int64_t> sub_n;
-    for (int64_t k = 0; k < K; ++k) {
-        if (k == 0 || patient_id[k] != patient_id[k - 1]) {
-            sub_start.push_back(k);
-            sub_n.push_back(0);
-        }
-        sub_n.back() += y[k];
-    }
-    const int64_t nsub = static_cast<int64_t>(sub_start.size());
-    sub_start.push_back(K);
+    // ---- subjects, n_i, dropping n_i = 0 (chunked parallel scans: the subjects' first rows,
+    //      their event counts, then the kept subjects' new positions by prefix sums)
+    const int64_t PK = std::max<int64_t>(1, std::min<int64_t>(8 * host_threads(), K / 65536 + 1));
+    std::vector<int64_t> c_first(static_cast<size_t>(PK), 0);
+    parallel_chunks(K, PK, [&](int64_t c, int64_t lo, int64_t hi) {
+        int64_t n = 0;
+        for (int64_t k = lo; k < hi; ++k) n += (k == 0 || patient_id[k] != patient_id[k - 1]) ? 1 : 0;
+        c_first[c] = n;
+    });
+    std::vector<int64_t> c_off(static_cast<size_t>(PK) + 1, 0);
+    for (int64_t c = 0; c < PK; ++c) c_off[c + 1] = c_off[c] + c_first[c];
+    const int64_t nsub = c_off[PK];
+    std::vector<int64_t> sub_start(static_cast<size_t>(nsub) + 1);
+    parallel_chunks(K, PK, [&](int64_t c, int64_t lo, int64_t hi) {
+        int64_t w = c_off[c];
+        for (int64_t k = lo; k < hi; ++k)
+            if (k == 0 || patient_id[k] != patient_id[k - 1]) sub_start[w++] = k;
+    });
+    sub_start[nsub] = K;
     hl.subjects_in = nsub;
-    std::vector<int32_t> newrow(static_cast<size_t>(K), -1);
-    int64_t Kk = 0, Nk = 0;
-    for (int64_t i = 0; i < nsub; ++i)
-        if (sub_n[i] > 0) {
-            Kk += sub_start[i + 1] - sub_start[i];
-            Nk++;
+    const int64_t PS = std::max<int64_t>(1, std::min<int64_t>(8 * host_threads(), nsub / 16384 + 1));
+    std::vector<int64_t> sub_n(static_cast<size_t>(std::max<int64_t>(nsub, 1)));
+    std::vector<int64_t> ck(static_cast<size_t>(PS), 0), cr(static_cast<size_t>(PS), 0);
+    std::vector<char> c_big(static_cast<size_t>(PS), 0);
+    parallel_chunks(nsub, PS, [&](int64_t c, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            int64_t n = 0;
+            for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) n += y[k];
+            sub_n[i] = n;
+            if (n > 0) {
+                ck[c]++;
+                cr[c] += sub_start[i + 1] - sub_start[i];
+            }
+            if (n >= (int64_t(1) << 31)) c_big[c] = 1;
         }
+    });
+    std::vector<int64_t> ck_off(static_cast<size_t>(PS) + 1, 0), cr_off(static_cast<size_t>(PS) + 1, 0);
+    for (int64_t c = 0; c < PS; ++c) {
+        ck_off[c + 1] = ck_off[c] + ck[c];
+        cr_off[c + 1] = cr_off[c] + cr[c];
+    }
+    const int64_t Nk = ck_off[PS], Kk = cr_off[PS];
     if (Kk >= (int64_t(1) << 31)) return fail(SCCS_E_INVAL, "more than 2^31-1 kept rows");
-    for (int64_t i = 0; i < nsub; ++i)
-        if (sub_n[i] >= (int64_t(1) << 31)) return fail(SCCS_E_INVAL, "n_i exceeds 2^31-1");
+    for (int64_t c = 0; c < PS; ++c)
+        if (c_big[c]) return fail(SCCS_E_INVAL, "n_i exceeds 2^31-1");
     hl.K = Kk;
     hl.N = Nk;
     hl.J = J;
@@ -285,12 +332,16 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     hl.nev.assign(static_cast<size_t>(Nk), 0);
     hl.kept_from.assign(static_cast<size_t>(Nk), 0);
     hl.L.assign(static_cast<size_t>(Kk), 0.0);
-    std::vector<int32_t> row_pat(static_cast<size_t>(Kk));
-    std::vector<int64_t> ykept(static_cast<size_t>(Kk));
-    {
-        int64_t i2 = 0, k2 = 0;
-        for (int64_t i = 0; i < nsub; ++i) {
-            if (sub_n[i] == 0) continue;
+    HostBuf<int32_t> newrow(static_cast<size_t>(K));
+    HostBuf<int32_t> row_pat(static_cast<size_t>(Kk));
+    HostBuf<int64_t> ykept(static_cast<size_t>(Kk));
+    parallel_chunks(nsub, PS, [&](int64_t c, int64_t lo, int64_t hi) {
+        int64_t i2 = ck_off[c], k2 = cr_off[c];
+        for (int64_t i = lo; i < hi; ++i) {
+            if (sub_n[i] == 0) {
+                for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) newrow[k] = -1;
+                continue;
+            }
             hl.pat_ptr[i2] = k2;
             hl.nev[i2] = static_cast<int32_t>(sub_n[i]);
             hl.kept_from[i2] = i;
@@ -303,12 +354,17 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             }
             i2++;
         }
-        hl.pat_ptr[Nk] = Kk;
-    }
+    });
+    hl.pat_ptr[Nk] = Kk;
 
-    // ---- columns: map, drop, sort, reject duplicates; Y'X_j
+    // ---- columns: map, drop, sort, reject duplicates; Y'X_j.  Per-column work is cut into
+    //      tasks of at most kTask nonzeros so that the largest columns do not serialise it.
+    const int64_t nnz_in = col_ptr[J];
     std::vector<int64_t> cptr(static_cast<size_t>(J) + 1, 0);
-    {
+    const bool all_kept = Kk == K;                  // then row k stays row k
+    if (all_kept) {
+        for (int32_t j = 0; j <= J; ++j) cptr[j] = col_ptr[j];
+    } else {
         std::vector<int64_t> cnt(static_cast<size_t>(J), 0);
         parallel_for(J, [&](int64_t j) {
             int64_t c = 0;
@@ -318,59 +374,117 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
         for (int32_t j = 0; j < J; ++j) cptr[j + 1] = cptr[j] + cnt[j];
     }
     hl.nnz = cptr[J];
-    std::vector<int32_t> crow(static_cast<size_t>(hl.nnz));
-    std::vector<int> dup(static_cast<size_t>(J), 0);
-    hl.ytx.assign(static_cast<size_t>(J), 0.0);
-    parallel_for(J, [&](int64_t j) {
-        int64_t w = cptr[j];
-        for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) {
-            int32_t r = newrow[row_idx[e]];
-            if (r >= 0) crow[w++] = r;
-        }
-        std::sort(crow.begin() + cptr[j], crow.begin() + cptr[j + 1]);
-        int64_t t = 0;
-        for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) {
-            if (e > cptr[j] && crow[e] == crow[e - 1]) dup[j] = 1;
-            t += ykept[crow[e]];
-        }
-        hl.ytx[j] = static_cast<double>(t);
+    HostBuf<int32_t> crow(static_cast<size_t>(hl.nnz));
+    if (all_kept) {
+        parallel_chunks(nnz_in, std::max<int64_t>(1, std::min<int64_t>(8 * host_threads(), nnz_in / 65536 + 1)),
+                        [&](int64_t, int64_t lo, int64_t hi) {
+                            std::memcpy(crow.data() + lo, row_idx + lo, sizeof(int32_t) * static_cast<size_t>(hi - lo));
+                        });
+    } else {
+        parallel_for(J, [&](int64_t j) {
+            int64_t w = cptr[j];
+            for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) {
+                int32_t r = newrow[row_idx[e]];
+                if (r >= 0) crow[w++] = r;
+            }
+        });
+    }
+    parallel_for(J, [&](int64_t j) {                 // usually sorted already: a linear check
+        int32_t *b = crow.data() + cptr[j], *e = crow.data() + cptr[j + 1];
+        if (!std::is_sorted(b, e)) std::sort(b, e);
     });
+    // tasks: (column, first nonzero, end); a column's tasks are adjacent and in order
+    constexpr int64_t kTask = 65536;
+    std::vector<int32_t> t_col;
+    std::vector<int64_t> t_lo, t_hi;
     for (int32_t j = 0; j < J; ++j)
-        if (dup[j]) return fail(SCCS_E_DUPLICATE, "a row appears twice in column " + std::to_string(j));
+        for (int64_t lo = cptr[j]; lo < cptr[j + 1]; lo += kTask) {
+            t_col.push_back(j);
+            t_lo.push_back(lo);
+            t_hi.push_back(std::min(lo + kTask, cptr[j + 1]));
+        }
+    const int64_t NT = static_cast<int64_t>(t_col.size());
+    std::vector<int64_t> t_sum(static_cast<size_t>(NT), 0);
+    std::vector<char> t_dup(static_cast<size_t>(NT), 0);
+    // per nonzero, its subject and whether its row has an event: the one pass of random lookups
+    // (the later passes read these in order)
+    HostBuf<int32_t> csub(static_cast<size_t>(hl.nnz));
+    HostBuf<uint8_t> cev(static_cast<size_t>(hl.nnz));
+    parallel_for(NT, [&](int64_t t) {
+        const int64_t c0 = cptr[t_col[t]];
+        int64_t sum = 0;
+        for (int64_t e = t_lo[t]; e < t_hi[t]; ++e) {
+            const int32_t r = crow[e];
+            if (e > c0 && r == crow[e - 1]) t_dup[t] = 1;
+            const int64_t yv = ykept[r];
+            csub[e] = row_pat[r];
+            cev[e] = yv > 0 ? 1 : 0;
+            sum += yv;
+        }
+        t_sum[t] = sum;
+    });
+    hl.ytx.assign(static_cast<size_t>(J), 0.0);
+    {
+        std::vector<int64_t> ytx_i(static_cast<size_t>(J), 0);
+        for (int64_t t = 0; t < NT; ++t) {
+            if (t_dup[t]) return fail(SCCS_E_DUPLICATE, "a row appears twice in column " + std::to_string(t_col[t]));
+            ytx_i[t_col[t]] += t_sum[t];
+        }
+        for (int32_t j = 0; j < J; ++j) hl.ytx[j] = static_cast<double>(ytx_i[j]);   // exact below 2^53
+    }
     for (int32_t j = 0; j < J; ++j) hl.max_col = std::max<int64_t>(hl.max_col, cptr[j + 1] - cptr[j]);
 
     // ---- per column, the subjects with events on its rows and their event sums (what a
-    //      weighted Y'X_j needs, Section 2.5); rows are ascending, so a subject's rows are adjacent
+    //      weighted Y'X_j needs, Section 2.5); rows are ascending, so a subject's rows are adjacent.
+    //      The same tasks, each start moved forward to a subject boundary so that no subject's
+    //      rows are split between two tasks.
     {
-        std::vector<int64_t> npairs(static_cast<size_t>(J), 0);
-        parallel_for(J, [&](int64_t j) {
+        std::vector<int64_t> s_lo2(static_cast<size_t>(NT)), s_hi2(static_cast<size_t>(NT));
+        for (int64_t t = 0; t < NT; ++t) {
+            const int64_t c0 = cptr[t_col[t]], c1 = cptr[t_col[t] + 1];
+            int64_t lo = t_lo[t];
+            while (lo > c0 && lo < c1 && csub[lo] == csub[lo - 1]) ++lo;
+            if (t > 0 && t_col[t - 1] == t_col[t]) lo = std::max(lo, s_lo2[t - 1]);   // monotone
+            s_lo2[t] = lo;
+        }
+        for (int64_t t = 0; t < NT; ++t)
+            s_hi2[t] = (t + 1 < NT && t_col[t + 1] == t_col[t]) ? s_lo2[t + 1] : cptr[t_col[t] + 1];
+        std::vector<int64_t> npairs(static_cast<size_t>(NT), 0);
+        parallel_for(NT, [&](int64_t t) {
             int64_t c = 0;
             int32_t cur = -1;
-            for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) {
-                const int32_t r = crow[e];
-                if (ykept[r] > 0 && row_pat[r] != cur) {
-                    cur = row_pat[r];
+            for (int64_t e = s_lo2[t]; e < s_hi2[t]; ++e) {
+                if (cev[e] && csub[e] != cur) {
+                    cur = csub[e];
                     ++c;
                 }
             }
-            npairs[j] = c;
+            npairs[t] = c;
         });
+        std::vector<int64_t> t_off(static_cast<size_t>(NT) + 1, 0);
+        for (int64_t t = 0; t < NT; ++t) t_off[t + 1] = t_off[t] + npairs[t];
         hl.ycol_ptr.assign(static_cast<size_t>(J) + 1, 0);
-        for (int32_t j = 0; j < J; ++j) hl.ycol_ptr[j + 1] = hl.ycol_ptr[j] + npairs[j];
-        hl.ysub.assign(static_cast<size_t>(hl.ycol_ptr[J]), 0);
-        hl.ycnt.assign(static_cast<size_t>(hl.ycol_ptr[J]), 0);
-        parallel_for(J, [&](int64_t j) {
-            int64_t q = hl.ycol_ptr[j] - 1;
+        {
+            int64_t t = 0;
+            for (int32_t j = 0; j < J; ++j) {
+                hl.ycol_ptr[j] = t_off[t];
+                while (t < NT && t_col[t] == j) ++t;
+            }
+            hl.ycol_ptr[J] = t_off[NT];
+        }
+        hl.ysub.assign(static_cast<size_t>(t_off[NT]), 0);
+        hl.ycnt.assign(static_cast<size_t>(t_off[NT]), 0);
+        parallel_for(NT, [&](int64_t t) {
+            int64_t q = t_off[t] - 1;
             int32_t cur = -1;
-            for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) {
-                const int32_t r = crow[e];
-                if (ykept[r] <= 0) continue;
-                if (row_pat[r] != cur) {
-                    cur = row_pat[r];
+            for (int64_t e = s_lo2[t]; e < s_hi2[t]; ++e) {
+                if (!cev[e]) continue;
+                if (csub[e] != cur) {
+                    cur = csub[e];
                     ++q;
                     hl.ysub[q] = cur;
                 }
-                hl.ycnt[q] += static_cast<int32_t>(ykept[r]);   // <= n_i < 2^31
+                hl.ycnt[q] += static_cast<int32_t>(ykept[crow[e]]);   // <= n_i < 2^31
             }
         });
     }
@@ -386,8 +500,8 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             int64_t c = 0;
             int32_t cur = -1;
             for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e)
-                if (row_pat[crow[e]] != cur) {
-                    cur = row_pat[crow[e]];
+                if (csub[e] != cur) {
+                    cur = csub[e];
                     ++c;
                 }
             nseg[j] = c;
@@ -413,8 +527,8 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             int32_t cur = -1;
             for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) {
                 const int32_t r = crow[e];
-                if (row_pat[r] != cur) {
-                    cur = row_pat[r];
+                if (csub[e] != cur) {
+                    cur = csub[e];
                     ++q;
                     hl.nar_seg[q] = make_int4(cur, 0, static_cast<int>(hl.nar_row.size()), 0);
                 }
@@ -534,23 +648,23 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     const int64_t SJ = static_cast<int64_t>(S) * (J + 1);
     std::vector<int64_t> s_nnz(static_cast<size_t>(SJ), 0), s_seg(static_cast<size_t>(SJ), 0);
     std::vector<int64_t> s_lo(static_cast<size_t>(SJ), 0);
-    parallel_for(S, [&](int64_t s) {
-        const int32_t r0 = static_cast<int32_t>(hl.shard_row[s]), r1 = static_cast<int32_t>(hl.shard_row[s + 1]);
-        for (int32_t j = 0; j < J; ++j) {
-            auto b = crow.begin() + cptr[j], e = crow.begin() + cptr[j + 1];
-            auto lo = std::lower_bound(b, e, r0), hi = std::lower_bound(b, e, r1);
-            const int64_t idx = s * (J + 1) + j;
-            s_lo[idx] = lo - crow.begin();
-            s_nnz[idx] = hi - lo;
+    // one merge of each column's (ascending) rows with the shard boundaries
+    parallel_for(J, [&](int64_t j) {
+        int64_t e = cptr[j];
+        const int64_t e1 = cptr[j + 1];
+        for (int32_t s = 0; s < S; ++s) {
+            const int32_t r1 = static_cast<int32_t>(hl.shard_row[s + 1]);
+            const int64_t lo = e;
             int64_t ns = 0;
             int32_t prev = -1;
-            for (auto it = lo; it != hi; ++it) {
-                const int32_t p = row_pat[*it];
-                if (p != prev) {
+            for (; e < e1 && crow[e] < r1; ++e)
+                if (csub[e] != prev) {
                     ns++;
-                    prev = p;
+                    prev = csub[e];
                 }
-            }
+            const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
+            s_lo[idx] = lo;
+            s_nnz[idx] = e - lo;
             s_seg[idx] = ns;
         }
     });
@@ -584,7 +698,7 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     // ---- pass 2: fill segments (longest first) and rows (diagonal-major per group)
     parallel_for(S, [&](int64_t s) {
         std::vector<int64_t> seg_start;
-        std::vector<int32_t> seg_len, seg_pid, order;
+        std::vector<int32_t> seg_len, seg_pid, order, len_pos;
         for (int32_t j = 0; j < J; ++j) {
             const int64_t idx = s * (J + 1) + j;
             const int64_t lo = s_lo[idx], n = s_nnz[idx];
@@ -593,7 +707,7 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             seg_pid.clear();
             int32_t prev = -1;
             for (int64_t q = lo; q < lo + n; ++q) {
-                const int32_t p = row_pat[crow[q]];
+                const int32_t p = csub[q];
                 if (p != prev) {
                     seg_start.push_back(q);
                     seg_len.push_back(0);
@@ -603,10 +717,18 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
                 seg_len.back()++;
             }
             const int32_t ns = static_cast<int32_t>(seg_len.size());
+            // longest first, ties in subject order: a stable counting sort by length
+            int32_t lmax = 0;
+            for (int32_t i = 0; i < ns; ++i) lmax = std::max(lmax, seg_len[i]);
+            len_pos.assign(static_cast<size_t>(lmax) + 2, 0);
+            for (int32_t i = 0; i < ns; ++i) len_pos[seg_len[i]]++;
+            for (int32_t l = lmax, run = 0; l >= 1; --l) {
+                const int32_t c = len_pos[l];
+                len_pos[l] = run;
+                run += c;
+            }
             order.resize(ns);
-            for (int32_t i = 0; i < ns; ++i) order[i] = i;
-            std::stable_sort(order.begin(), order.end(),
-                             [&](int32_t a, int32_t b) { return seg_len[a] > seg_len[b]; });
+            for (int32_t i = 0; i < ns; ++i) order[len_pos[seg_len[i]]++] = i;
             int64_t rpos = hl.slice_row[idx];
             const int64_t spos = hl.slice_seg[idx], gpos = hl.slice_grp[idx];
             for (int32_t i = 0; i < ns; ++i) hl.segs[spos + i] = int2{seg_pid[order[i]], seg_len[order[i]]};
