@@ -245,6 +245,24 @@ using sccs::kNarrowGroupMax;
 constexpr int32_t kNarrowMinShards = 4;
 
 // Checks everything about the inputs that needs no GPU.
+// The smallest i in [0, n) with bad(i), or -1: chunks in parallel, each stopping at its first.
+template <class F>
+int64_t first_bad(int64_t n, F bad) {
+    if (n <= 0) return -1;
+    const int64_t P = std::max<int64_t>(1, std::min<int64_t>(8 * host_threads(), n / 65536 + 1));
+    std::vector<int64_t> f(static_cast<size_t>(P), -1);
+    parallel_chunks(n, P, [&](int64_t c, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i)
+            if (bad(i)) {
+                f[c] = i;
+                return;
+            }
+    });
+    for (int64_t c = 0; c < P; ++c)
+        if (f[c] >= 0) return f[c];
+    return -1;
+}
+
 int validate_inputs(int64_t K, const int64_t *patient_id, const int32_t *y, const double *Lin, int32_t J,
                     const int64_t *col_ptr, const int32_t *row_idx, const double *x_values) {
     if (K < 0 || J < 0) return fail(SCCS_E_INVAL, "K and J must be >= 0");
@@ -255,25 +273,22 @@ int validate_inputs(int64_t K, const int64_t *patient_id, const int32_t *y, cons
         if (col_ptr[j + 1] < col_ptr[j]) return fail(SCCS_E_INVAL, "col_ptr decreases at column " + std::to_string(j));
     const int64_t nnz_in = col_ptr[J];
     if (nnz_in > 0 && !row_idx) return fail(SCCS_E_INVAL, "row_idx is null");
-    for (int64_t k = 1; k < K; ++k)
-        if (patient_id[k] < patient_id[k - 1])
-            return fail(SCCS_E_UNSORTED, "patient_id decreases at row " + std::to_string(k));
-    bool any_event = false;
-    for (int64_t k = 0; k < K; ++k) {
+    int64_t k = first_bad(K - 1, [&](int64_t i) { return patient_id[i + 1] < patient_id[i]; });
+    if (k >= 0) return fail(SCCS_E_UNSORTED, "patient_id decreases at row " + std::to_string(k + 1));
+    k = first_bad(K, [&](int64_t i) { return y[i] < 0 || !(Lin[i] > 0.0) || !std::isfinite(Lin[i]); });
+    if (k >= 0) {
         if (y[k] < 0) return fail(SCCS_E_INVAL, "negative event count at row " + std::to_string(k));
-        if (!(Lin[k] > 0.0) || !std::isfinite(Lin[k]))
-            return fail(SCCS_E_INVAL, "offset must be positive and finite at row " + std::to_string(k));
-        any_event = any_event || y[k] > 0;
+        return fail(SCCS_E_INVAL, "offset must be positive and finite at row " + std::to_string(k));
+    }
+    k = first_bad(nnz_in, [&](int64_t e) { return row_idx[e] < 0 || static_cast<int64_t>(row_idx[e]) >= K; });
+    if (k >= 0) return fail(SCCS_E_INVAL, "row index out of range at nonzero " + std::to_string(k));
+    if (x_values) {
+        k = first_bad(nnz_in, [&](int64_t e) { return x_values[e] != 1.0; });
+        if (k >= 0) return fail(SCCS_E_NONBINARY, "X value at nonzero " + std::to_string(k) + " is not 1");
     }
     // every n_i = 0: no subject contributes to Eq. 2, so there is nothing to fit
-    if (!any_event) return fail(SCCS_E_INVAL, "no events: every subject has n_i = 0");
-    for (int64_t e = 0; e < nnz_in; ++e)
-        if (row_idx[e] < 0 || static_cast<int64_t>(row_idx[e]) >= K)
-            return fail(SCCS_E_INVAL, "row index out of range at nonzero " + std::to_string(e));
-    if (x_values)
-        for (int64_t e = 0; e < nnz_in; ++e)
-            if (x_values[e] != 1.0)
-                return fail(SCCS_E_NONBINARY, "X value at nonzero " + std::to_string(e) + " is not 1");
+    if (first_bad(K, [&](int64_t i) { return y[i] > 0; }) < 0)
+        return fail(SCCS_E_INVAL, "no events: every subject has n_i = 0");
     return SCCS_OK;
 }
 
