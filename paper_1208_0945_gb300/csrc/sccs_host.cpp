@@ -81,11 +81,19 @@ int64_t host_threads() {
 template <class T>
 struct HostBuf {
     std::unique_ptr<T[]> p;
-    explicit HostBuf(size_t n) : p(new T[n > 0 ? n : 1]) {}
+    size_t n = 0;
+    HostBuf() = default;
+    explicit HostBuf(size_t m) { alloc(m); }
+    void alloc(size_t m) {
+        p.reset(new T[m > 0 ? m : 1]);
+        n = m;
+    }
     T &operator[](size_t i) { return p[i]; }
     const T &operator[](size_t i) const { return p[i]; }
     T *data() { return p.get(); }
+    const T *data() const { return p.get(); }
     T *begin() { return p.get(); }
+    size_t size() const { return n; }
 };
 
 struct DeviceArena {
@@ -214,12 +222,12 @@ struct HostLayout {
     int32_t J = 0, S = 0;
     std::vector<int64_t> pat_ptr;   // N+1
     std::vector<int32_t> nev;       // N
-    std::vector<double> L;          // K
+    HostBuf<double> L;              // K (every element written)
     std::vector<double> ytx;        // J
     std::vector<int64_t> shard_row, shard_pat;
-    std::vector<int32_t> rows;      // JDS rows
-    std::vector<int2> segs;
-    std::vector<int64_t> grp_base;
+    HostBuf<int32_t> rows;          // JDS rows (every element written)
+    HostBuf<int2> segs;
+    HostBuf<int64_t> grp_base;
     std::vector<int64_t> slice_row, slice_seg, slice_grp;  // S*(J+1)
     int64_t stash_stride = 1;
     int64_t estash_stride = 1;
@@ -346,7 +354,7 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     hl.pat_ptr.assign(static_cast<size_t>(Nk) + 1, 0);
     hl.nev.assign(static_cast<size_t>(Nk), 0);
     hl.kept_from.assign(static_cast<size_t>(Nk), 0);
-    hl.L.assign(static_cast<size_t>(Kk), 0.0);
+    hl.L.alloc(static_cast<size_t>(Kk));
     HostBuf<int32_t> newrow(static_cast<size_t>(K));
     HostBuf<int32_t> row_pat(static_cast<size_t>(Kk));
     HostBuf<int64_t> ykept(static_cast<size_t>(Kk));
@@ -706,9 +714,9 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     hl.stash_stride = max_seg;
     hl.estash_stride = max_rows;
     hl.segments = ts;
-    hl.rows.assign(static_cast<size_t>(tr), 0);
-    hl.segs.assign(static_cast<size_t>(ts), int2{0, 0});
-    hl.grp_base.assign(static_cast<size_t>(tg), 0);
+    hl.rows.alloc(static_cast<size_t>(tr));
+    hl.segs.alloc(static_cast<size_t>(ts));
+    hl.grp_base.alloc(static_cast<size_t>(tg));
 
     // ---- pass 2: fill segments (longest first) and rows (diagonal-major per group)
     parallel_for(S, [&](int64_t s) {
