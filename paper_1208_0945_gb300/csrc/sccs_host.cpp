@@ -356,8 +356,8 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     hl.kept_from.assign(static_cast<size_t>(Nk), 0);
     hl.L.alloc(static_cast<size_t>(Kk));
     HostBuf<int32_t> newrow(static_cast<size_t>(K));
-    HostBuf<int32_t> row_pat(static_cast<size_t>(Kk));
-    HostBuf<int64_t> ykept(static_cast<size_t>(Kk));
+    // per kept row, its subject (high word) and its event count (low word): one lookup for both
+    HostBuf<uint64_t> rowinfo(static_cast<size_t>(Kk));
     parallel_chunks(nsub, PS, [&](int64_t c, int64_t lo, int64_t hi) {
         int64_t i2 = ck_off[c], k2 = cr_off[c];
         for (int64_t i = lo; i < hi; ++i) {
@@ -370,9 +370,8 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             hl.kept_from[i2] = i;
             for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) {
                 newrow[k] = static_cast<int32_t>(k2);
-                row_pat[k2] = static_cast<int32_t>(i2);
+                rowinfo[k2] = (static_cast<uint64_t>(i2) << 32) | static_cast<uint32_t>(y[k]);
                 hl.L[k2] = Lin[k];
-                ykept[k2] = y[k];
                 k2++;
             }
             i2++;
@@ -429,19 +428,20 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     const int64_t NT = static_cast<int64_t>(t_col.size());
     std::vector<int64_t> t_sum(static_cast<size_t>(NT), 0);
     std::vector<char> t_dup(static_cast<size_t>(NT), 0);
-    // per nonzero, its subject and whether its row has an event: the one pass of random lookups
+    // per nonzero, its subject and its row's event count: the one pass of random lookups
     // (the later passes read these in order)
     HostBuf<int32_t> csub(static_cast<size_t>(hl.nnz));
-    HostBuf<uint8_t> cev(static_cast<size_t>(hl.nnz));
+    HostBuf<int32_t> cy(static_cast<size_t>(hl.nnz));
     parallel_for(NT, [&](int64_t t) {
         const int64_t c0 = cptr[t_col[t]];
         int64_t sum = 0;
         for (int64_t e = t_lo[t]; e < t_hi[t]; ++e) {
             const int32_t r = crow[e];
             if (e > c0 && r == crow[e - 1]) t_dup[t] = 1;
-            const int64_t yv = ykept[r];
-            csub[e] = row_pat[r];
-            cev[e] = yv > 0 ? 1 : 0;
+            const uint64_t ri = rowinfo[r];
+            const int32_t yv = static_cast<int32_t>(ri & 0xffffffffu);
+            csub[e] = static_cast<int32_t>(ri >> 32);
+            cy[e] = yv;
             sum += yv;
         }
         t_sum[t] = sum;
@@ -477,7 +477,7 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             int64_t c = 0;
             int32_t cur = -1;
             for (int64_t e = s_lo2[t]; e < s_hi2[t]; ++e) {
-                if (cev[e] && csub[e] != cur) {
+                if (cy[e] > 0 && csub[e] != cur) {
                     cur = csub[e];
                     ++c;
                 }
@@ -501,13 +501,13 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             int64_t q = t_off[t] - 1;
             int32_t cur = -1;
             for (int64_t e = s_lo2[t]; e < s_hi2[t]; ++e) {
-                if (!cev[e]) continue;
+                if (cy[e] <= 0) continue;
                 if (csub[e] != cur) {
                     cur = csub[e];
                     ++q;
                     hl.ysub[q] = cur;
                 }
-                hl.ycnt[q] += static_cast<int32_t>(ykept[crow[e]]);   // <= n_i < 2^31
+                hl.ycnt[q] += cy[e];   // <= n_i < 2^31
             }
         });
     }
