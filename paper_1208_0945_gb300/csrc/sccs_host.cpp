@@ -236,7 +236,7 @@ struct HostLayout {
     int64_t subjects_in = 0;
     std::vector<int64_t> kept_from;   // N: input subject of each kept subject
     std::vector<int64_t> ycol_ptr;    // J+1: per column, (subject, sum of y) pairs with events
-    std::vector<int32_t> ysub, ycnt;
+    HostBuf<int32_t> ysub, ycnt;      // every element written
     // narrow columns (whole column on one CTA)
     int32_t narrow_count = 0, first_wide = -1;
     std::vector<uint8_t> narrow;      // J
@@ -495,20 +495,23 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
             }
             hl.ycol_ptr[J] = t_off[NT];
         }
-        hl.ysub.assign(static_cast<size_t>(t_off[NT]), 0);
-        hl.ycnt.assign(static_cast<size_t>(t_off[NT]), 0);
+        hl.ysub.alloc(static_cast<size_t>(t_off[NT]));
+        hl.ycnt.alloc(static_cast<size_t>(t_off[NT]));
         parallel_for(NT, [&](int64_t t) {
             int64_t q = t_off[t] - 1;
-            int32_t cur = -1;
+            int32_t cur = -1, acc = 0;                  // a pair's sum <= n_i < 2^31
             for (int64_t e = s_lo2[t]; e < s_hi2[t]; ++e) {
                 if (cy[e] <= 0) continue;
                 if (csub[e] != cur) {
+                    if (q >= t_off[t]) hl.ycnt[q] = acc;
                     cur = csub[e];
                     ++q;
                     hl.ysub[q] = cur;
+                    acc = 0;
                 }
-                hl.ycnt[q] += cy[e];   // <= n_i < 2^31
+                acc += cy[e];
             }
+            if (q >= t_off[t]) hl.ycnt[q] = acc;
         });
     }
 
