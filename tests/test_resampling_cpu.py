@@ -43,3 +43,42 @@ def test_interval_summary(R):
         R.interval_summary(b, level=1.0)
     with pytest.raises(ValueError):
         R.interval_summary(np.zeros(3))
+
+
+class _FakeServer:
+    """Records submissions; results carry the request's own index, completed in any order."""
+
+    def __init__(self):
+        self.outstanding, self.max_outstanding, self.closed = set(), 0, False
+        self.next = 0
+
+    def submit(self, model, alt=None, **kw):
+        t = self.next
+        self.next += 1
+        self.outstanding.add(t)
+        self.max_outstanding = max(self.max_outstanding, len(self.outstanding))
+        self.kw = kw
+        return t
+
+    def wait(self, t):
+        self.outstanding.discard(t)
+        return {"status": 0, "ticket": t, "beta": np.array([float(t)]), "cycles": 1, "logpost": 0.0,
+                "heldout_loglik": -float(t)}
+
+    def close(self):
+        self.closed = True
+
+
+def test_submission_window_and_result_order(R):
+    srv = _FakeServer()
+    reqs = [dict(variance=float(i)) for i in range(10)]
+    res = R._run(None, reqs, srv, None, 4, window=3)
+    assert [r["ticket"] for r in res] == list(range(10))     # results in request order
+    assert srv.max_outstanding <= 3 and not srv.outstanding
+    assert not srv.closed                                      # a caller's server stays open
+
+
+def test_failed_fits_are_reported(R):
+    with pytest.raises(RuntimeError):
+        R._check_done([{"status": 0}, {"status": -7}], "bootstrap")
+    R._check_done([{"status": 0}, {"status": 1}], "bootstrap")   # not converged is kept
