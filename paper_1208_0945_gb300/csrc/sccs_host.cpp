@@ -355,21 +355,24 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
     hl.nev.assign(static_cast<size_t>(Nk), 0);
     hl.kept_from.assign(static_cast<size_t>(Nk), 0);
     hl.L.alloc(static_cast<size_t>(Kk));
-    HostBuf<int32_t> newrow(static_cast<size_t>(K));
+    HostBuf<int32_t> newrow;                         // input row -> kept row, when subjects are dropped
+    const bool map_rows = Kk < K;
+    if (map_rows) newrow.alloc(static_cast<size_t>(K));
     // per kept row, its subject (high word) and its event count (low word): one lookup for both
     HostBuf<uint64_t> rowinfo(static_cast<size_t>(Kk));
     parallel_chunks(nsub, PS, [&](int64_t c, int64_t lo, int64_t hi) {
         int64_t i2 = ck_off[c], k2 = cr_off[c];
         for (int64_t i = lo; i < hi; ++i) {
             if (sub_n[i] == 0) {
-                for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) newrow[k] = -1;
+                if (map_rows)
+                    for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) newrow[k] = -1;
                 continue;
             }
             hl.pat_ptr[i2] = k2;
             hl.nev[i2] = static_cast<int32_t>(sub_n[i]);
             hl.kept_from[i2] = i;
             for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) {
-                newrow[k] = static_cast<int32_t>(k2);
+                if (map_rows) newrow[k] = static_cast<int32_t>(k2);
                 rowinfo[k2] = (static_cast<uint64_t>(i2) << 32) | static_cast<uint32_t>(y[k]);
                 hl.L[k2] = Lin[k];
                 k2++;
@@ -396,25 +399,43 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
         for (int32_t j = 0; j < J; ++j) cptr[j + 1] = cptr[j] + cnt[j];
     }
     hl.nnz = cptr[J];
-    HostBuf<int32_t> crow(static_cast<size_t>(hl.nnz));
-    if (all_kept) {
-        parallel_chunks(nnz_in, std::max<int64_t>(1, std::min<int64_t>(8 * host_threads(), nnz_in / 65536 + 1)),
-                        [&](int64_t, int64_t lo, int64_t hi) {
-                            std::memcpy(crow.data() + lo, row_idx + lo, sizeof(int32_t) * static_cast<size_t>(hi - lo));
-                        });
-    } else {
-        parallel_for(J, [&](int64_t j) {
-            int64_t w = cptr[j];
-            for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) {
-                int32_t r = newrow[row_idx[e]];
-                if (r >= 0) crow[w++] = r;
+    // the kept rows of each column, ascending: the input itself when nothing is dropped and every
+    // column is ascending already (the usual case), else a mapped and sorted copy
+    HostBuf<int32_t> crow_own;
+    const int32_t *crow = row_idx;
+    {
+        std::vector<char> unsorted(static_cast<size_t>(J), 0);
+        if (all_kept)
+            parallel_for(J, [&](int64_t j) {
+                unsorted[j] = std::is_sorted(row_idx + cptr[j], row_idx + cptr[j + 1]) ? 0 : 1;
+            });
+        const bool any_unsorted = std::find(unsorted.begin(), unsorted.end(), 1) != unsorted.end();
+        if (!all_kept || any_unsorted) {
+            crow_own.alloc(static_cast<size_t>(hl.nnz));
+            if (all_kept) {
+                parallel_chunks(nnz_in, std::max<int64_t>(1, std::min<int64_t>(8 * host_threads(), nnz_in / 65536 + 1)),
+                                [&](int64_t, int64_t lo, int64_t hi) {
+                                    std::memcpy(crow_own.data() + lo, row_idx + lo,
+                                                sizeof(int32_t) * static_cast<size_t>(hi - lo));
+                                });
+            } else {
+                parallel_for(J, [&](int64_t j) {
+                    int64_t w = cptr[j];
+                    for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) {
+                        int32_t r = newrow[row_idx[e]];
+                        if (r >= 0) crow_own[w++] = r;
+                    }
+                });
             }
-        });
+            parallel_for(J, [&](int64_t j) {
+                int32_t *b = crow_own.data() + cptr[j], *e = crow_own.data() + cptr[j + 1];
+                if (!all_kept || unsorted[j]) {
+                    if (!std::is_sorted(b, e)) std::sort(b, e);
+                }
+            });
+            crow = crow_own.data();
+        }
     }
-    parallel_for(J, [&](int64_t j) {                 // usually sorted already: a linear check
-        int32_t *b = crow.data() + cptr[j], *e = crow.data() + cptr[j + 1];
-        if (!std::is_sorted(b, e)) std::sort(b, e);
-    });
     // tasks: (column, first nonzero, end); a column's tasks are adjacent and in order
     constexpr int64_t kTask = 65536;
     std::vector<int32_t> t_col;
@@ -631,7 +652,7 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
                 int w = 0;
                 if (run_start) {
                     if (g > 0) {
-                        const int32_t *b = crow.data() + cptr[g - 1], *e = crow.data() + cptr[g];
+                        const int32_t *b = crow + cptr[g - 1], *e = crow + cptr[g];
                         const int32_t *f = std::lower_bound(b, e, static_cast<int32_t>(hl.pat_ptr[i]));
                         if (f != e && *f < hl.pat_ptr[i + 1]) w = sccs::kNarrowAfterWide;
                     }
