@@ -1,0 +1,173 @@
+// Host-side check of the whole layout the library's host code builds (sccs_host.cpp, compiled
+// into this program), against a brute-force construction from the definitions: the kept
+// subjects (n_i > 0, input order) and their rows, each column's kept rows and Y'X_j, the
+// per-column (subject, event sum) pairs, and every (shard, column) slice -- its rows, its subject
+// segments longest first (ties in subject order), the rows of each 32-segment group diagonal by
+// diagonal, the group bases -- and the stash strides.  The data has subjects without events and
+// columns in shuffled order, or neither, so both paths of the host code run.  Exit status 0
+// when all hold.  Test infrastructure only.
+#include "../../paper_1208_0945_gb300/csrc/sccs_host.cpp"
+#include <algorithm>
+#include <cstdio>
+#include <map>
+#include <random>
+
+static long long g_bad = 0;
+#define CHECK(cond, ...)                      \
+    do {                                      \
+        if (!(cond)) {                        \
+            if (g_bad < 8) printf(__VA_ARGS__); \
+            ++g_bad;                          \
+        }                                     \
+    } while (0)
+
+int main(int argc, char **argv) {
+    const int nsub = argc > 1 ? atoi(argv[1]) : 8000;
+    const int J = argc > 2 ? atoi(argv[2]) : 120;
+    const unsigned seed = argc > 3 ? static_cast<unsigned>(atoi(argv[3])) : 5u;
+    const int S = argc > 4 ? atoi(argv[4]) : 7;
+    const bool messy = argc > 5 ? atoi(argv[5]) != 0 : true;   // dropped subjects, shuffled columns
+    std::mt19937_64 rng(seed);
+    std::vector<int64_t> pid;
+    std::vector<int32_t> y;
+    std::vector<double> L;
+    for (int i = 0; i < nsub; ++i) {
+        const int k = 1 + static_cast<int>(rng() % 14);
+        const bool events = !messy || rng() % 4 != 0;
+        for (int t = 0; t < k; ++t) {
+            pid.push_back(3 * static_cast<int64_t>(i) + 1);          // ids need not be dense
+            y.push_back(events ? (t == 0 ? 1 + static_cast<int>(rng() % 3) : static_cast<int>(rng() % 2)) : 0);
+            L.push_back(1.0 + static_cast<double>(rng() % 365));
+        }
+    }
+    const int64_t K = static_cast<int64_t>(pid.size());
+    std::vector<int64_t> cp(J + 1, 0);
+    std::vector<int32_t> ri;
+    for (int j = 0; j < J; ++j) {
+        int64_t n = j % 11 == 0 ? K / 4 : static_cast<int64_t>(rng() % 300);
+        if (j % 29 == 5) n = 0;                                         // empty columns
+        std::vector<char> used(static_cast<size_t>(K), 0);
+        std::vector<int32_t> col;
+        while (static_cast<int64_t>(col.size()) < n) {
+            const int32_t r = static_cast<int32_t>(rng() % K);
+            if (!used[r]) {
+                used[r] = 1;
+                col.push_back(r);
+            }
+        }
+        if (messy) std::shuffle(col.begin(), col.end(), rng);
+        else std::sort(col.begin(), col.end());
+        for (int32_t r : col) ri.push_back(r);
+        cp[j + 1] = static_cast<int64_t>(ri.size());
+    }
+    HostLayout hl;
+    if (build_layout(K, pid.data(), y.data(), L.data(), J, cp.data(), ri.data(), S, 1024, 8, hl)) {
+        printf("build_layout failed: %s\n", g_last_error.c_str());
+        return 2;
+    }
+
+    // ---- subjects and rows, from the definitions
+    std::vector<int64_t> first;                      // input subjects' first rows
+    for (int64_t k = 0; k < K; ++k)
+        if (k == 0 || pid[k] != pid[k - 1]) first.push_back(k);
+    first.push_back(K);
+    const int64_t nin = static_cast<int64_t>(first.size()) - 1;
+    std::vector<int64_t> kept_row(static_cast<size_t>(K), -1);   // input row -> kept row
+    std::vector<int32_t> kept_sub;                               // kept row -> kept subject
+    int64_t Nk = 0, Kk = 0;
+    CHECK(hl.subjects_in == nin, "subjects_in %lld != %lld\n", (long long)hl.subjects_in, (long long)nin);
+    for (int64_t i = 0; i < nin; ++i) {
+        int64_t n = 0;
+        for (int64_t k = first[i]; k < first[i + 1]; ++k) n += y[k];
+        if (n == 0) continue;
+        CHECK(hl.pat_ptr[Nk] == Kk, "pat_ptr[%lld]\n", (long long)Nk);
+        CHECK(hl.nev[Nk] == n, "nev[%lld]\n", (long long)Nk);
+        CHECK(hl.kept_from[Nk] == i, "kept_from[%lld]\n", (long long)Nk);
+        for (int64_t k = first[i]; k < first[i + 1]; ++k) {
+            CHECK(hl.L[Kk] == L[k], "L[%lld]\n", (long long)Kk);
+            kept_row[k] = Kk++;
+            kept_sub.push_back(static_cast<int32_t>(Nk));
+        }
+        ++Nk;
+    }
+    CHECK(hl.N == Nk && hl.K == Kk, "N/K %lld/%lld != %lld/%lld\n", (long long)hl.N, (long long)hl.K, (long long)Nk,
+          (long long)Kk);
+    CHECK(hl.pat_ptr[Nk] == Kk, "pat_ptr end\n");
+    std::vector<int32_t> ykept(static_cast<size_t>(Kk));
+    for (int64_t k = 0; k < K; ++k)
+        if (kept_row[k] >= 0) ykept[kept_row[k]] = y[k];
+
+    // ---- columns: kept rows ascending, Y'X_j, event pairs
+    std::vector<std::vector<int32_t>> colrows(static_cast<size_t>(J));
+    int64_t nnz = 0;
+    for (int j = 0; j < J; ++j) {
+        for (int64_t e = cp[j]; e < cp[j + 1]; ++e)
+            if (kept_row[ri[e]] >= 0) colrows[j].push_back(static_cast<int32_t>(kept_row[ri[e]]));
+        std::sort(colrows[j].begin(), colrows[j].end());
+        nnz += static_cast<int64_t>(colrows[j].size());
+        int64_t ytx = 0;
+        std::map<int32_t, int32_t> pairs;
+        for (int32_t r : colrows[j]) {
+            ytx += ykept[r];
+            if (ykept[r] > 0) pairs[kept_sub[r]] += ykept[r];
+        }
+        CHECK(hl.ytx[j] == static_cast<double>(ytx), "ytx[%d]\n", j);
+        CHECK(hl.ycol_ptr[j + 1] - hl.ycol_ptr[j] == static_cast<int64_t>(pairs.size()), "pairs count col %d\n", j);
+        int64_t q = hl.ycol_ptr[j];
+        for (const auto &pr : pairs) {
+            CHECK(hl.ysub[q] == pr.first && hl.ycnt[q] == pr.second, "pair col %d\n", j);
+            ++q;
+        }
+    }
+    CHECK(hl.nnz == nnz, "nnz\n");
+
+    // ---- slices
+    int64_t max_seg = 1, max_rows = 1;
+    for (int s = 0; s < S; ++s) {
+        const int64_t r0 = hl.shard_row[s], r1 = hl.shard_row[s + 1];
+        CHECK(r0 == hl.pat_ptr[hl.shard_pat[s]], "shard_row[%d]\n", s);
+        for (int j = 0; j < J; ++j) {
+            const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
+            std::vector<int32_t> rows;
+            for (int32_t r : colrows[j])
+                if (r >= r0 && r < r1) rows.push_back(r);
+            // subjects in ascending order with their rows (ascending)
+            std::vector<std::pair<int32_t, std::vector<int32_t>>> segs;
+            for (int32_t r : rows) {
+                if (segs.empty() || segs.back().first != kept_sub[r]) segs.push_back({kept_sub[r], {}});
+                segs.back().second.push_back(r);
+            }
+            std::stable_sort(segs.begin(), segs.end(),
+                             [](const auto &a, const auto &b) { return a.second.size() > b.second.size(); });
+            const int64_t nr = hl.slice_row[idx + 1] - hl.slice_row[idx];
+            const int64_t ns = hl.slice_seg[idx + 1] - hl.slice_seg[idx];
+            CHECK(nr == static_cast<int64_t>(rows.size()), "slice rows s%d j%d\n", s, j);
+            CHECK(ns == static_cast<int64_t>(segs.size()), "slice segs s%d j%d\n", s, j);
+            CHECK(hl.slice_grp[idx + 1] - hl.slice_grp[idx] == (ns + 31) / 32, "slice groups s%d j%d\n", s, j);
+            max_seg = std::max<int64_t>(max_seg, ns);
+            max_rows = std::max<int64_t>(max_rows, nr);
+            if (nr != static_cast<int64_t>(rows.size()) || ns != static_cast<int64_t>(segs.size())) continue;
+            for (int64_t i = 0; i < ns; ++i) {
+                const int2 sg = hl.segs[hl.slice_seg[idx] + i];
+                CHECK(sg.x == segs[i].first && sg.y == static_cast<int>(segs[i].second.size()), "seg s%d j%d i%lld\n", s,
+                      j, (long long)i);
+            }
+            int64_t pos = hl.slice_row[idx];
+            for (int64_t g = 0; g * 32 < ns; ++g) {
+                CHECK(hl.grp_base[hl.slice_grp[idx] + g] == pos, "grp_base s%d j%d g%lld\n", s, j, (long long)g);
+                const int64_t a = 32 * g, b = std::min<int64_t>(ns, a + 32);
+                const size_t maxlen = segs[a].second.size();
+                for (size_t t = 0; t < maxlen; ++t)
+                    for (int64_t l = a; l < b; ++l)
+                        if (segs[l].second.size() > t) {
+                            CHECK(hl.rows[pos] == segs[l].second[t], "row s%d j%d pos%lld\n", s, j, (long long)pos);
+                            ++pos;
+                        }
+            }
+        }
+    }
+    CHECK(hl.stash_stride == max_seg && hl.estash_stride == max_rows, "stash strides\n");
+    printf("subjects %lld kept %lld rows %lld nnz %lld shards %d columns %d mismatches %lld\n", (long long)nin,
+           (long long)Nk, (long long)Kk, (long long)nnz, S, J, g_bad);
+    return g_bad ? 1 : 0;
+}

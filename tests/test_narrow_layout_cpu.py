@@ -1,4 +1,4 @@
-"""Host logic of the narrow-column layout (no GPU): groups of consecutive narrow columns touch
+"""Host logic of the device layout (no GPU).  Narrow columns: groups of consecutive narrow columns touch
 pairwise disjoint subjects and fit half the shared buffers, and each segment's mark names the
 one earlier step that can change its subject (the GPU re-gathers a segment exactly when that
 step was not zero).  The check compiles the library's host source into a small C++ program and
@@ -44,3 +44,34 @@ def test_narrow_groups_and_marks(checker, nsub, J, seed, S, gmax):
     assert int(stats["after_wide"]) > 0
     if gmax > 1:
         assert int(stats["after_prev"]) > 0 and int(stats["multi"]) > 0
+
+
+SLICE_SRC = os.path.join(ROOT, "tests", "native", "slice_layout_check.cpp")
+
+
+@pytest.fixture(scope="module")
+def slice_checker(tmp_path_factory):
+    nvcc = os.environ.get("NVCC") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc")
+                                      else shutil.which("nvcc"))
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    import __graft_entry__
+    lib = __graft_entry__._build_module().build()
+    exe = str(tmp_path_factory.mktemp("slices") / "slice_layout_check")
+    cmd = [nvcc, "-std=c++17", "-O2", "-I" + os.path.join(ROOT, "include"), SLICE_SRC, lib,
+           "-Xlinker", "-rpath=" + os.path.dirname(lib), "-o", exe, "-lpthread"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return exe
+
+
+@pytest.mark.parametrize("nsub,J,seed,S,messy", [(8000, 120, 5, 7, 1), (8000, 120, 6, 7, 0), (3000, 60, 7, 1, 1),
+                                                  (20000, 90, 8, 33, 1), (500, 40, 9, 4, 0)])
+def test_slice_layout_against_brute_force(slice_checker, nsub, J, seed, S, messy):
+    """The whole host layout -- kept subjects and rows, per-column kept rows, Y'X_j and event
+    pairs, every (shard, column) slice's segments, diagonal-major rows and group bases -- against
+    a brute-force construction, with dropped subjects and shuffled columns (messy) or without."""
+    r = subprocess.run([slice_checker, str(nsub), str(J), str(seed), str(S), str(messy)], capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "mismatches 0" in r.stdout
