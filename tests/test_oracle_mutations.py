@@ -33,6 +33,17 @@ MUTATIONS = [
     # the evaluation straight from the input arrays
     ("raw_eval_unweighted_W", "nW += (double)n[i] * Wi;", "nW += Wi;"),
     ("raw_eval_counts_zero_event_rows", "if (n[sub[k]] > 0) ytx += y[k];", "ytx += y[k] + (n[sub[k]] == 0);"),
+    # the Genkin trust region and convergence rule (Section 2.2)
+    ("trust_update_factor", "double t2 = 2.0 * fabs(db), th = 0.5 * (*trust);",
+     "double t2 = fabs(db), th = 0.5 * (*trust);"),
+    ("trust_initial_radius", "beta[j] = beta0 ? beta0[j] : 0.0; trust[j] = 1.0;",
+     "beta[j] = beta0 ? beta0[j] : 0.0; trust[j] = 2.0;"),
+    ("genkin_drops_one_plus", "conv = dsum / (1.0 + asum);", "conv = dsum / asum;"),
+    ("genkin_previous_cycle_not_saved",
+     "if (tol_mode == ORC_TOL_GENKIN_XBETA) memcpy(xb_prev, xb, (size_t)K * sizeof(double));",
+     "if (tol_mode == ORC_TOL_GENKIN_XBETA && t == 1) memcpy(xb_prev, xb, (size_t)K * sizeof(double));"),
+    # q = 0 (R5): a nonzero Laplace coefficient with |g| <= lambda returns to 0
+    ("laplace_q_zero_keeps_beta", "if (fabs(g) <= lambda) dv = -bj;", "if (fabs(g) <= lambda) dv = 0.0;"),
 ]
 
 PIN_CASES = [
@@ -46,6 +57,9 @@ PIN_CASES = [
     (wpins.test_weighted_fit_equals_replicated_dataset, dict(seed=0, prior="normal", var=0.5)),
     (wpins.test_fold_fit_and_heldout_loglik, dict(seed=0)),
     (pins.test_raw_eval_equals_canonical_oracle, dict(seed=0)),
+    (pins.test_golden_trust_region_trajectory, {}),
+    (pins.test_genkin_xbeta_stopping_rule, dict(seed=2)),
+    (pins.test_column_covering_whole_subjects_q_zero, {}),
 ]
 
 

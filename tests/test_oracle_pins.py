@@ -162,6 +162,77 @@ def test_golden_one_covariate_closed_forms():
             assert r["beta"][0] == 0.0  # the soft threshold keeps it exactly at zero
 
 
+def test_golden_trust_region_trajectory():
+    """The Genkin trust region (R1): on a one-drug example whose Newton step has a closed form,
+    the first two steps are cut to the radius (b = 1, then b = 3) and the radius update
+    T <- max(2|db|, T/2) decides the second cut; the later cycles follow the closed form."""
+    d, expected = read_golden(os.path.join(HERE, "golden", "one_covariate_trust_trajectory.txt"))
+    p = P(d)
+    for _tag, cycle, b_expected in expected:
+        r = p.fit(prior="none", fixed_cycles=int(cycle))
+        assert r["cycles"] == int(cycle)
+        if b_expected in (1.0, 3.0):
+            assert r["beta"][0] == b_expected, cycle        # a clamp to the radius is exact
+        else:
+            assert r["beta"][0] == pytest.approx(b_expected, rel=0, abs=1e-12), cycle
+    # the limit is the closed-form MLE log(A / (n - A)) - log r = log 100
+    r = p.fit(prior="none", tol_mode="abs_logpost", tol=1e-15, max_cycles=100)
+    assert r["beta"][0] == pytest.approx(math.log(100.0), abs=1e-12)
+
+
+@pytest.mark.parametrize("seed", [2, 5])
+def test_genkin_xbeta_stopping_rule(seed):
+    """Genkin's X-beta rule (R4, after the Section 2.2 criterion): a fit stops after the first
+    cycle t with sum_k |(Xb_t - Xb_{t-1})_k| / (1 + sum_k |(Xb_t)_k|) < tol.  The statistic is
+    computed here from a dense X and the oracle's beta after each cycle, and the tolerance is
+    placed where the rule without the 1 + in the denominator would stop one cycle later."""
+    d = random_tiny(seed, n_patients=8, max_eras=3, J=3, density=0.3, beta_scale=0.3)
+    p = P(d)
+    X = to_dense(d)
+    T = 6
+    betas = [np.zeros(d.J)] + [p.fit(prior="normal", variance=1.0, fixed_cycles=t)["beta"] for t in range(1, T + 1)]
+    xb = [X @ b for b in betas]
+    stat = [None] + [np.abs(xb[t] - xb[t - 1]).sum() / (1.0 + np.abs(xb[t]).sum()) for t in range(1, T + 1)]
+    asum = [None] + [np.abs(xb[t]).sum() for t in range(1, T + 1)]
+    t_star = 3
+    assert stat[t_star] > 0 and stat[t_star - 1] > stat[t_star] * 1.5, stat
+    tol = stat[t_star] * (1.0 + 0.5 / asum[t_star])
+    # the rule without the 1 + would not stop at t_star
+    assert np.abs(xb[t_star] - xb[t_star - 1]).sum() / asum[t_star] > tol
+    r = p.fit(prior="normal", variance=1.0, tol_mode="genkin_xbeta", tol=tol, max_cycles=50)
+    assert r["status"] == oracle.OK and r["cycles"] == t_star, (r["cycles"], stat, tol)
+    np.testing.assert_array_equal(r["beta"], betas[t_star])
+
+
+def test_column_covering_whole_subjects_q_zero():
+    """R5: a column holding every era of each subject it touches has W_i = 1 for those subjects,
+    so g_j = Y'X_j - sum n_i = 0 and h_j = 0 exactly (Eqs. 7-9).  The 1-D optimum of the
+    penalised objective along that coordinate is then b_j = 0: the Laplace step returns to 0
+    (cut to the trust radius 1 first when |b_j| > 1), the Normal step -b_j (s2/s2) lands on 0
+    up to rounding, and without a prior the step is 0."""
+    pid = [0, 0, 0, 1, 1, 2, 2, 2, 3, 3]
+    L = [30.0, 40.0, 50.0, 20.0, 60.0, 10.0, 70.0, 90.0, 25.0, 35.0]
+    y = [1, 0, 2, 1, 1, 0, 1, 1, 2, 0]
+    X = np.zeros((10, 2))
+    X[[0, 1, 2, 5, 6, 7], 0] = 1.0          # subjects 0 and 2, all their eras
+    X[[1, 3, 8], 1] = 1.0
+    d = from_dense(pid, y, L, X)
+    p = P(d)
+    g, h = p.grad_hess(0, np.array([0.4, -0.3]))
+    assert g == 0.0 and h == 0.0
+    # Laplace, |b| > radius: cut to the radius, then to 0
+    r = p.fit(prior="laplace", variance=0.5, beta0=np.array([1.7, 0.0]), fixed_cycles=1)
+    assert r["beta"][0] == pytest.approx(0.7, abs=1e-15)
+    r = p.fit(prior="laplace", variance=0.5, beta0=np.array([1.7, 0.0]), fixed_cycles=2)
+    assert r["beta"][0] == 0.0
+    r = p.fit(prior="laplace", variance=0.5, beta0=np.array([-0.6, 0.0]), fixed_cycles=1)
+    assert r["beta"][0] == 0.0
+    r = p.fit(prior="normal", variance=0.3, beta0=np.array([0.6, 0.0]), fixed_cycles=1)
+    assert abs(r["beta"][0]) < 1e-15
+    r = p.fit(prior="none", beta0=np.array([0.6, 0.0]), fixed_cycles=1)
+    assert r["beta"][0] == 0.6 and not r["warning"]
+
+
 @pytest.mark.parametrize("r_ratio", [0.1, 0.5, 2.0])
 def test_one_covariate_closed_form_random(r_ratio):
     """b_hat = log(A / (n - A)) - log r when every subject has exposed/unexposed time ratio r."""
