@@ -296,20 +296,31 @@ typedef struct sccs_server_stats {
 } sccs_server_stats;
 
 /*
- * sccs_server_create -- start a fit server on one device.  A scheduler thread admits queued
- * requests in arrival order as soon as their per-fit device state fits the HBM budget and their
- * dataset's CTA team fits next to the fits already running; each admitted fit runs (Algorithm 1,
- * as sccs_fit) on a stream of its own, so fits that arrive while others run overlap with them.
- * A fit gives the same result alone or in the mix.  Errors: SCCS_E_INVAL, SCCS_E_CUDA.
+ * sccs_server_create -- start a fit server on one device.  Section 2.5 turns one analysis into
+ * many independent MAP fits of the same data: cross-validation fits every candidate prior
+ * variance on each training portion (10 folds) and scores the held-out portion's predictive
+ * log-likelihood, and the bootstrap refits resampled subjects (200 replicates); across outcomes
+ * the same drugs are fitted again for every outcome of interest.  The server runs such fits as
+ * they are requested: a scheduler thread admits queued requests in arrival order as soon as
+ * their per-fit device state fits the HBM budget and their dataset's CTA team fits next to the
+ * fits already running; each admitted fit runs (Algorithm 1, as sccs_fit) on a stream of its
+ * own, so fits that arrive while others run overlap with them (continuous batching).  A fit
+ * gives the same result alone or in the mix.  Errors: SCCS_E_INVAL, SCCS_E_CUDA.
  */
 int sccs_server_create(sccs_server **out, const sccs_server_opts *opts);
 
-/* Queue one fit; never waits for the GPU.  SCCS_E_BUSY when the queue is full; SCCS_E_INVAL on a
- * bad request.  *ticket identifies the request for sccs_poll. */
+/* Queue one fit of Section 2.5's workflows: a (prior, variance) point of the cross-validation
+ * grid fitted on the training folds (subject_weights = the training mask) with the held-out fold's
+ * predictive log-likelihood (heldout_weights = the fold's mask), or a bootstrap replicate
+ * (subject_weights = the resampled multiplicities).  Never waits for the GPU.  SCCS_E_BUSY when
+ * the queue is full; SCCS_E_INVAL on a bad request.  *ticket identifies the request for sccs_poll. */
 int sccs_submit(sccs_server *srv, const sccs_request *req, uint64_t *ticket);
 
-/* SCCS_PENDING until the fit is done; then fills *res (and res->beta if given), retires the
- * ticket and returns SCCS_OK.  The fit's own outcome is res->status.  Unknown ticket: SCCS_E_INVAL. */
+/* The result of one submitted fit: the MAP beta of Algorithm 1 (Section 2.2), P(beta), and for a
+ * cross-validation request the held-out predictive log-likelihood of Section 2.5 (Eq. 2 over the
+ * held-out subjects), with its queueing time and latency.  SCCS_PENDING until the fit is done;
+ * then fills *res (and res->beta if given), retires the ticket and returns SCCS_OK.  The fit's
+ * own outcome is res->status.  Unknown ticket: SCCS_E_INVAL. */
 int sccs_poll(sccs_server *srv, uint64_t ticket, sccs_result *res);
 
 /* Queue depth, fits running, fits completed, state memory, CTAs in use. */
@@ -357,7 +368,9 @@ int sccs_check_wait_timeout(sccs_handle *h, double timeout_ms);
  * The reduction across CTAs uses a scratch array compiled into the library (about 197 KB,
  * room for SCCS_NOALLOC_MAX_SEGMENTS segments); every device that loads the library holds it
  * until the process exits.  The first call on a device looks up that array's device address
- * (with the device current); make that first call before any stream capture.  The call runs
+ * (with the device current); make that first call before any stream capture.  The address is
+ * looked up again when the device's context has changed since (after cudaDeviceReset, say), so
+ * the first call after such a reset is a set-up call too.  The call runs
  * on the calling thread's current device and is asynchronous on `stream`.  All calls share
  * the one array, so calls that overlap on the GPU (on different streams, or from different
  * host threads) race and give wrong results: order them on one stream.

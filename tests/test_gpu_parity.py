@@ -539,7 +539,7 @@ def test_genkin_xbeta_rule_against_oracle(P, tol):
     assert ocycles == c
 
 
-@pytest.mark.slow
+@pytest.mark.fullsize
 def test_paper_scale_sampled_against_oracle(P):
     """The paper-scale workload at full size (4M subjects, 5,000 drugs, ~1e9 nonzeros, Laplace) in
     FP32 + FP64 polish, checked on sampled outputs the oracle computes straight from the input
