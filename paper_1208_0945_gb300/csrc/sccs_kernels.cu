@@ -2575,7 +2575,38 @@ __global__ void __launch_bounds__(kNoallocThreads) grad_hess_noalloc_kernel(
 
 namespace {
 std::mutex g_noalloc_mu;
+// Per device: the array's device address and the id of the context it was looked up in.  A
+// context torn down and made again (cudaDeviceReset, say) maps the array elsewhere, so the
+// address is looked up again whenever the current context's id differs.
 void *g_noalloc_addr[64] = {};
+unsigned long long g_noalloc_ctx[64] = {};
+
+// The current context's id (unique for the life of the process), 0 if none is current.  The
+// driver's functions come through the runtime, so the library does not link libcuda itself.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        cudaDriverEntryPointQueryResult q1{}, q2{};
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        (void)cudaGetLastError();
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 }  // namespace
 
 extern "C" int sccs_grad_hess_noalloc(const int64_t *seg_ptr, const int32_t *seg_subject, const int32_t *rows,
@@ -2591,15 +2622,21 @@ extern "C" int sccs_grad_hess_noalloc(const int64_t *seg_ptr, const int32_t *seg
     if (dev < 0 || dev >= 64) return sccs_set_error(SCCS_E_INVAL, "device ordinal above 63");
     void *scratch = nullptr;
     {
-        // First call on a device: look up the device address of the array (with the device
-        // current).  Host code must not pass the array's name itself to a kernel.
+        // First call on a device (or in a new context on it): look up the device address of the
+        // array with the device current.  Host code must not pass the array's name itself to a
+        // kernel: on the host that name is a stand-in, not a device address.
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
-            e = cudaGetSymbolAddress(&g_noalloc_addr[dev], sccs::g_noalloc_scratch);
+        const unsigned long long ctx = current_ctx_id();
+        if (!g_noalloc_addr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
+            void *addr = nullptr;
+            e = cudaGetSymbolAddress(&addr, sccs::g_noalloc_scratch);   // makes the context current if needed
             if (e != cudaSuccess) {
                 g_noalloc_addr[dev] = nullptr;
+                g_noalloc_ctx[dev] = 0;
                 return sccs_set_error(SCCS_E_CUDA, cudaGetErrorString(e));
             }
+            g_noalloc_addr[dev] = addr;
+            g_noalloc_ctx[dev] = current_ctx_id();
         }
         scratch = g_noalloc_addr[dev];
     }

@@ -64,3 +64,58 @@ def test_noalloc_rejects_more_segments_than_its_scratch_holds():
     with pytest.raises(P.SCCSError) as ei:
         P.sccs_grad_hess_noalloc(1, 1, 1, 1, 1, 1, 0.0, P.sccs.NOALLOC_MAX_SEGMENTS + 1, 1, None)
     assert ei.value.code == -1 and "SCCS_NOALLOC_MAX_SEGMENTS" in str(ei.value)
+
+
+def _call(P, t, ytx, nseg, out, stream):
+    P.sccs_grad_hess_noalloc(t["seg_ptr"].data_ptr(), t["seg_subj"].data_ptr(), t["rows"].data_ptr(),
+                             t["E"].data_ptr(), t["D"].data_ptr(), t["n"].data_ptr(), ytx, nseg, out.data_ptr(),
+                             stream)
+
+
+def test_noalloc_at_its_maximum_size_and_on_bad_inputs():
+    """Every scratch slot in use (SCCS_NOALLOC_MAX_SEGMENTS one-row segments, one per subject),
+    against the exact sum of the per-subject terms in float64, on two calls in a row; then a
+    subject with D = 0 and an infinite E, which must give NaN for both g and h; then P = 0."""
+    import math
+
+    import torch
+    import paper_1208_0945_gb300 as P
+
+    nseg = P.sccs.NOALLOC_MAX_SEGMENTS
+    rng = np.random.default_rng(11)
+    E = rng.uniform(1.0, 365.0, 2 * nseg) * np.exp(rng.normal(0, 0.5, 2 * nseg))
+    D = E[0::2] + E[1::2]                      # subject i: rows 2i (in the column) and 2i + 1
+    n = rng.integers(1, 6, nseg).astype(np.int32)
+    w = E[0::2] / D
+    G = math.fsum(n * w)
+    H = math.fsum(n * w * (1.0 - w))
+    ytx = float(rng.integers(0, 3 * nseg))
+    dev = torch.device("cuda", 0)
+    t = {"seg_ptr": torch.arange(nseg + 1, dtype=torch.int64, device=dev),
+         "seg_subj": torch.arange(nseg, dtype=torch.int32, device=dev),
+         "rows": torch.arange(0, 2 * nseg, 2, dtype=torch.int32, device=dev),
+         "E": torch.tensor(E, device=dev), "D": torch.tensor(D, device=dev), "n": torch.tensor(n, device=dev)}
+    out = torch.zeros(2, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    for _ in range(2):
+        out.fill_(-1.0)
+        _call(P, t, ytx, nseg, out, stream)
+        torch.cuda.synchronize(dev)
+        g, h = out.cpu().numpy()
+        assert abs(g - (ytx - G)) <= 1e-12 * max(1.0, abs(G)), (g, ytx - G)
+        assert abs(h + H) <= 1e-12 * H, (h, -H)
+    # a subject with D = 0, then an infinite E: NaN for both outputs
+    t["D"][12345] = 0.0
+    _call(P, t, ytx, nseg, out, stream)
+    torch.cuda.synchronize(dev)
+    assert np.isnan(out.cpu().numpy()).all()
+    t["D"][12345] = float(D[12345])
+    t["E"][2 * 777] = float("inf")
+    _call(P, t, ytx, nseg, out, stream)
+    torch.cuda.synchronize(dev)
+    assert np.isnan(out.cpu().numpy()).all()
+    # no segments: g = Y'X_j, h = 0
+    _call(P, t, 7.0, 0, out, stream)
+    torch.cuda.synchronize(dev)
+    g, h = out.cpu().numpy()
+    assert g == 7.0 and h == 0.0
