@@ -88,6 +88,15 @@ typedef struct sccs_create_opts {
                                   have their steps taken side by side, up to this many at a time
                                   (the result is the sequential one): 0 = the default 8; 1 = one
                                   at a time */
+    int32_t cluster_ctas;      /* FP64 fits (sccs_fit, served fits): columns with at most
+                                  cluster_max_nnz nonzeros run on one thread-block cluster of this
+                                  many CTAs, whose partial sums meet in distributed shared memory
+                                  instead of a grid-wide reduction per coordinate; the other columns
+                                  run on the whole team.  The team is then the CTAs the device holds
+                                  in whole clusters.  0 = the default (16 when num_shards is 0, else
+                                  off); 2, 4, 8 or 16; < 0 = off.  The result is the same as without
+                                  clusters up to rounding (the sums are split differently). */
+    int32_t cluster_max_nnz;   /* 0 = the default 65536 */
 } sccs_create_opts;
 
 typedef struct sccs_data_info {
@@ -102,6 +111,8 @@ typedef struct sccs_data_info {
     int32_t num_shards;
     int32_t threads_per_block;
     int32_t narrow_columns;             /* columns run whole on one CTA (see narrow_max_nnz) */
+    int32_t cluster_ctas;               /* cluster size of the cluster columns (0: none) */
+    int32_t cluster_columns;            /* columns run on one cluster (see cluster_ctas) */
 } sccs_data_info;
 
 typedef struct sccs_fit_opts {

@@ -246,9 +246,150 @@ struct HostLayout {
     std::vector<int32_t> nar_row;
     std::vector<int32_t> nar_group;   // J: at a group's first column, its number of columns; else 0
     int32_t narrow_groups = 0;
+    // cluster columns: run on the C CTAs of one thread-block cluster, over C subject shards of
+    // their own (their slices below; every other column has empty slices there)
+    int32_t C = 0, cluster_count = 0, first_grid = -1;
+    std::vector<uint8_t> ccls;        // J: 1 for a cluster column
+    std::vector<int32_t> cgroup;      // J: at a cluster group's first column its size, else 0
+    int32_t cluster_groups = 0;
+    std::vector<int32_t> next_grid;   // J: the next column run by the whole team, cyclically
+    std::vector<int64_t> cshard_row, cshard_pat;              // C+1
+    HostBuf<int32_t> crows;
+    HostBuf<int2> csegs;
+    HostBuf<int64_t> cgrp_base;
+    std::vector<int64_t> cslice_row, cslice_seg, cslice_grp;  // C*(J+1)
 };
 
+// Shards at subject boundaries, balanced by rows: shard s holds subjects [shard_pat[s],
+// shard_pat[s+1]) and rows [shard_row[s], shard_row[s+1]).
+void subject_shards(const std::vector<int64_t> &pat_ptr, int64_t Nk, int64_t Kk, int32_t S,
+                    std::vector<int64_t> &shard_pat, std::vector<int64_t> &shard_row) {
+    shard_pat.assign(static_cast<size_t>(S) + 1, 0);
+    shard_row.assign(static_cast<size_t>(S) + 1, 0);
+    for (int32_t s = 1; s < S; ++s) {
+        const int64_t target = (Kk * s) / S;
+        const int64_t p = std::lower_bound(pat_ptr.begin(), pat_ptr.end(), target) - pat_ptr.begin();
+        shard_pat[s] = std::max<int64_t>(shard_pat[s - 1], std::min<int64_t>(p, Nk));
+    }
+    shard_pat[S] = Nk;
+    for (int32_t s = 0; s <= S; ++s) shard_row[s] = pat_ptr[shard_pat[s]];
+}
+
+// Per (shard, column) slices of the columns with in_set(j) (the others get empty slices): a
+// slice's subject segments, longest first with ties in subject order, packed 32 to a group whose
+// rows are stored diagonal by diagonal.  crow / csub: each column's kept rows ascending and their
+// subjects.  Returns the largest slice's segments and rows.
+template <class InSet>
+void build_slices(int32_t J, int32_t S, const std::vector<int64_t> &shard_row, const std::vector<int64_t> &cptr,
+                  const int32_t *crow, const int32_t *csub, InSet in_set, HostBuf<int32_t> &rows_out,
+                  HostBuf<int2> &segs_out, HostBuf<int64_t> &grp_out, std::vector<int64_t> &slice_row,
+                  std::vector<int64_t> &slice_seg, std::vector<int64_t> &slice_grp, int64_t &max_seg,
+                  int64_t &max_rows, int64_t &segments) {
+    // ---- pass 1: per (shard, column) slice: nonzeros and segments
+    const int64_t SJ = static_cast<int64_t>(S) * (J + 1);
+    std::vector<int64_t> s_nnz(static_cast<size_t>(SJ), 0), s_seg(static_cast<size_t>(SJ), 0);
+    std::vector<int64_t> s_lo(static_cast<size_t>(SJ), 0);
+    // one merge of each column's (ascending) rows with the shard boundaries
+    parallel_for(J, [&](int64_t j) {
+        if (!in_set(static_cast<int32_t>(j))) return;
+        int64_t e = cptr[j];
+        const int64_t e1 = cptr[j + 1];
+        for (int32_t s = 0; s < S; ++s) {
+            const int32_t r1 = static_cast<int32_t>(shard_row[s + 1]);
+            const int64_t lo = e;
+            int64_t ns = 0;
+            int32_t prev = -1;
+            for (; e < e1 && crow[e] < r1; ++e)
+                if (csub[e] != prev) {
+                    ns++;
+                    prev = csub[e];
+                }
+            const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
+            s_lo[idx] = lo;
+            s_nnz[idx] = e - lo;
+            s_seg[idx] = ns;
+        }
+    });
+    slice_row.assign(static_cast<size_t>(SJ), 0);
+    slice_seg.assign(static_cast<size_t>(SJ), 0);
+    slice_grp.assign(static_cast<size_t>(SJ), 0);
+    int64_t tr = 0, ts = 0, tg = 0;
+    max_seg = 1;
+    max_rows = 1;
+    for (int32_t s = 0; s < S; ++s) {
+        for (int32_t j = 0; j <= J; ++j) {
+            const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
+            slice_row[idx] = tr;
+            slice_seg[idx] = ts;
+            slice_grp[idx] = tg;
+            if (j < J) {
+                tr += s_nnz[idx];
+                ts += s_seg[idx];
+                tg += (s_seg[idx] + 31) / 32;
+                max_seg = std::max<int64_t>(max_seg, s_seg[idx]);
+                max_rows = std::max<int64_t>(max_rows, s_nnz[idx]);
+            }
+        }
+    }
+    segments = ts;
+    rows_out.alloc(static_cast<size_t>(tr));
+    segs_out.alloc(static_cast<size_t>(ts));
+    grp_out.alloc(static_cast<size_t>(tg));
+
+    // ---- pass 2: fill segments (longest first) and rows (diagonal-major per group)
+    parallel_for(S, [&](int64_t s) {
+        std::vector<int64_t> seg_start;
+        std::vector<int32_t> seg_len, seg_pid, order, len_pos;
+        for (int32_t j = 0; j < J; ++j) {
+            const int64_t idx = s * (J + 1) + j;
+            const int64_t lo = s_lo[idx], n = s_nnz[idx];
+            seg_start.clear();
+            seg_len.clear();
+            seg_pid.clear();
+            int32_t prev = -1;
+            for (int64_t q = lo; q < lo + n; ++q) {
+                const int32_t p = csub[q];
+                if (p != prev) {
+                    seg_start.push_back(q);
+                    seg_len.push_back(0);
+                    seg_pid.push_back(p);
+                    prev = p;
+                }
+                seg_len.back()++;
+            }
+            const int32_t ns = static_cast<int32_t>(seg_len.size());
+            // longest first, ties in subject order: a stable counting sort by length
+            int32_t lmax = 0;
+            for (int32_t i = 0; i < ns; ++i) lmax = std::max(lmax, seg_len[i]);
+            len_pos.assign(static_cast<size_t>(lmax) + 2, 0);
+            for (int32_t i = 0; i < ns; ++i) len_pos[seg_len[i]]++;
+            for (int32_t l = lmax, run = 0; l >= 1; --l) {
+                const int32_t c = len_pos[l];
+                len_pos[l] = run;
+                run += c;
+            }
+            order.resize(ns);
+            for (int32_t i = 0; i < ns; ++i) order[len_pos[seg_len[i]]++] = i;
+            int64_t rpos = slice_row[idx];
+            const int64_t spos = slice_seg[idx], gpos = slice_grp[idx];
+            for (int32_t i = 0; i < ns; ++i) segs_out[spos + i] = int2{seg_pid[order[i]], seg_len[order[i]]};
+            for (int32_t g = 0; g * 32 < ns; ++g) {
+                grp_out[gpos + g] = rpos;
+                const int32_t a = g * 32, b = std::min(ns, a + 32);
+                const int32_t maxlen = seg_len[order[a]];
+                for (int32_t t = 0; t < maxlen; ++t)
+                    for (int32_t l = a; l < b; ++l) {
+                        const int32_t o = order[l];
+                        if (seg_len[o] > t) rows_out[rpos++] = crow[seg_start[o] + t];
+                    }
+            }
+        }
+    });
+}
+
 constexpr int32_t kNarrowDefault = 1024;
+constexpr int32_t kClusterDefault = 16;
+constexpr int64_t kClusterMaxNnzDefault = 65536;
 using sccs::kNarrowGroupMax;
 constexpr int32_t kNarrowMinShards = 4;
 
@@ -302,7 +443,7 @@ int validate_inputs(int64_t K, const int64_t *patient_id, const int32_t *y, cons
 
 int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const double *Lin, int32_t J,
                  const int64_t *col_ptr, const int32_t *row_idx, int32_t S, int32_t narrow_max, int32_t group_max,
-                 HostLayout &hl) {
+                 HostLayout &hl, int32_t C = 0, int64_t cluster_max = 0) {
     // ---- subjects, n_i, dropping n_i = 0 (chunked parallel scans: the subjects' first rows,
     //      their event counts, then the kept subjects' new positions by prefix sums)
     const int64_t PK = std::max<int64_t>(1, std::min<int64_t>(8 * host_threads(), K / 65536 + 1));
@@ -679,118 +820,108 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
         }
     }
 
-    // ---- shards at subject boundaries, balanced by rows
+    // ---- shards at subject boundaries, balanced by rows; every column's slices over them
     hl.S = S;
-    hl.shard_pat.assign(static_cast<size_t>(S) + 1, 0);
-    hl.shard_row.assign(static_cast<size_t>(S) + 1, 0);
-    for (int32_t s = 1; s < S; ++s) {
-        const int64_t target = (Kk * s) / S;
-        const int64_t p = std::lower_bound(hl.pat_ptr.begin(), hl.pat_ptr.end(), target) - hl.pat_ptr.begin();
-        hl.shard_pat[s] = std::max<int64_t>(hl.shard_pat[s - 1], std::min<int64_t>(p, Nk));
-    }
-    hl.shard_pat[S] = Nk;
-    for (int32_t s = 0; s <= S; ++s) hl.shard_row[s] = hl.pat_ptr[hl.shard_pat[s]];
+    subject_shards(hl.pat_ptr, Nk, Kk, S, hl.shard_pat, hl.shard_row);
+    build_slices(J, S, hl.shard_row, cptr, crow, csub.data(), [](int32_t) { return true; }, hl.rows, hl.segs,
+                 hl.grp_base, hl.slice_row, hl.slice_seg, hl.slice_grp, hl.stash_stride, hl.estash_stride,
+                 hl.segments);
 
-    // ---- pass 1: per (shard, column) slice: nonzeros and segments
-    const int64_t SJ = static_cast<int64_t>(S) * (J + 1);
-    std::vector<int64_t> s_nnz(static_cast<size_t>(SJ), 0), s_seg(static_cast<size_t>(SJ), 0);
-    std::vector<int64_t> s_lo(static_cast<size_t>(SJ), 0);
-    // one merge of each column's (ascending) rows with the shard boundaries
-    parallel_for(J, [&](int64_t j) {
-        int64_t e = cptr[j];
-        const int64_t e1 = cptr[j + 1];
-        for (int32_t s = 0; s < S; ++s) {
-            const int32_t r1 = static_cast<int32_t>(hl.shard_row[s + 1]);
-            const int64_t lo = e;
-            int64_t ns = 0;
-            int32_t prev = -1;
-            for (; e < e1 && crow[e] < r1; ++e)
-                if (csub[e] != prev) {
-                    ns++;
-                    prev = csub[e];
-                }
-            const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
-            s_lo[idx] = lo;
-            s_nnz[idx] = e - lo;
-            s_seg[idx] = ns;
-        }
-    });
-    hl.slice_row.assign(static_cast<size_t>(SJ), 0);
-    hl.slice_seg.assign(static_cast<size_t>(SJ), 0);
-    hl.slice_grp.assign(static_cast<size_t>(SJ), 0);
-    int64_t tr = 0, ts = 0, tg = 0;
-    int64_t max_seg = 1, max_rows = 1;
-    for (int32_t s = 0; s < S; ++s) {
-        for (int32_t j = 0; j <= J; ++j) {
-            const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
-            hl.slice_row[idx] = tr;
-            hl.slice_seg[idx] = ts;
-            hl.slice_grp[idx] = tg;
-            if (j < J) {
-                tr += s_nnz[idx];
-                ts += s_seg[idx];
-                tg += (s_seg[idx] + 31) / 32;
-                max_seg = std::max<int64_t>(max_seg, s_seg[idx]);
-                max_rows = std::max<int64_t>(max_rows, s_nnz[idx]);
-            }
-        }
-    }
-    hl.stash_stride = max_seg;
-    hl.estash_stride = max_rows;
-    hl.segments = ts;
-    hl.rows.alloc(static_cast<size_t>(tr));
-    hl.segs.alloc(static_cast<size_t>(ts));
-    hl.grp_base.alloc(static_cast<size_t>(tg));
-
-    // ---- pass 2: fill segments (longest first) and rows (diagonal-major per group)
-    parallel_for(S, [&](int64_t s) {
-        std::vector<int64_t> seg_start;
-        std::vector<int32_t> seg_len, seg_pid, order, len_pos;
-        for (int32_t j = 0; j < J; ++j) {
-            const int64_t idx = s * (J + 1) + j;
-            const int64_t lo = s_lo[idx], n = s_nnz[idx];
-            seg_start.clear();
-            seg_len.clear();
-            seg_pid.clear();
-            int32_t prev = -1;
-            for (int64_t q = lo; q < lo + n; ++q) {
-                const int32_t p = csub[q];
-                if (p != prev) {
-                    seg_start.push_back(q);
-                    seg_len.push_back(0);
-                    seg_pid.push_back(p);
-                    prev = p;
-                }
-                seg_len.back()++;
-            }
-            const int32_t ns = static_cast<int32_t>(seg_len.size());
-            // longest first, ties in subject order: a stable counting sort by length
-            int32_t lmax = 0;
-            for (int32_t i = 0; i < ns; ++i) lmax = std::max(lmax, seg_len[i]);
-            len_pos.assign(static_cast<size_t>(lmax) + 2, 0);
-            for (int32_t i = 0; i < ns; ++i) len_pos[seg_len[i]]++;
-            for (int32_t l = lmax, run = 0; l >= 1; --l) {
-                const int32_t c = len_pos[l];
-                len_pos[l] = run;
-                run += c;
-            }
-            order.resize(ns);
-            for (int32_t i = 0; i < ns; ++i) order[len_pos[seg_len[i]]++] = i;
-            int64_t rpos = hl.slice_row[idx];
-            const int64_t spos = hl.slice_seg[idx], gpos = hl.slice_grp[idx];
-            for (int32_t i = 0; i < ns; ++i) hl.segs[spos + i] = int2{seg_pid[order[i]], seg_len[order[i]]};
-            for (int32_t g = 0; g * 32 < ns; ++g) {
-                hl.grp_base[gpos + g] = rpos;
-                const int32_t a = g * 32, b = std::min(ns, a + 32);
-                const int32_t maxlen = seg_len[order[a]];
-                for (int32_t t = 0; t < maxlen; ++t)
-                    for (int32_t l = a; l < b; ++l) {
-                        const int32_t o = order[l];
-                        if (seg_len[o] > t) hl.rows[rpos++] = crow[seg_start[o] + t];
+    // ---- cluster columns: at most cluster_max nonzeros, over C subject shards of their own, each
+    //      slice small enough to be staged whole (else the column stays with the whole team)
+    hl.ccls.assign(static_cast<size_t>(J), 0);
+    hl.next_grid.assign(static_cast<size_t>(J), 0);
+    if (C > 0) {
+        hl.C = C;
+        subject_shards(hl.pat_ptr, Nk, Kk, C, hl.cshard_pat, hl.cshard_row);
+        for (int32_t j = 0; j < J; ++j) hl.ccls[j] = (cptr[j + 1] - cptr[j]) <= cluster_max ? 1 : 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            int64_t ms = 0, mr = 0, segs = 0;
+            build_slices(J, C, hl.cshard_row, cptr, crow, csub.data(), [&](int32_t j) { return hl.ccls[j] != 0; },
+                         hl.crows, hl.csegs, hl.cgrp_base, hl.cslice_row, hl.cslice_seg, hl.cslice_grp, ms, mr,
+                         segs);
+            bool changed = false;
+            for (int32_t j = 0; j < J; ++j) {
+                if (!hl.ccls[j]) continue;
+                for (int32_t c = 0; c < C; ++c) {
+                    const int64_t idx = static_cast<int64_t>(c) * (J + 1) + j;
+                    if (hl.cslice_row[idx + 1] - hl.cslice_row[idx] > sccs::kRowCap ||
+                        hl.cslice_seg[idx + 1] - hl.cslice_seg[idx] > sccs::kSegCap) {
+                        hl.ccls[j] = 0;
+                        changed = true;
+                        break;
                     }
+                }
             }
+            if (!changed) break;
         }
-    });
+        for (int32_t j = 0; j < J; ++j) hl.cluster_count += hl.ccls[j];
+        // Groups: consecutive cluster columns with pairwise disjoint subjects, up to group_max, whose
+        // slices on every cluster shard fit one staging buffer together.  Neither column of a pair
+        // reads what the other writes, so their steps can be taken side by side with exactly the
+        // sequential result.
+        hl.cgroup.assign(static_cast<size_t>(J), 0);
+        std::vector<uint8_t> seen(static_cast<size_t>(std::max<int64_t>(Nk, 1)), 0);
+        std::vector<int32_t> touched;
+        std::vector<int64_t> rows_c(static_cast<size_t>(C)), segs_c(static_cast<size_t>(C));
+        auto slice_n = [&](const std::vector<int64_t> &a, int32_t c, int32_t j) {
+            const int64_t idx = static_cast<int64_t>(c) * (J + 1) + j;
+            return a[idx + 1] - a[idx];
+        };
+        for (int32_t j = 0; j < J;) {
+            if (!hl.ccls[j]) {
+                ++j;
+                continue;
+            }
+            for (int32_t c = 0; c < C; ++c) {
+                rows_c[c] = slice_n(hl.cslice_row, c, j);
+                segs_c[c] = slice_n(hl.cslice_seg, c, j);
+            }
+            for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e)
+                if (!seen[csub[e]]) {
+                    seen[csub[e]] = 1;
+                    touched.push_back(csub[e]);
+                }
+            int32_t m = 1;
+            while (j + m < J && hl.ccls[j + m] && m < group_max) {
+                const int32_t jn = j + m;
+                bool fits = true;
+                for (int32_t c = 0; c < C && fits; ++c)
+                    fits = rows_c[c] + slice_n(hl.cslice_row, c, jn) <= sccs::kRowCap &&
+                           segs_c[c] + slice_n(hl.cslice_seg, c, jn) <= sccs::kSegCap;
+                for (int64_t e = cptr[jn]; e < cptr[jn + 1] && fits; ++e)
+                    if (seen[csub[e]]) fits = false;
+                if (!fits) break;
+                for (int32_t c = 0; c < C; ++c) {
+                    rows_c[c] += slice_n(hl.cslice_row, c, jn);
+                    segs_c[c] += slice_n(hl.cslice_seg, c, jn);
+                }
+                for (int64_t e = cptr[jn]; e < cptr[jn + 1]; ++e)
+                    if (!seen[csub[e]]) {
+                        seen[csub[e]] = 1;
+                        touched.push_back(csub[e]);
+                    }
+                ++m;
+            }
+            for (int32_t i : touched) seen[i] = 0;
+            touched.clear();
+            hl.cgroup[j] = m;
+            hl.cluster_groups++;
+            j += m;
+        }
+    }
+    for (int32_t j = 0; j < J; ++j)
+        if (!hl.ccls[j]) {
+            hl.first_grid = j;
+            break;
+        }
+    {
+        int32_t nxt = hl.first_grid;
+        for (int32_t j = J - 1; j >= 0; --j) {
+            hl.next_grid[j] = nxt;
+            if (!hl.ccls[j]) nxt = j;
+        }
+    }
     return SCCS_OK;
 }
 
@@ -1218,13 +1349,32 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     int S = o.num_shards ? o.num_shards : sms;
     if (S < 1 || S > sms * per_sm || S > sccs::kMaxShards)
         return fail(SCCS_E_INVAL, "num_shards must be in [1, " + std::to_string(std::min(sms * per_sm, sccs::kMaxShards)) + "]");
+    // cluster columns: a cluster of C CTAs, and a team of whole clusters
+    int32_t C = o.cluster_ctas < 0 ? 0 : (o.cluster_ctas == 0 ? (o.num_shards == 0 ? kClusterDefault : 0) : o.cluster_ctas);
+    if (C != 0 && C != 2 && C != 4 && C != 8 && C != 16)
+        return fail(SCCS_E_INVAL, "cluster_ctas must be 2, 4, 8 or 16 (0 = default, < 0 = off)");
+    if (C > 0) {
+        int ncl = 0;
+        const int ce2 = sccs::fit_kernel_max_clusters(threads, C, &ncl);
+        if (ce2 != 0 || ncl < 1) {
+            if (o.cluster_ctas > 0) return fail(SCCS_E_UNSUPPORTED, "the device cannot hold clusters of that size");
+            C = 0;   // the default quietly falls back to whole-team columns
+        } else if (o.num_shards == 0) {
+            S = std::min(S, ncl * C);
+        } else if (S % C != 0 || S > ncl * C) {
+            return fail(SCCS_E_INVAL, "with cluster_ctas, num_shards must be a multiple of it and at most " +
+                                          std::to_string(ncl * C));
+        }
+    }
+    const int64_t cluster_max = o.cluster_max_nnz > 0 ? o.cluster_max_nnz : kClusterMaxNnzDefault;
 
     HostLayout hl;
     const int32_t narrow_max = o.narrow_max_nnz == 0 ? kNarrowDefault : o.narrow_max_nnz;
     // every column of a group keeps at least two warps of the CTA
     const int32_t group_cap = std::max(1, std::min(kNarrowGroupMax, threads / 64));
     const int32_t group_max = o.narrow_group_max <= 0 ? group_cap : std::min(o.narrow_group_max, group_cap);
-    int rc = build_layout(K, patient_id, y, offset_L, J, col_ptr, row_idx, S, narrow_max, group_max, hl);
+    int rc = build_layout(K, patient_id, y, offset_L, J, col_ptr, row_idx, S, narrow_max, group_max, hl, C,
+                          cluster_max);
     if (rc != SCCS_OK) return rc;
 
     sccs_handle *h = new sccs_handle();
@@ -1366,6 +1516,36 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
         d.nar_group = ngrp;
         d.nar_sync = nsync;
     }
+    if (hl.C > 0) {
+        uint8_t *ccls;
+        int32_t *ngrid, *crows, *cgrp_n;
+        int2 *csegs;
+        int64_t *cgrp, *csr, *css, *csg;
+        unsigned long long *csync;
+        if ((rc = upload(h, &ccls, hl.ccls.data(), hl.ccls.size())) ||
+            (rc = upload(h, &ngrid, hl.next_grid.data(), hl.next_grid.size())) ||
+            (rc = upload(h, &cgrp_n, hl.cgroup.data(), hl.cgroup.size())) ||
+            (rc = upload(h, &crows, hl.crows.data(), hl.crows.size(), sccs::kCopyPad)) ||
+            (rc = upload(h, &csegs, hl.csegs.data(), hl.csegs.size(), sccs::kCopyPad)) ||
+            (rc = upload(h, &cgrp, hl.cgrp_base.data(), hl.cgrp_base.size(), sccs::kCopyPad)) ||
+            (rc = upload(h, &csr, hl.cslice_row.data(), hl.cslice_row.size())) ||
+            (rc = upload(h, &css, hl.cslice_seg.data(), hl.cslice_seg.size())) ||
+            (rc = upload(h, &csg, hl.cslice_grp.data(), hl.cslice_grp.size())) ||
+            (rc = alloc_zero(h, &csync, static_cast<size_t>(32))))
+            return bail(rc);
+        d.C = hl.C;
+        d.first_grid = hl.first_grid;
+        d.ccls = ccls;
+        d.next_grid = ngrid;
+        d.cgroup = cgrp_n;
+        d.crows = crows;
+        d.csegs = csegs;
+        d.cgrp_base = cgrp;
+        d.cslice_row = csr;
+        d.cslice_seg = css;
+        d.cslice_grp = csg;
+        d.clu_sync = csync;
+    }
     {
         // E per row of an unstaged slice between its phases A and C (allocated last: the arrays
         // above keep their measured placement)
@@ -1393,6 +1573,8 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     info.num_shards = S;
     info.threads_per_block = threads;
     info.narrow_columns = hl.narrow_count;
+    info.cluster_ctas = hl.C;
+    info.cluster_columns = hl.cluster_count;
     *out = h;
     return SCCS_OK;
 }

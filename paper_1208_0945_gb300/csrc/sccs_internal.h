@@ -68,6 +68,23 @@ struct DevLayout {
     const int64_t *ycol_ptr;   // J+1: per column, its (subject, sum of y) pairs with events
     const int32_t *ysub;       //   kept subject of each pair
     const int32_t *ycnt;       //   sum of y over the column's rows of that subject
+    // cluster columns (FP64 fits launched with thread-block clusters of C CTAs): a column with
+    // ccls[j] = 1 runs on the C CTAs of the first cluster, CTA c over its own subject shard c of a
+    // second partition (slices cslice_*), with the partial sums reduced through distributed
+    // shared memory instead of the grid all-reduce.  C = 0: no cluster columns.
+    int32_t C;
+    int32_t first_grid;        // first column run by the whole team (-1: none)
+    const uint8_t *ccls;       // J
+    const int32_t *next_grid;  // J: the next column run by the whole team after j, cyclically
+    const int32_t *cgroup;     // J: columns in the cluster group starting at j (0 inside a group):
+                               //    consecutive cluster columns with pairwise disjoint subjects
+    const int32_t *crows;      // as rows / segs / grp_base, over the C shards
+    const int2 *csegs;
+    const int64_t *cgrp_base;
+    const int64_t *cslice_row; // C*(J+1)
+    const int64_t *cslice_seg;
+    const int64_t *cslice_grp;
+    unsigned long long *clu_sync;  // per fit state: [0] CTAs arrived at a cluster run, [16] runs done
     // state
     double *E;                 // K: L x exp(Xb)
     double *E_prev;            // K: E at the start of the cycle (Genkin's X-beta rule), or null
@@ -100,6 +117,8 @@ struct FitParams {
                                         // seq_end of the launch before it on the same stream)
     const int32_t *ho_nev;     // device [N] or null: held-out counts w_i n_i (FP64 fits only); the
     const double *ho_ytx;      // [J] fit then ends with Eq. 2 under them in out->heldout_loglik
+    int32_t cluster;           // 1: launched in clusters of DevLayout::C CTAs (cluster columns on)
+    int32_t pad_c;
 };
 
 struct FitOut {
@@ -164,6 +183,8 @@ int launch_grad_hess(const DevLayout &d, int32_t j, const FitParams &p, FitOut *
 int launch_grad_hess_partial(const DevLayout &d, int32_t j, const FitParams &p, FitOut *out_dev,
                              int threads, int ctas, void *stream);
 int fit_kernel_max_blocks_per_sm(int threads, int *blocks);
+// Clusters of `cluster` CTAs of the FP64 fit kernel that can be resident at once (0 if none).
+int fit_kernel_max_clusters(int threads, int cluster, int *clusters);
 // Independent fits in one cooperative launch: CTA b runs shard map[b].y of fit map[b].x
 // (entries and map in device memory; every fit's CTAs form its own all-reduce team).
 // The batched fits in one persistent cooperative launch of `ctas` CTAs.  entries (device) are

@@ -159,6 +159,29 @@ __device__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long timeout_ns) 
     }
 }
 
+// ------------------------------------------------------------------ thread-block clusters
+
+// The shared::cluster address of `local` (this CTA's shared memory) in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void *local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr(local)), "r"(rank));
+    return r;
+}
+
+// 16 bytes into another CTA's shared memory, counted (complete_tx) on an mbarrier of that CTA:
+// the receiver sees the bytes once that mbarrier's phase completes.
+__device__ __forceinline__ void st_async_f64x2(uint32_t addr, double a, double b, uint32_t remote_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "d"(a), "d"(b), "r"(remote_bar)
+                 : "memory");
+}
+
+// Every thread of every CTA of the cluster (hardware barrier; used only where all of them arrive
+// unconditionally: after the mbarrier initialisation and before the kernel exits).
+__device__ __forceinline__ void cluster_barrier_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ exact fixed-point sums
 
 // A non-negative value V * 2^-128 held in three 64-bit limbs (w0 least significant).
@@ -278,7 +301,13 @@ struct StageBuf {
 struct ColDesc {
     long long seg0, row0, grp0;
     int nseg, nnz, ngrp, staged;
-    int seg_off, row_off, grp_off, pad;
+    int seg_off, row_off, grp_off, cl;   // cl: a slice of the cluster partition
+    int gm;                              // columns of a cluster group (1 otherwise)
+};
+
+// A staged cluster group: column t's JDS groups, segments and rows within the staged slice.
+struct GroupOffs {
+    int goff[kNarrowGroupMax + 1], soff[kNarrowGroupMax + 1], roff[kNarrowGroupMax + 1];
 };
 
 struct SharedState {
@@ -286,7 +315,7 @@ struct SharedState {
     Fx wb[kMaxWarps];
     int wbad[kMaxWarps];
     double db, r, em1;
-    // a group of narrow columns: per column step results, and the group's flags
+    // a group of narrow (or cluster) columns: per column step results, and the group's flags
     double gdb[kNarrowGroupMax], gr[kNarrowGroupMax], gem1[kNarrowGroupMax], gnbj[kNarrowGroupMax],
         gtrust[kNarrowGroupMax];
     int gnumeric, gwarn, gnonzero;
@@ -296,11 +325,16 @@ struct SharedState {
     int ok;
     int stop;
     ColDesc desc[2];
+    GroupOffs gofs[2];
     uint64_t bar[2];
     int run_status;         // a finished run_fit's status (thread 0 writes it)
     int drained;            // its staging copies all landed (thread blockDim - 32 writes it)
     unsigned long long run_seq;   // the all-reduce sequence number it ended at
     int nar_pre;            // CTA 0: the narrow run whose first group's static data is in nar_hi
+    // cluster all-reduce: each CTA's pair of partials, written by every CTA of the cluster into
+    // every CTA's slots, and the mbarriers that count their bytes (both by round parity)
+    double2 cslot[2][kNarrowGroupMax][16];
+    uint64_t cbar[2];
 };
 
 // One narrow group's gathered data (half of the narrow buffers).
@@ -643,18 +677,20 @@ __device__ __forceinline__ void segment_terms(double num, double Dv, int nv, dou
 // ------------------------------------------------------------------ column phases
 
 // Phase A over a staged slice (everything static already in shared memory).
+// The JDS groups g0, g0 + gstep, ... below g1 of one column of the staged slice, whose groups
+// start at gbase and segments at sbase, sbase + 32, ... up to send (the whole slice of one column:
+// g0 = warp, gstep = warps, gbase = sbase = 0, send = segments).
 __device__ void phase_a_staged(const DevLayout &d, const ColDesc &cd, const StageBuf &sb, SmemLayout &sm,
-                               double &G, double &H, bool &bad) {
-    const int warp = threadIdx.x >> 5;
+                               int g0, int g1, int gstep, int gbase, int sbase, int send, double &G, double &H,
+                               bool &bad) {
     const int lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
     const int2 *sseg = sb.segs + cd.seg_off;
     const int32_t *srow = sb.rows + cd.row_off;
     const long long *sgrp = sb.grp + cd.grp_off;
     bool first = true;
-    for (int g = warp; g < cd.ngrp; g += nwarps) {
-        const int si = 32 * g + lane;
-        const bool valid = si < cd.nseg;
+    for (int g = g0; g < g1; g += gstep) {
+        const int si = sbase + 32 * (g - gbase) + lane;
+        const bool valid = si < send;
         const int2 sg = valid ? sseg[si] : make_int2(0, 0);
         const double Dv = valid ? d.D[sg.x] : 1.0;
         const int nv = valid ? d.nev[sg.x] : 0;
@@ -1164,6 +1200,9 @@ __device__ bool refresh_and_reduce32(const DevLayout &d, int s, unsigned long lo
 
 struct SliceBounds {
     long long seg0, seg1, row0, row1, grp0, grp1;
+    int cl;                    // 1: a slice of the cluster partition (cslice_*, crows, csegs, cgrp_base)
+    int m;                     // cluster slices: the group's columns (their slices are adjacent)
+    long long so0;             // cluster slices: index of the group's first slice in cslice_*
 };
 
 __device__ __forceinline__ SliceBounds load_bounds(const DevLayout &d, int s, int j) {
@@ -1175,6 +1214,23 @@ __device__ __forceinline__ SliceBounds load_bounds(const DevLayout &d, int s, in
     b.row1 = d.slice_row[so + 1];
     b.grp0 = d.slice_grp[so];
     b.grp1 = d.slice_grp[so + 1];
+    b.cl = 0;
+    return b;
+}
+
+// Slices (c, j) .. (c, j + m - 1) of the cluster partition (c < C): a cluster group, one range.
+__device__ __forceinline__ SliceBounds load_bounds_c(const DevLayout &d, int c, int j, int m) {
+    const long long so = static_cast<long long>(c) * (d.J + 1) + j;
+    SliceBounds b;
+    b.seg0 = d.cslice_seg[so];
+    b.seg1 = d.cslice_seg[so + m];
+    b.row0 = d.cslice_row[so];
+    b.row1 = d.cslice_row[so + m];
+    b.grp0 = d.cslice_grp[so];
+    b.grp1 = d.cslice_grp[so + m];
+    b.cl = 1;
+    b.m = m;
+    b.so0 = so;
     return b;
 }
 
@@ -1190,22 +1246,36 @@ __device__ bool issue_stage(const DevLayout &d, const SliceBounds &b, SmemLayout
     cd.ngrp = static_cast<int>(b.grp1 - b.grp0);
     cd.staged = (cd.nseg <= kSegCap && cd.nnz <= kRowCap) ? 1 : 0;
     cd.seg_off = cd.row_off = cd.grp_off = 0;
+    cd.cl = b.cl;
+    cd.gm = 1;
+    if (b.cl) {
+        GroupOffs &go = sh.gofs[buf];
+        cd.gm = b.m;
+        for (int t = 0; t <= b.m; ++t) {
+            go.goff[t] = static_cast<int>(d.cslice_grp[b.so0 + t] - b.grp0);
+            go.soff[t] = static_cast<int>(d.cslice_seg[b.so0 + t] - b.seg0);
+            go.roff[t] = static_cast<int>(d.cslice_row[b.so0 + t] - b.row0);
+        }
+    }
     if (!cd.staged) return false;
+    const int2 *asegs = b.cl ? d.csegs : d.segs;
+    const int32_t *arows = b.cl ? d.crows : d.rows;
+    const int64_t *agrp = b.cl ? d.cgrp_base : d.grp_base;
     StageBuf &st = sm.stage[buf];
     uint32_t total = 0;
     const char *gs = nullptr, *gr = nullptr, *gg = nullptr;
     uint32_t ns = 0, nr = 0, ng = 0;
     if (cd.nseg > 0) {
         const long long a0 = (8 * b.seg0) & ~15ll, a1 = (8 * b.seg1 + 15) & ~15ll;
-        gs = reinterpret_cast<const char *>(d.segs) + a0;
+        gs = reinterpret_cast<const char *>(asegs) + a0;
         ns = static_cast<uint32_t>(a1 - a0);
         cd.seg_off = static_cast<int>((8 * b.seg0 - a0) / 8);
         const long long r0 = (4 * b.row0) & ~15ll, r1 = (4 * b.row1 + 15) & ~15ll;
-        gr = reinterpret_cast<const char *>(d.rows) + r0;
+        gr = reinterpret_cast<const char *>(arows) + r0;
         nr = static_cast<uint32_t>(r1 - r0);
         cd.row_off = static_cast<int>((4 * b.row0 - r0) / 4);
         const long long g0 = (8 * b.grp0) & ~15ll, g1 = (8 * b.grp1 + 15) & ~15ll;
-        gg = reinterpret_cast<const char *>(d.grp_base) + g0;
+        gg = reinterpret_cast<const char *>(agrp) + g0;
         ng = static_cast<uint32_t>(g1 - g0);
         cd.grp_off = static_cast<int>((8 * b.grp0 - g0) / 8);
         total = ns + nr + ng;
@@ -1573,6 +1643,138 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
     }
 }
 
+// ------------------------------------------------------------------ cluster groups
+//
+// A group of m consecutive cluster columns j .. j + m - 1 with pairwise disjoint subjects, taken by
+// the C CTAs of the first cluster, CTA c over cluster shard c (its slices of the m columns are one
+// staged range).  Neither column reads the E or D another writes, so their steps are taken side by
+// side and the result is the sequential one.  Warps are interleaved over the columns (warp w works
+// for column w mod m, as in a narrow group).  Per column: phase A of Section 2.3 over its slice
+// (gather L x exp(Xb), the segment numerators, the W terms of Eqs. 7-9), the CTA's exact sums,
+// then warp t sends its column's pair to slot [t][c] of every CTA of the cluster by asynchronous
+// stores counted on the receiver's mbarrier of this round (r & 1; armed by warp 0 for the C x m
+// pairs it receives), waits (bounded) for that phase, adds the C pairs exactly -- every CTA holds
+// the same totals -- and lane 0 takes the step of Eq. 4 (prior, trust region) for column j + t.
+// Then phase C for every column with db != 0.  A CTA is at most one round ahead of another (the
+// round after needs the slower CTA's own pairs), so bytes of round r + 1 only meet the other
+// mbarrier, whose phase for round r - 1 is complete; bytes that arrive before the receiver armed
+// it leave its byte count negative until it does, which the mbarrier allows.
+// Results in sh.gdb / gr / gem1 / gnbj (and sh.gnumeric, sh.gwarn); false on abort.
+__device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColDesc &cd, const GroupOffs &go,
+                              const StageBuf &sb, SmemLayout &sm, SharedState &sh, int rank, int j, unsigned round,
+                              const double *beta, const double *trust, bool staged_ok, long long timeout_ns) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int m = cd.gm;
+    const int wpc = nwarps / m;                  // warps per column (the host keeps m <= warps / 2)
+    const int t = warp % m, wi = warp / m;
+    const bool mine = wi < wpc;
+    if (threadIdx.x == 0) {
+        sh.gnumeric = sh.gwarn = 0;
+        sh.ok = 1;
+    }
+    double G = 0.0, H = 0.0;
+    bool bad = !cd.staged || !staged_ok;          // never unstaged: the host sizes groups to the buffer
+    if (!staged_ok && threadIdx.x == 0) atomicExch(d.abort_flag, 1);   // a stage that did not arrive
+    if (!bad && mine)
+        phase_a_staged(d, cd, sb, sm, go.goff[t] + wi, go.goff[t + 1], wpc, go.goff[t], go.soff[t], go.soff[t + 1], G, H,
+                       bad);
+    {
+        const Fx fa = fx_warp_sum(fx_from_double(G, bad));
+        const Fx fb = fx_warp_sum(fx_from_double(H, bad));
+        const int wbad = __any_sync(kFull, bad);
+        if (lane == 0) {
+            sh.wa[warp] = fa;
+            sh.wb[warp] = fb;
+            sh.wbad[warp] = wbad;
+        }
+    }
+    __syncthreads();
+    if (warp < m) {
+        const int C = d.C;
+        const int buf = static_cast<int>(round & 1u);
+        const uint32_t parity = (round >> 1) & 1u;
+        // this CTA's total for column warp, over that column's warps
+        Fx ta = lane < wpc ? sh.wa[warp + m * lane] : fx_zero();
+        Fx tbx = lane < wpc ? sh.wb[warp + m * lane] : fx_zero();
+        const bool cbad = __any_sync(kFull, lane < wpc ? sh.wbad[warp + m * lane] != 0 : false);
+        ta = fx_warp_sum(ta);
+        tbx = fx_warp_sum(tbx);
+        double ca = fx_to_double(ta), cb = fx_to_double(tbx);
+        if (cbad) ca = cb = __longlong_as_double(0x7ff8000000000000ll);
+        ca = __shfl_sync(kFull, ca, 0);
+        cb = __shfl_sync(kFull, cb, 0);
+        if (warp == 0 && lane == 0) mbar_arrive_expect_tx(&sh.cbar[buf], static_cast<uint32_t>(16 * C * m));
+        if (lane < C)
+            st_async_f64x2(cluster_addr(&sh.cslot[buf][warp][rank], lane), ca, cb, cluster_addr(&sh.cbar[buf], lane));
+        int ok = 1;
+        if (!mbar_try_wait(&sh.cbar[buf], parity)) {
+            const long long deadline = now_ns() + timeout_ns;
+            for (int it = 0;; ++it) {
+                if (mbar_try_wait(&sh.cbar[buf], parity)) break;
+                if ((it & 31) == 31 && (ld_relaxed_i32(d.abort_flag) != 0 || now_ns() > deadline)) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        if (!__all_sync(kFull, ok)) {
+            if (lane == 0) {
+                atomicExch(d.abort_flag, 1);
+                sh.ok = 0;
+            }
+        } else {
+            Fx sa = fx_zero(), sbx = fx_zero();
+            bool gbad = false;
+            if (lane < C) {
+                const double2 v = sh.cslot[buf][warp][lane];
+                sa = fx_from_double(v.x, gbad);
+                sbx = fx_from_double(v.y, gbad);
+            }
+            sa = fx_warp_sum(sa);
+            sbx = fx_warp_sum(sbx);
+            const bool any_bad = __any_sync(kFull, gbad);
+            if (lane == 0) {
+                double At = fx_to_double(sa), Bt = fx_to_double(sbx);
+                if (any_bad) At = Bt = __longlong_as_double(0x7ff8000000000000ll);
+                const int jc = j + warp;
+                const double bj = beta[jc], tj = trust[jc];
+                const double g = d.ytx[jc] - At, q = Bt;
+                int wl = 0;
+                double db = newton_step(g, q, bj, p, tj, wl), r = 1.0, em1 = 0.0;
+                if (nonfinite_bits(db) || nan_bits(g) || nan_bits(q)) {
+                    db = 0.0;
+                    atomicExch(&sh.gnumeric, 1);
+                } else if (db != 0.0) {
+                    const ExpStep es = exp_step(db);
+                    r = es.r;
+                    em1 = es.em1;
+                }
+                if (wl) atomicOr(&sh.gwarn, wl);
+                sh.gdb[warp] = db;
+                sh.gr[warp] = r;
+                sh.gem1[warp] = em1;
+                sh.gnbj[warp] = bj + db;
+            }
+        }
+    }
+    __syncthreads();
+    if (!sh.ok) return false;
+    // phase C: E_k <- E_k e^{db} on the column's rows, D_i <- D_i + (e^{db} - 1) num_i on its subjects
+    const int2 *sseg = sb.segs + cd.seg_off;
+    const int32_t *srow = sb.rows + cd.row_off;
+    for (int c = 0; c < m; ++c) {
+        const double db = sh.gdb[c];
+        if (db == 0.0) continue;
+        const double r = sh.gr[c], em1 = sh.gem1[c];
+        for (int q = go.roff[c] + threadIdx.x; q < go.roff[c + 1]; q += blockDim.x) d.E[srow[q]] = sm.wide.est[q] * r;
+        for (int q = go.soff[c] + threadIdx.x; q < go.soff[c + 1]; q += blockDim.x) {
+            const double2 st = sm.wide.seg_stash[q];
+            d.D[sseg[q].x] = fma(em1, st.x, st.y);
+        }
+    }
+    return true;
+}
+
 // ------------------------------------------------------------------ kernels
 
 // One fit (Algorithm 1) on the CTA that owns shard `s` of `d` (d.S CTAs take part).  F32
@@ -1595,7 +1797,25 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
     long long nonzero = 0;
     double P_prev = 0.0, P = 0.0, conv = 0.0, loglik = 0.0, heldout = __longlong_as_double(0x7ff8000000000000ll);
     long long col = 0;          // wide columns processed: stage buffer = col & 1
-    const bool use_narrow = !F32 && d.narrow != nullptr;
+    // cluster columns (FP64 fits launched in clusters of d.C CTAs): the first cluster's CTAs (s < C)
+    // run every column, the cluster columns over subject shards of their own; the other CTAs run
+    // the grid columns only and wait while the cluster runs the rest
+    const bool use_cluster = !F32 && p.cluster != 0 && d.C > 0 && d.ccls != nullptr;
+    const bool in_cluster = use_cluster && s < d.C;
+    const bool use_narrow = !F32 && !use_cluster && d.narrow != nullptr;
+    unsigned cround = 0;             // cluster all-reduce rounds taken (one per cluster column)
+    unsigned long long crun = 0;     // cluster runs in this launch
+    // the column this CTA takes after j (cyclically), and its slice's bounds
+    // (in the first cluster a cluster column here is a group's first column: the group is one unit)
+    auto next_col = [&](int j) -> int {
+        if (use_narrow) return d.next_wide[j];
+        if (use_cluster && !in_cluster) return d.next_grid[j];
+        const int jn = j + ((in_cluster && d.ccls[j]) ? d.cgroup[j] : 1);
+        return jn < d.J ? jn : 0;
+    };
+    auto col_bounds = [&](int j) -> SliceBounds {
+        return (in_cluster && d.ccls[j]) ? load_bounds_c(d, s, j, d.cgroup[j]) : load_bounds(d, s, j);
+    };
     // Genkin's rule (the paper's Section 2.2 criterion): sum_k |d(Xb)_k| / (1 + sum_k |(Xb)_k|) over
     // a cycle, with (Xb)_k = log(E_k / l_k) and d(Xb)_k = log(E_k / E_k at the cycle's start).
     const bool genkin = !F32 && p.tol_mode == 2 && d.E_prev != nullptr;
@@ -1606,6 +1826,11 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
         if (use_narrow && s == 0) {   // reset before this CTA's first all-reduce arrival
             d.nar_sync[0] = 0ull;
             d.nar_sync[16] = 0ull;
+            __threadfence();
+        }
+        if (use_cluster && s == 0) {
+            d.clu_sync[0] = 0ull;
+            d.clu_sync[16] = 0ull;
             __threadfence();
         }
         mbar_init(&sh.bar[0], 1);
@@ -1620,11 +1845,11 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
     __syncthreads();
     // staging (copies, pending set, next bounds) belongs to the last warp's lane 0
     if (threadIdx.x == static_cast<int>(blockDim.x) - 32 && J > 0 && p.max_cycles > 0 &&
-        (!use_narrow || d.first_wide >= 0)) {
-        const int j0 = use_narrow ? d.first_wide : 0;
-        const SliceBounds b0 = load_bounds(d, s, j0);
+        (!use_narrow || d.first_wide >= 0) && (!use_cluster || in_cluster || d.first_grid >= 0)) {
+        const int j0 = use_narrow ? d.first_wide : (use_cluster && !in_cluster ? d.first_grid : 0);
+        const SliceBounds b0 = col_bounds(j0);
         if (issue_stage(d, b0, sm, sh, 0)) pending |= 1u;
-        nb = load_bounds(d, s, use_narrow ? d.next_wide[j0] : (J > 1 ? 1 : 0));
+        nb = col_bounds(next_col(j0));
     }
     __syncthreads();
 
@@ -1717,6 +1942,59 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     --col;             // the loop's increments: no wide column was processed
                     continue;
                 }
+                const bool clcol = use_cluster && d.ccls[j] != 0;   // a cluster column
+                if (clcol && !in_cluster) {
+                    // a run of cluster columns, taken by the first cluster: arrive (this CTA's writes
+                    // released), wait for the run's end (acquire) while the next grid column's state
+                    // on this shard goes to L2, then add the run's columns to the cycle sums in column
+                    // order (the cluster wrote every shard's copy of their beta)
+                    int j1 = j + 1;
+                    while (j1 < J && d.ccls[j1]) ++j1;
+                    ++crun;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        __threadfence();
+                        atomicAdd(&d.clu_sync[0], 1ull);
+                        sh.ok = wait_counter(&d.clu_sync[16], crun * static_cast<unsigned long long>(d.C),
+                                             d.abort_flag, timeout) ? 1 : 0;
+                    } else if (d.first_grid >= 0) {
+                        prefetch_slice_state_l2(d, s, d.next_grid[j1 - 1], threadIdx.x - 1, blockDim.x - 1);
+                    }
+                    __syncthreads();
+                    if (!sh.ok) goto aborted;
+                    if (threadIdx.x == tb) {
+                        if (pend_j >= 0) {
+                            bookkeep(beta, trust, pend_j, pend_b, pend_t, pend_y, pend_db, lin_c, sq_c, ab_c, nonzero_tb);
+                            pend_j = -1;
+                        }
+                        for (int jj = j; jj < j1; ++jj) {
+                            const double b = beta[jj];
+                            lin_c = fma(b, d.ytx[jj], lin_c);
+                            sq_c = fma(b, b, sq_c);
+                            ab_c += fabs(b);
+                        }
+                    }
+                    j = j1 - 1;
+                    --col;             // the loop's increments: no column was processed here
+                    continue;
+                }
+                const int gm = clcol ? d.cgroup[j] : 1;              // columns taken as one unit
+                const bool run_first = clcol && (j == 0 || !d.ccls[j - 1]);
+                const bool run_last = clcol && (j + gm == J || !d.ccls[j + gm]);
+                if (run_first) {
+                    // entering a cluster run: every CTA of the team has arrived after its last grid
+                    // column's updates (released), so this CTA may read and write any subject
+                    ++crun;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        __threadfence();
+                        atomicAdd(&d.clu_sync[0], 1ull);
+                        sh.ok = wait_counter(&d.clu_sync[0], crun * static_cast<unsigned long long>(d.S), d.abort_flag,
+                                             timeout) ? 1 : 0;
+                    }
+                    __syncthreads();
+                    if (!sh.ok) goto aborted;
+                }
                 const int buf = static_cast<int>(col & 1);
                 double bj = 0.0, tj = 0.0, yj = 0.0;
                 if (threadIdx.x == 0 || threadIdx.x == tb) {
@@ -1737,13 +2015,48 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                 if (threadIdx.x == tb) {
                     // stage the next column, then the deferred bookkeeping of the previous one
                     if (issue_stage(d, nb, sm, sh, buf ^ 1)) pending |= 1u << (buf ^ 1);
-                    const int jn = use_narrow ? d.next_wide[j] : (j + 1 < J ? j + 1 : 0);
-                    const int jnn = use_narrow ? d.next_wide[jn] : (jn + 1 < J ? jn + 1 : 0);
-                    nb = load_bounds(d, s, jnn);
+                    nb = col_bounds(next_col(next_col(j)));
                     if (pend_j >= 0) {
                         bookkeep(beta, trust, pend_j, pend_b, pend_t, pend_y, pend_db, lin_c, sq_c, ab_c, nonzero_tb);
                         pend_j = -1;
                     }
+                }
+                if (clcol) {
+                    // a cluster group: steps, updates, then the bookkeeping of its columns in order
+                    if (!cluster_group(d, p, cd, sh.gofs[buf], sm.stage[buf], sm, sh, s, j, cround, beta, trust, staged_ok,
+                                       timeout))
+                        goto aborted;
+                    ++cround;
+                    if (threadIdx.x == 0) {
+                        if (sh.gnumeric) status = kStNumeric;
+                        warn |= sh.gwarn;
+                    }
+                    if (threadIdx.x == tb)
+                        for (int t = 0; t < gm; ++t)
+                            bookkeep(beta, trust, j + t, beta[j + t], trust[j + t], d.ytx[j + t], sh.gdb[t], lin_c, sq_c,
+                                     ab_c, nonzero_tb);
+                    // the CTAs outside the cluster keep their own copy of beta (for their cycle sums)
+                    for (int t = 0; t < gm; ++t) {
+                        const double nbj = sh.gnbj[t];
+                        for (int q = d.C + s + static_cast<int>(threadIdx.x) * d.C; q < d.S;
+                             q += static_cast<int>(blockDim.x) * d.C)
+                            d.beta_priv[static_cast<long long>(q) * J + j + t] = nbj;
+                    }
+                    __syncthreads();   // E and D writes visible to the next unit's reads
+                    if (run_last) {
+                        // leaving a cluster run: its writes (E, D, every shard's beta) released to the
+                        // team, and the other cluster CTAs' writes acquired before the grid columns
+                        if (threadIdx.x == 0) {
+                            __threadfence();
+                            atomicAdd(&d.clu_sync[16], 1ull);
+                            sh.ok = wait_counter(&d.clu_sync[16], crun * static_cast<unsigned long long>(d.C),
+                                                 d.abort_flag, timeout) ? 1 : 0;
+                        }
+                        __syncthreads();
+                        if (!sh.ok) goto aborted;
+                    }
+                    j += gm - 1;
+                    continue;
                 }
                 Fx ga = fx_zero(), ha = fx_zero();
                 bool bad = false;
@@ -1755,7 +2068,8 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     else phase_a_global32(d, s, j, reinterpret_cast<int *>(&sm.wide), ga, ha, bad);
                 } else {
                     double G = 0.0, H = 0.0;
-                    if (cd.staged) phase_a_staged(d, cd, sm.stage[buf], sm, G, H, bad);
+                    if (cd.staged)
+                        phase_a_staged(d, cd, sm.stage[buf], sm, warp, cd.ngrp, nwarps, 0, 0, cd.nseg, G, H, bad);
                     else phase_a_global<true>(d, s, j, reinterpret_cast<int *>(&sm.wide), G, H, bad);
                     ga = fx_from_double(G, bad);
                     ha = fx_from_double(H, bad);
@@ -1820,8 +2134,12 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     // warps 1..: desc[buf ^ 1] (written by thread tb) is visible after this barrier
                     if (one_warp) named_barrier_all_but_warp0();
                     const ColDesc &nd = sh.desc[buf ^ 1];
-                    // no early L1 copies of state that a narrow run will change first
-                    const bool gap = use_narrow && d.next_wide[j] != (j + 1 < J ? j + 1 : 0);
+                    // no early L1 copies of state that a narrow run, or the other CTAs, will change
+                    // first: the next column of this CTA is taken by another team (cluster / grid),
+                    // or a cluster run comes between
+                    const bool gap = (use_narrow && d.next_wide[j] != (j + 1 < J ? j + 1 : 0)) ||
+                                     (in_cluster && (j + 1 >= J || d.ccls[j] != d.ccls[j + 1])) ||
+                                     (use_cluster && !in_cluster && d.next_grid[j] != j + 1);
                     if (gap && s == 0 && j + 1 < J) {
                         // the next narrow run's first group: its static data, while the
                         // all-reduce runs (E and D are read once the other CTAs arrive)
@@ -1951,7 +2269,25 @@ template <bool F32>
 __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, FitOut *out, double *hist) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ SharedState sh;
+    const bool clustered = p.cluster != 0;
+    if (clustered) {
+        // the cluster all-reduce's mbarriers (one arrival and C x 16 bytes a round) are initialised
+        // in every CTA before any CTA of the cluster can send bytes to them
+        if (threadIdx.x == 0) {
+            mbar_init(&sh.cbar[0], 1);
+            mbar_init(&sh.cbar[1], 1);
+            mbar_init_fence();
+            // the cluster columns take CTA c of the first cluster as cluster shard c: a launch whose
+            // clusters are not runs of consecutive CTAs is refused (every wait then gives up)
+            unsigned cid, crank;
+            asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+            asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+            if (cid * static_cast<unsigned>(d.C) + crank != blockIdx.x) atomicExch(d.abort_flag, 1);
+        }
+        cluster_barrier_all();
+    }
     run_fit<F32>(d, p, out, hist, blockIdx.x, *reinterpret_cast<SmemLayout *>(smem_raw), sh);
+    if (clustered) cluster_barrier_all();   // no CTA exits while another may still write its shared memory
 }
 
 // E_k = l_k exp(Xb_k) on shard s's rows, with Xb_k summed over row k's columns in ascending j;
@@ -2318,6 +2654,8 @@ int ensure_smem_attr() {
     const int bytes = static_cast<int>(sizeof(SmemLayout));
     cudaError_t e = cudaFuncSetAttribute(fit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)   // clusters of 16 CTAs are past the portable size of 8
+        e = cudaFuncSetAttribute(fit_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fit_queue_kernel<kBatchFp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
@@ -2396,10 +2734,52 @@ int launch_fit(const DevLayout &d, const FitParams &p, FitOut *out_dev, double *
     if (e) return e;
     DevLayout dd = d;
     FitParams pp = p;
+    // FP64 fits of a layout with cluster columns launch in clusters of d.C CTAs
+    pp.cluster = (!fp32 && d.C > 0 && d.S % d.C == 0) ? 1 : 0;
     void *args[] = {&dd, &pp, &out_dev, &hist_dev};
     void *fn = fp32 ? reinterpret_cast<void *>(fit_kernel<true>) : reinterpret_cast<void *>(fit_kernel<false>);
-    return static_cast<int>(cudaLaunchCooperativeKernel(fn, dim3(d.S), dim3(threads), args, sizeof(SmemLayout),
-                                                         static_cast<cudaStream_t>(stream)));
+    if (!pp.cluster)
+        return static_cast<int>(cudaLaunchCooperativeKernel(fn, dim3(d.S), dim3(threads), args, sizeof(SmemLayout),
+                                                             static_cast<cudaStream_t>(stream)));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(d.S);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = sizeof(SmemLayout);
+    cfg.stream = static_cast<cudaStream_t>(stream);
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = static_cast<unsigned>(d.C);
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return static_cast<int>(cudaLaunchKernelExC(&cfg, fn, args));
+}
+
+int fit_kernel_max_clusters(int threads, int cluster, int *clusters) {
+    *clusters = 0;
+    int e = ensure_smem_attr();
+    if (e) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(static_cast<unsigned>(cluster));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = sizeof(SmemLayout);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(cluster);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t ce = cudaOccupancyMaxActiveClusters(clusters, reinterpret_cast<const void *>(fit_kernel<false>), &cfg);
+    if (ce != cudaSuccess) {
+        (void)cudaGetLastError();
+        *clusters = 0;
+        return static_cast<int>(ce);
+    }
+    return 0;
 }
 
 int launch_fit_queue(const BatchEntry *entries_dev, const int *team_start_dev, int n, unsigned *counters_dev,

@@ -191,6 +191,7 @@ FitSlot *make_slot(const sccs_handle *dataset, int max_cycles) {
     auto *nsync = reinterpret_cast<unsigned long long *>(take(256));
     d.E_prev = reinterpret_cast<double *>(take(8 * std::max<size_t>(K, 1)));   // Genkin's X-beta test
     if (d.narrow) d.nar_sync = nsync;   // the slot's own narrow-run counters
+    if (d.C > 0) d.clu_sync = nsync + 8;   // and cluster-run counters ([8] and [24] of the same 256 bytes)
     s->ytx_ho = reinterpret_cast<double *>(take(8 * J));
     d.estash = reinterpret_cast<double *>(take(8 * S * static_cast<size_t>(d.estash_stride)));
     d.abort_flag = &s->out_dev->abort_flag;

@@ -33,7 +33,8 @@ class sccs_create_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("num_shards", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("alloc", _alloc_fn), ("free", _free_fn), ("alloc_ctx", ctypes.c_void_p),
-                ("narrow_max_nnz", ctypes.c_int32), ("narrow_group_max", ctypes.c_int32)]
+                ("narrow_max_nnz", ctypes.c_int32), ("narrow_group_max", ctypes.c_int32),
+                ("cluster_ctas", ctypes.c_int32), ("cluster_max_nnz", ctypes.c_int32)]
 
 
 class sccs_data_info(ctypes.Structure):
@@ -42,7 +43,8 @@ class sccs_data_info(ctypes.Structure):
                 ("max_column_nnz", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("upload_bytes", ctypes.c_int64),
                 ("columns", ctypes.c_int32), ("num_shards", ctypes.c_int32),
-                ("threads_per_block", ctypes.c_int32), ("narrow_columns", ctypes.c_int32)]
+                ("threads_per_block", ctypes.c_int32), ("narrow_columns", ctypes.c_int32),
+                ("cluster_ctas", ctypes.c_int32), ("cluster_columns", ctypes.c_int32)]
 
 
 class sccs_fit_opts(ctypes.Structure):
@@ -165,7 +167,8 @@ def sccs_last_error(handle) -> str:
 
 
 def sccs_create(K, patient_id, y, offset_L, J, col_ptr, row_idx, x_values=None, *, device=0, stream=None,
-                num_shards=0, threads_per_block=0, narrow_max_nnz=0, narrow_group_max=0):
+                num_shards=0, threads_per_block=0, narrow_max_nnz=0, narrow_group_max=0, cluster_ctas=0,
+                cluster_max_nnz=0):
     """Returns an opaque handle (int).  Arrays are copied by the library before it returns."""
     pid = np.ascontiguousarray(patient_id, np.int64)
     yy = np.ascontiguousarray(y, np.int32)
@@ -175,7 +178,8 @@ def sccs_create(K, patient_id, y, offset_L, J, col_ptr, row_idx, x_values=None, 
     xv = None if x_values is None else np.ascontiguousarray(x_values, np.float64)
     o = sccs_create_opts(struct_size=ctypes.sizeof(sccs_create_opts), device=int(device),
                          stream=stream, num_shards=int(num_shards), threads_per_block=int(threads_per_block),
-                         narrow_max_nnz=int(narrow_max_nnz), narrow_group_max=int(narrow_group_max))
+                         narrow_max_nnz=int(narrow_max_nnz), narrow_group_max=int(narrow_group_max),
+                         cluster_ctas=int(cluster_ctas), cluster_max_nnz=int(cluster_max_nnz))
     h = ctypes.c_void_p()
     _check(_lib.sccs_create(ctypes.byref(h), int(K), _ptr(pid), _ptr(yy), _ptr(LL), int(J), _ptr(cp), _ptr(ri),
                             _ptr(xv), ctypes.byref(o)), "sccs_create")
@@ -418,7 +422,7 @@ class SCCSModel:
 
     def __init__(self, data=None, *, K=None, patient_id=None, y=None, L=None, J=None, col_ptr=None,
                  row_idx=None, x_values=None, device=0, stream="torch", num_shards=0, threads_per_block=0,
-                 narrow_max_nnz=0, narrow_group_max=0):
+                 narrow_max_nnz=0, narrow_group_max=0, cluster_ctas=0, cluster_max_nnz=0):
         if data is not None:
             K, patient_id, y, L, J = data.K, data.patient_id, data.y, data.L, data.J
             col_ptr, row_idx = data.col_ptr, data.row_idx
@@ -427,7 +431,8 @@ class SCCSModel:
         self.device = int(device)
         self.handle = sccs_create(K, patient_id, y, L, J, col_ptr, row_idx, x_values, device=device, stream=st,
                                   num_shards=num_shards, threads_per_block=threads_per_block,
-                                  narrow_max_nnz=narrow_max_nnz, narrow_group_max=narrow_group_max)
+                                  narrow_max_nnz=narrow_max_nnz, narrow_group_max=narrow_group_max,
+                                  cluster_ctas=cluster_ctas, cluster_max_nnz=cluster_max_nnz)
 
     def close(self):
         if getattr(self, "handle", None):

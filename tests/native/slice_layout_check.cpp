@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <map>
+#include <iterator>
 #include <random>
 
 static long long g_bad = 0;
@@ -27,6 +28,8 @@ int main(int argc, char **argv) {
     const unsigned seed = argc > 3 ? static_cast<unsigned>(atoi(argv[3])) : 5u;
     const int S = argc > 4 ? atoi(argv[4]) : 7;
     const bool messy = argc > 5 ? atoi(argv[5]) != 0 : true;   // dropped subjects, shuffled columns
+    const int C = argc > 6 ? atoi(argv[6]) : 0;                 // cluster partition (0: none)
+    const int64_t cmax = argc > 7 ? atoll(argv[7]) : 0;         // cluster columns: at most this many nonzeros
     std::mt19937_64 rng(seed);
     std::vector<int64_t> pid;
     std::vector<int32_t> y;
@@ -61,7 +64,7 @@ int main(int argc, char **argv) {
         cp[j + 1] = static_cast<int64_t>(ri.size());
     }
     HostLayout hl;
-    if (build_layout(K, pid.data(), y.data(), L.data(), J, cp.data(), ri.data(), S, 1024, 8, hl)) {
+    if (build_layout(K, pid.data(), y.data(), L.data(), J, cp.data(), ri.data(), S, 1024, 8, hl, C, cmax)) {
         printf("build_layout failed: %s\n", g_last_error.c_str());
         return 2;
     }
@@ -121,53 +124,155 @@ int main(int argc, char **argv) {
     }
     CHECK(hl.nnz == nnz, "nnz\n");
 
-    // ---- slices
-    int64_t max_seg = 1, max_rows = 1;
-    for (int s = 0; s < S; ++s) {
-        const int64_t r0 = hl.shard_row[s], r1 = hl.shard_row[s + 1];
-        CHECK(r0 == hl.pat_ptr[hl.shard_pat[s]], "shard_row[%d]\n", s);
-        for (int j = 0; j < J; ++j) {
-            const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
-            std::vector<int32_t> rows;
-            for (int32_t r : colrows[j])
-                if (r >= r0 && r < r1) rows.push_back(r);
-            // subjects in ascending order with their rows (ascending)
-            std::vector<std::pair<int32_t, std::vector<int32_t>>> segs;
-            for (int32_t r : rows) {
-                if (segs.empty() || segs.back().first != kept_sub[r]) segs.push_back({kept_sub[r], {}});
-                segs.back().second.push_back(r);
-            }
-            std::stable_sort(segs.begin(), segs.end(),
-                             [](const auto &a, const auto &b) { return a.second.size() > b.second.size(); });
-            const int64_t nr = hl.slice_row[idx + 1] - hl.slice_row[idx];
-            const int64_t ns = hl.slice_seg[idx + 1] - hl.slice_seg[idx];
-            CHECK(nr == static_cast<int64_t>(rows.size()), "slice rows s%d j%d\n", s, j);
-            CHECK(ns == static_cast<int64_t>(segs.size()), "slice segs s%d j%d\n", s, j);
-            CHECK(hl.slice_grp[idx + 1] - hl.slice_grp[idx] == (ns + 31) / 32, "slice groups s%d j%d\n", s, j);
-            max_seg = std::max<int64_t>(max_seg, ns);
-            max_rows = std::max<int64_t>(max_rows, nr);
-            if (nr != static_cast<int64_t>(rows.size()) || ns != static_cast<int64_t>(segs.size())) continue;
-            for (int64_t i = 0; i < ns; ++i) {
-                const int2 sg = hl.segs[hl.slice_seg[idx] + i];
-                CHECK(sg.x == segs[i].first && sg.y == static_cast<int>(segs[i].second.size()), "seg s%d j%d i%lld\n", s,
-                      j, (long long)i);
-            }
-            int64_t pos = hl.slice_row[idx];
-            for (int64_t g = 0; g * 32 < ns; ++g) {
-                CHECK(hl.grp_base[hl.slice_grp[idx] + g] == pos, "grp_base s%d j%d g%lld\n", s, j, (long long)g);
-                const int64_t a = 32 * g, b = std::min<int64_t>(ns, a + 32);
-                const size_t maxlen = segs[a].second.size();
-                for (size_t t = 0; t < maxlen; ++t)
-                    for (int64_t l = a; l < b; ++l)
-                        if (segs[l].second.size() > t) {
-                            CHECK(hl.rows[pos] == segs[l].second[t], "row s%d j%d pos%lld\n", s, j, (long long)pos);
-                            ++pos;
-                        }
+    // ---- slices of one partition (S shards, or the C cluster shards) of the columns in_set
+    auto check_slices = [&](const char *tag, int S_, const std::vector<int64_t> &shard_row, const std::vector<int64_t> &shard_pat,
+                            const std::vector<int64_t> &slice_row, const std::vector<int64_t> &slice_seg,
+                            const std::vector<int64_t> &slice_grp, const HostBuf<int32_t> &hrows, const HostBuf<int2> &hsegs,
+                            const HostBuf<int64_t> &hgrp, auto in_set, int64_t &max_seg, int64_t &max_rows) {
+        max_seg = 1;
+        max_rows = 1;
+        CHECK(shard_row[0] == 0 && shard_row[S_] == Kk && shard_pat[S_] == Nk, "%s shard ends\n", tag);
+        for (int s = 0; s < S_; ++s) {
+            const int64_t r0 = shard_row[s], r1 = shard_row[s + 1];
+            CHECK(r0 == hl.pat_ptr[shard_pat[s]], "%s shard_row[%d]\n", tag, s);
+            CHECK(r0 <= r1, "%s shard order %d\n", tag, s);
+            for (int j = 0; j < J; ++j) {
+                const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
+                std::vector<int32_t> rows;
+                if (in_set(j))
+                    for (int32_t r : colrows[j])
+                        if (r >= r0 && r < r1) rows.push_back(r);
+                // subjects in ascending order with their rows (ascending)
+                std::vector<std::pair<int32_t, std::vector<int32_t>>> segs;
+                for (int32_t r : rows) {
+                    if (segs.empty() || segs.back().first != kept_sub[r]) segs.push_back({kept_sub[r], {}});
+                    segs.back().second.push_back(r);
+                }
+                std::stable_sort(segs.begin(), segs.end(),
+                                 [](const auto &a, const auto &b) { return a.second.size() > b.second.size(); });
+                const int64_t nr = slice_row[idx + 1] - slice_row[idx];
+                const int64_t ns = slice_seg[idx + 1] - slice_seg[idx];
+                CHECK(nr == static_cast<int64_t>(rows.size()), "%s slice rows s%d j%d\n", tag, s, j);
+                CHECK(ns == static_cast<int64_t>(segs.size()), "%s slice segs s%d j%d\n", tag, s, j);
+                CHECK(slice_grp[idx + 1] - slice_grp[idx] == (ns + 31) / 32, "%s slice groups s%d j%d\n", tag, s, j);
+                max_seg = std::max<int64_t>(max_seg, ns);
+                max_rows = std::max<int64_t>(max_rows, nr);
+                if (nr != static_cast<int64_t>(rows.size()) || ns != static_cast<int64_t>(segs.size())) continue;
+                for (int64_t i = 0; i < ns; ++i) {
+                    const int2 sg = hsegs[slice_seg[idx] + i];
+                    CHECK(sg.x == segs[i].first && sg.y == static_cast<int>(segs[i].second.size()), "%s seg s%d j%d i%lld\n",
+                          tag, s, j, (long long)i);
+                }
+                int64_t pos = slice_row[idx];
+                for (int64_t g = 0; g * 32 < ns; ++g) {
+                    CHECK(hgrp[slice_grp[idx] + g] == pos, "%s grp_base s%d j%d g%lld\n", tag, s, j, (long long)g);
+                    const int64_t a = 32 * g, b = std::min<int64_t>(ns, a + 32);
+                    const size_t maxlen = segs[a].second.size();
+                    for (size_t t = 0; t < maxlen; ++t)
+                        for (int64_t l = a; l < b; ++l)
+                            if (segs[l].second.size() > t) {
+                                CHECK(hrows[pos] == segs[l].second[t], "%s row s%d j%d pos%lld\n", tag, s, j, (long long)pos);
+                                ++pos;
+                            }
+                }
             }
         }
+    };
+    int64_t max_seg = 1, max_rows = 1;
+    check_slices("grid", S, hl.shard_row, hl.shard_pat, hl.slice_row, hl.slice_seg, hl.slice_grp, hl.rows, hl.segs,
+                 hl.grp_base, [](int) { return true; }, max_seg, max_rows);
+    // ---- cluster columns: every column with at most cmax nonzeros whose slices over the C cluster
+    //      shards all fit the staging caps, their slices there, and the next-grid-column map
+    int64_t ccount = 0;
+    if (C > 0) {
+        CHECK(hl.C == C, "cluster size\n");
+        std::vector<int64_t> cpat(static_cast<size_t>(C) + 1), crow_b(static_cast<size_t>(C) + 1);
+        for (int c = 0; c <= C; ++c) {
+            cpat[c] = hl.cshard_pat[c];
+            crow_b[c] = hl.cshard_row[c];
+        }
+        for (int j = 0; j < J; ++j) {
+            bool want = static_cast<int64_t>(colrows[j].size()) <= cmax;
+            for (int c = 0; want && c < C; ++c) {
+                std::vector<int32_t> subs;
+                int64_t nr = 0;
+                for (int32_t r : colrows[j])
+                    if (r >= crow_b[c] && r < crow_b[c + 1]) {
+                        ++nr;
+                        if (subs.empty() || subs.back() != kept_sub[r]) subs.push_back(kept_sub[r]);
+                    }
+                if (nr > sccs::kRowCap || static_cast<int64_t>(subs.size()) > sccs::kSegCap) want = false;
+            }
+            CHECK(hl.ccls[j] == (want ? 1 : 0), "cluster class of column %d\n", j);
+            ccount += want ? 1 : 0;
+        }
+        CHECK(hl.cluster_count == ccount, "cluster count\n");
+        int64_t cms = 1, cmr = 1;
+        check_slices("cluster", C, crow_b, cpat, hl.cslice_row, hl.cslice_seg, hl.cslice_grp, hl.crows, hl.csegs,
+                     hl.cgrp_base, [&](int j) { return hl.ccls[j] != 0; }, cms, cmr);
+        // groups: greedy runs of consecutive cluster columns, pairwise disjoint in subjects, at most
+        // gmax, whose slices on every cluster shard fit the staging caps together
+        const int gmax = 8;
+        auto subjects = [&](int j) {
+            std::vector<int32_t> v;
+            for (int32_t r : colrows[j]) v.push_back(kept_sub[r]);
+            std::sort(v.begin(), v.end());
+            v.erase(std::unique(v.begin(), v.end()), v.end());
+            return v;
+        };
+        for (int j = 0; j < J;) {
+            if (!hl.ccls[j]) {
+                CHECK(hl.cgroup[j] == 0, "cgroup of grid column %d\n", j);
+                ++j;
+                continue;
+            }
+            std::vector<int32_t> used = subjects(j);
+            std::vector<int64_t> rs(static_cast<size_t>(C), 0), ss(static_cast<size_t>(C), 0);
+            auto add_counts = [&](int jj, std::vector<int64_t> &r_, std::vector<int64_t> &s_) {
+                for (int c = 0; c < C; ++c) {
+                    std::vector<int32_t> sb;
+                    for (int32_t r : colrows[jj])
+                        if (r >= crow_b[c] && r < crow_b[c + 1]) {
+                            r_[c]++;
+                            if (sb.empty() || sb.back() != kept_sub[r]) sb.push_back(kept_sub[r]);
+                        }
+                    s_[c] += static_cast<int64_t>(sb.size());
+                }
+            };
+            add_counts(j, rs, ss);
+            int m = 1;
+            while (j + m < J && hl.ccls[j + m] && m < gmax) {
+                std::vector<int32_t> sj = subjects(j + m), both;
+                std::set_intersection(used.begin(), used.end(), sj.begin(), sj.end(), std::back_inserter(both));
+                std::vector<int64_t> r2 = rs, s2 = ss;
+                add_counts(j + m, r2, s2);
+                bool fits = both.empty();
+                for (int c = 0; c < C && fits; ++c) fits = r2[c] <= sccs::kRowCap && s2[c] <= sccs::kSegCap;
+                if (!fits) break;
+                std::vector<int32_t> u2;
+                std::set_union(used.begin(), used.end(), sj.begin(), sj.end(), std::back_inserter(u2));
+                used.swap(u2);
+                rs.swap(r2);
+                ss.swap(s2);
+                ++m;
+            }
+            CHECK(hl.cgroup[j] == m, "cgroup at %d: %d != %d\n", j, hl.cgroup[j], m);
+            for (int t = 1; t < m; ++t) CHECK(hl.cgroup[j + t] == 0, "cgroup inside a group at %d\n", j + t);
+            j += m;
+        }
+    }
+    int32_t first_grid = -1;
+    for (int j = 0; j < J && first_grid < 0; ++j)
+        if (!hl.ccls[j]) first_grid = j;
+    CHECK(hl.first_grid == first_grid, "first grid column\n");
+    for (int j = 0; j < J; ++j) {
+        int32_t nx = -1;
+        for (int t = 1; t <= J && nx < 0; ++t)
+            if (!hl.ccls[(j + t) % J]) nx = (j + t) % J;
+        CHECK(hl.next_grid[j] == nx, "next grid column after %d\n", j);
     }
     CHECK(hl.stash_stride == max_seg && hl.estash_stride == max_rows, "stash strides\n");
-    printf("subjects %lld kept %lld rows %lld nnz %lld shards %d columns %d mismatches %lld\n", (long long)nin,
-           (long long)Nk, (long long)Kk, (long long)nnz, S, J, g_bad);
+    printf("subjects %lld kept %lld rows %lld nnz %lld shards %d columns %d cluster_columns %lld mismatches %lld\n",
+           (long long)nin, (long long)Nk, (long long)Kk, (long long)nnz, S, J, (long long)ccount, g_bad);
     return g_bad ? 1 : 0;
 }

@@ -65,13 +65,24 @@ def slice_checker(tmp_path_factory):
     return exe
 
 
-@pytest.mark.parametrize("nsub,J,seed,S,messy", [(8000, 120, 5, 7, 1), (8000, 120, 6, 7, 0), (3000, 60, 7, 1, 1),
-                                                  (20000, 90, 8, 33, 1), (500, 40, 9, 4, 0)])
-def test_slice_layout_against_brute_force(slice_checker, nsub, J, seed, S, messy):
+@pytest.mark.parametrize("nsub,J,seed,S,messy,C,cmax", [(8000, 120, 5, 7, 1, 0, 0), (8000, 120, 6, 7, 0, 0, 0),
+                                                         (3000, 60, 7, 1, 1, 0, 0), (20000, 90, 8, 33, 1, 0, 0),
+                                                         (500, 40, 9, 4, 0, 0, 0), (8000, 120, 10, 32, 1, 16, 300),
+                                                         (20000, 90, 11, 24, 0, 8, 100000),
+                                                         (6000, 50, 12, 8, 1, 4, 5000), (3000, 30, 13, 8, 1, 8, 10**9)])
+def test_slice_layout_against_brute_force(slice_checker, nsub, J, seed, S, messy, C, cmax):
     """The whole host layout -- kept subjects and rows, per-column kept rows, Y'X_j and event
     pairs, every (shard, column) slice's segments, diagonal-major rows and group bases -- against
-    a brute-force construction, with dropped subjects and shuffled columns (messy) or without."""
-    r = subprocess.run([slice_checker, str(nsub), str(J), str(seed), str(S), str(messy)], capture_output=True,
-                       text=True, timeout=600)
+    a brute-force construction, with dropped subjects and shuffled columns (messy) or without; with
+    C > 0 also the cluster columns (at most cmax nonzeros and every slice over the C cluster shards
+    within the staging caps), their slices over those shards, and the next-grid-column map."""
+    r = subprocess.run([slice_checker, str(nsub), str(J), str(seed), str(S), str(messy), str(C), str(cmax)],
+                       capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "mismatches 0" in r.stdout
+    if C:
+        words = r.stdout.split()
+        ncl = int(words[words.index("cluster_columns") + 1])
+        assert 0 < ncl <= J, r.stdout
+        if cmax < 10**6:
+            assert ncl < J, r.stdout   # both kinds of column occur
