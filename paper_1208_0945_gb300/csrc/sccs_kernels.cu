@@ -48,6 +48,11 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBatch = 8;        // diagonals gathered per batch
 constexpr int kMaxWarps = 32;
 constexpr int kFrac = 128;       // fraction bits of the fixed-point sums (value = V * 2^-128)
+// E_k <- E_k e^{db} rounds once per update; every so many cycles E is rebuilt from beta instead
+// (FP64: at most 1.5 ulp per update, so 64 cycles of a row in c columns drift <= 96 c ulp; FP32
+// rounds 2^29 times coarser, so it is rebuilt 4 times as often)
+constexpr int kRebuildCycles64 = 64;
+constexpr int kRebuildCycles32 = 16;
 
 // status values written to FitOut
 constexpr int kStOk = 0;
@@ -1777,6 +1782,9 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
 
 // ------------------------------------------------------------------ kernels
 
+__device__ void init_shard(const DevLayout &d, int s, const double *beta0, bool keep_trust);
+__device__ void e_to_f32_shard(const DevLayout &d, int s);
+
 // One fit (Algorithm 1) on the CTA that owns shard `s` of `d` (d.S CTAs take part).  F32
 // selects the FP32 mode; the scalar step is FP64 in both.
 template <bool F32>
@@ -2137,10 +2145,10 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     // no early L1 copies of state that a narrow run, or the other CTAs, will change
                     // first: the next column of this CTA is taken by another team (cluster / grid),
                     // or a cluster run comes between
-                    const bool gap = (use_narrow && d.next_wide[j] != (j + 1 < J ? j + 1 : 0)) ||
-                                     (in_cluster && (j + 1 >= J || d.ccls[j] != d.ccls[j + 1])) ||
+                    const bool narrow_gap = use_narrow && d.next_wide[j] != (j + 1 < J ? j + 1 : 0);
+                    const bool gap = narrow_gap || (in_cluster && (j + 1 >= J || d.ccls[j] != d.ccls[j + 1])) ||
                                      (use_cluster && !in_cluster && d.next_grid[j] != j + 1);
-                    if (gap && s == 0 && j + 1 < J) {
+                    if (narrow_gap && s == 0 && j + 1 < J) {
                         // the next narrow run's first group: its static data, while the
                         // all-reduce runs (E and D are read once the other CTAs arrive)
                         narrow_gather_static(d, j + 1, threadIdx.x - 32, blockDim.x - 32, sm.nar_hi);
@@ -2189,6 +2197,12 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                 sh.nonzero = nonzero_tb;
             }
             __syncthreads();
+            if (c % (F32 ? kRebuildCycles32 : kRebuildCycles64) == 0 && d.row_ptr) {
+                // bound the rounding drift of the multiplicative updates: E from this CTA's beta copy
+                // (every copy holds the same beta), then D and P from it below
+                init_shard(d, s, beta, true);
+                if (F32) e_to_f32_shard(d, s);
+            }
             if (!(F32 ? refresh_and_reduce32(d, s, seq++, timeout, sh) : refresh_and_reduce(d, s, seq++, timeout, sh)))
                 goto aborted;
             const double nlogG = sh.G, nlogH = sh.H;   // the refresh's totals (sh.G/H are reused below)

@@ -93,3 +93,22 @@ def test_cluster_options_validated(P):
         assert m.info["cluster_ctas"] == 0 and m.info["cluster_columns"] == 0
     with P.SCCSModel(d, device=0) as m:                             # default team: clusters of 16
         assert m.info["cluster_ctas"] == 16 and m.info["num_shards"] % 16 == 0
+
+
+def test_cluster_and_grid_columns_without_narrow_columns(P):
+    """Every column above the narrow size (so the layout has no narrow arrays), some on the
+    cluster and some on the whole team: the grid columns next to cluster runs must not touch the
+    narrow path.  Three cycles against the oracle."""
+    d = make_dataset(n_patients=60000, eras=("geometric", 8), J=60, columns=("density_range", 0.004, 0.04),
+                     n_true=4, beta_sd=0.3, seed=41)
+    nnz = np.diff(d.col_ptr)
+    assert nnz.min() > 1024
+    ref = oracle.Problem.from_data(d).fit(prior="normal", variance=0.5, fixed_cycles=3)
+    cmax = int(np.median(nnz))
+    with P.SCCSModel(d, device=0, cluster_ctas=16, cluster_max_nnz=cmax) as m:
+        info = m.info
+        assert info["narrow_columns"] == 0 and 0 < info["cluster_columns"] < d.J
+        m.set_prior("normal", 0.5)
+        r = m.fit(tol=-1.0, max_cycles=3)
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11, rtol=0)
+    assert rel(r["logpost"], ref["logpost"]) <= 1e-12
