@@ -66,6 +66,46 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def load_fp64_peak():
+    """FP64 FMA throughput of the GPU in GFLOP/s (measured on this machine, profiles/fp64_fma_peak.json)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp64_fma_peak.json")) as f:
+            return float(json.load(f)["fp64_gflops"]), "measured"
+    except Exception:
+        return 1000.0, "fallback"
+
+
+def fp64_flops(d, cycles, nonzero_frac=1.0):
+    """FP64 flops the fit must execute per launch (FMA = 2): per coordinate step, phase A's
+    nnz + 13 P (per segment the quotient 9, n w 1, n w (1 - w) 2, the two running sums 2; one add
+    per further row of a segment) and, when db != 0, phase C's nnz + 2 P (E e^db per row, the
+    D update by FMA per segment); per cycle end K adds and about 21 per subject for n_i log D_i."""
+    nnz, segs = d["nnz_kept"], d["segments"]
+    K, N = d["rows_kept"], d["subjects_kept"]
+    per_cycle = (nnz + 13 * segs) + nonzero_frac * (nnz + 2 * segs) + K + 21 * N
+    return cycles * per_cycle + K + 21 * N
+
+
+def roofline(bytes_launch, flops_launch, kern_ms, kernel, traffic=None, fp64=True):
+    """Both roofs of the dominant kernel: HBM (algorithmic bytes / time against the measured copy
+    bandwidth) and, for FP64 arithmetic, the FP64 ALU (algorithmic flops / time against the
+    measured FP64 FMA rate); the one closer to its peak is reported as the bound."""
+    peak, peak_kind = load_peaks()
+    hbm = bytes_launch / (kern_ms / 1e3) / 1e9
+    out = {"bound": "hbm", "achieved": hbm, "peak": peak, "unit": "GB/s", "frac": hbm / peak, "traffic": traffic,
+           "kernel": kernel, "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_kind}
+    if fp64 and flops_launch:
+        fpk, fpk_kind = load_fp64_peak()
+        alu = flops_launch / (kern_ms / 1e3) / 1e12
+        out["hbm"] = {"achieved": hbm, "peak": peak, "unit": "GB/s", "frac": hbm / peak, "peak_source": peak_kind}
+        out["fp64"] = {"achieved": alu, "peak": fpk / 1e3, "unit": "TFLOP/s", "frac": alu / (fpk / 1e3),
+                       "algorithmic_flops_per_launch": flops_launch, "peak_source": fpk_kind}
+        if alu / (fpk / 1e3) > hbm / peak:
+            out.update({"bound": "alu", "achieved": alu, "peak": fpk / 1e3, "unit": "TFLOP/s",
+                        "frac": alu / (fpk / 1e3), "peak_source": fpk_kind})
+    return out
+
+
 def algorithmic_bytes(d, cycles, nonzero_frac=1.0):
     """Bytes the fit must move per launch (see the design notes): per coordinate step
     20 B per nonzero (4 index + 8 E read + 8 E write) and 28 B per touched subject
@@ -248,8 +288,7 @@ def run_ours(args, rank, world, local):
     kern_ms = statistics.mean(r["kernel_ms"] for r in results)
     nz_frac = statistics.mean(r["nonzero_steps"] / max(1, r["steps"]) for r in results)
     bytes_launch = algorithmic_bytes(info, statistics.mean(cycles), nz_frac)
-    peak, peak_kind = load_peaks()
-    achieved = bytes_launch / (kern_ms / 1e3) / 1e9
+    flops_launch = fp64_flops(info, statistics.mean(cycles), nz_frac)
     clocks = clk.summary()
 
     # end to end through the C ABI from host arrays: create (validate, lay out, upload),
@@ -286,11 +325,8 @@ def run_ours(args, rank, world, local):
                     "kernel_ms": kern_ms, "nnz_steps_per_s": info["nnz_kept"] * cycles[0] / (kern_ms / 1e3),
                     "shards": info["num_shards"], "threads_per_block": info["threads_per_block"],
                     "wall_s": wall},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": recorded_traffic() if args.scale == 1.0 else None,
-                         "kernel": "fit_kernel (one persistent launch per fit)",
-                         "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_kind},
+            "roofline": roofline(bytes_launch, flops_launch, kern_ms, "fit_kernel (one persistent launch per fit)",
+                                 recorded_traffic() if args.scale == 1.0 else None),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms_max,
                     "what": "sccs_create from host arrays (validate, lay out, upload) + sccs_fit + beta D2H + destroy"},
@@ -437,12 +473,11 @@ def run_batched(args, rank, world, local):
     same_cycles = sum(1 for a, b in zip(res, seq_res) if a["cycles"] == b["cycles"])
     max_dlogpost = max(abs(a["logpost"] - b["logpost"]) / max(1.0, abs(b["logpost"])) for a, b in zip(res, seq_res))
 
-    total_bytes = 0.0
+    total_bytes = total_flops = 0.0
     for info, r in zip(infos, res):
         nz = r["nonzero_steps"] / max(1, r["steps"])
         total_bytes += algorithmic_bytes(info, r["cycles"], nz)
-    peak, peak_kind = load_peaks()
-    achieved = total_bytes / (statistics.mean(step_ms) / 1e3) / 1e9
+        total_flops += fp64_flops(info, r["cycles"], nz)
 
     cpu = None
     if cpu_sample:
@@ -477,9 +512,8 @@ def run_batched(args, rank, world, local):
                               "speedup_of_batch": seq_ms / ms,
                               "same_cycles": f"{same_cycles}/{n}",
                               "max_rel_logpost_diff": max_dlogpost},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "fit_queue_kernel (one launch per batch)",
-                         "algorithmic_bytes_per_launch": total_bytes, "peak_source": peak_kind},
+            "roofline": roofline(total_bytes, total_flops, statistics.mean(step_ms),
+                                 "fit_queue_kernel (one launch per batch)"),
             "e2e": {"value": n / (statistics.mean(walls) / 1e3), "unit": "fits/s",
                     "h2d_bytes_per_step": None, "d2h_bytes_per_step": int(sum(8 * J for J in Js)),
                     "what": "sccs_fit_batch wall time: per-fit entries staged, graph launched, results and betas "
@@ -681,8 +715,7 @@ def run_paper(args, rank, world, local):
     nz32 = r32["nonzero_steps"] / max(1, r32["steps"])
     fp32_c = r32["fp32_cycles"]
     bytes32 = algorithmic_bytes32(info, fp32_c, nz32) + algorithmic_bytes(info, r32["cycles"] - fp32_c, nz32)
-    peak, peak_kind = load_peaks()
-    achieved = bytes32 / (ms32 / 1e3) / 1e9
+    flops_polish = fp64_flops(info, r32["cycles"] - fp32_c, nz32)
     if rank == 0:
         line = {
             "metric": "coord-updates/s (paper-scale SCCS MAP fit, FP32 compensated + FP64 polish)",
@@ -708,13 +741,79 @@ def run_paper(args, rank, world, local):
                               "zero_pattern_identical": zero_same,
                               "reference": "the same fit in FP64 on the GPU (which matches the oracle to 1e-8 "
                                            "at reduced scale in the tests)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "fit_kernel (FP32 phase then FP64 polish)",
-                         "algorithmic_bytes_per_launch": bytes32, "peak_source": peak_kind},
+            "roofline": roofline(bytes32, flops_polish, ms32, "fit_kernel (FP32 phase then FP64 polish)"),
             "e2e": {"value": None, "unit": "coord-updates/s", "h2d_bytes_per_step": int(info["upload_bytes"]),
                     "d2h_bytes_per_step": 8 * d.J, "what": f"create {t_create:.1f} s, not repeated per step"},
             "gpu_launches": 6 * args.steps,
             "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    model.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_large_columns(args, rank, world, local):
+    """The regime where HBM or the FP64 ALU can bind a coordinate step: 1M subjects and 16 drug
+    columns of 1M to 2M nonzeros each.  FP64 fits (against the FP64-ALU and HBM roofs) and FP32
+    cycles (against HBM), a fixed number of cycles per step."""
+    import ctypes
+    import torch
+    import paper_1208_0945_gb300 as sccs
+    from synth import large_columns_config
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    d, fit = large_columns_config(scale=args.scale)
+    stream = torch.cuda.current_stream(dev)
+    model = sccs.SCCSModel(d, device=local, stream=ctypes.c_void_p(stream.cuda_stream))
+    model.set_prior(fit["prior"], fit["variance"])
+    info = model.info
+    cycles = fit["cycles"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    with ClockSampler(local) as clk:
+        for prec in ("fp64", "fp32"):
+            for _ in range(args.warmup):
+                model.fit(precision=prec, tol=-1.0, max_cycles=cycles)
+            rs = []
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                torch.cuda.synchronize(dev)
+                rs.append(model.fit(precision=prec, tol=-1.0, max_cycles=cycles))
+            res[prec] = rs
+    clocks = clk.summary()
+    out = {}
+    for prec, rs in res.items():
+        ms = reduce_max(statistics.mean(r["kernel_ms"] for r in rs), world, dev)
+        nz = statistics.mean(r["nonzero_steps"] / max(1, r["steps"]) for r in rs)
+        if prec == "fp64":
+            rl = roofline(algorithmic_bytes(info, cycles, nz), fp64_flops(info, cycles, nz), ms,
+                          "fit_kernel (FP64, 16 columns of 1-2M nonzeros)")
+        else:
+            rl = roofline(algorithmic_bytes32(info, cycles, nz), 0.0, ms, "fit_kernel (FP32, 16 columns of 1-2M nonzeros)",
+                          fp64=False)
+        out[prec] = {"kernel_ms": ms, "us_per_step": 1e3 * ms / (cycles * d.J),
+                     "value": reduce_sum(float(d.J * cycles), world, dev) / (ms / 1e3), "roofline": rl}
+    if rank == 0:
+        r64 = out["fp64"]
+        line = {
+            "metric": "coord-updates/s (large-column SCCS fit, FP64)", "value": r64["value"], "unit": "coord-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r64["kernel_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator)", "workload": "large-columns",
+            "config": {"workload": f"large columns: {int(info['subjects_kept'])} subjects, {int(info['rows_kept'])} eras, "
+                                   f"{d.J} drugs of 1M-2M nonzeros, Normal prior var {fit['variance']}, "
+                                   f"{cycles} cycles per step", "nnz": int(info["nnz_kept"]),
+                       "segments": int(info["segments"]), "seed": d.recipe["seed"],
+                       "l2": "256 MB buffer written between timed steps (L2 flushed)"},
+            "roofline": r64["roofline"], "us_per_step": r64["us_per_step"], "fp32": out["fp32"],
+            "e2e": None, "gpu_launches": 2 * args.steps, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     model.close()
@@ -732,7 +831,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's subjects")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="fit", choices=["fit", "batched", "serving", "paper"],
+    ap.add_argument("--workload", default="fit", choices=["fit", "batched", "serving", "paper", "large-columns"],
                     help="fit: one full MAP fit per step (default); batched: all fits of a batch in one "
                          "launch per step; serving: Poisson-arrival requests over resident outcomes")
     ap.add_argument("--fits", type=int, default=256, help="batched: fits per batch")
@@ -759,6 +858,8 @@ def main():
         return run_serving(args, rank, world, local)
     if args.workload == "paper":
         return run_paper(args, rank, world, local)
+    if args.workload == "large-columns":
+        return run_large_columns(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

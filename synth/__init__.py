@@ -10,6 +10,7 @@ from .sccs_synth import (  # noqa: F401
     tiny_fit_config,
     mid_fit_config,
     paper_scale_config,
+    large_columns_config,
     batched_fit_configs,
     batched_fit_plan,
     batched_fit_one,

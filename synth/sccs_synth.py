@@ -225,6 +225,17 @@ def mid_fit_config(seed: int = 1209, scale: float = 1.0) -> tuple[SCCSData, dict
     return d, fit
 
 
+def large_columns_config(seed: int = 1215, scale: float = 1.0) -> tuple[SCCSData, dict]:
+    """1M subjects (eras geometric, mean 10), 16 drug columns of 1M to 2M nonzeros each (uniform
+    sizes), 5 true effects N(0, 0.3^2); Normal prior variance 0.1; a fixed 4 cycles per fit."""
+    n = max(1000, int(round(1_000_000 * scale)))
+    rng = np.random.default_rng(seed)
+    sizes = (rng.integers(1_000_000, 2_000_001, size=16) * (n / 1_000_000)).astype(np.int64)
+    d = make_dataset(n_patients=n, eras=("geometric", 10), J=16, columns=("sizes", sizes), n_true=5, beta_sd=0.3,
+                     seed=seed, name="large-columns")
+    return d, {"prior": "normal", "variance": 0.1, "cycles": 4}
+
+
 def paper_scale_config(seed: int = 1210, scale: float = 1.0) -> tuple[SCCSData, dict]:
     """4M subjects (~40M eras), 5,000 drugs with Zipf(1.1) sizes 10..5M, 50 true effects.
 

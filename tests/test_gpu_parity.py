@@ -587,3 +587,21 @@ def test_narrow_groups_of_independent_columns(P):
         np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11, rtol=0)
         np.testing.assert_allclose(r["history"], ref["history"], rtol=1e-12)
         assert r["nonzero_steps"] == res[0]["nonzero_steps"]
+
+
+def test_long_fit_stays_on_the_oracle_trajectory(P):
+    """The 1,000-cycle default cap run in full (tol < 0), long past convergence: E is updated
+    multiplicatively (E_k <- E_k e^{db}) and rebuilt from beta every 64 cycles, the oracle
+    recomputes l_k exp(Xb_k) at every update; after 1,000 cycles beta still agrees to 1e-10 and P
+    to 1e-12.  The FP32 mode (rebuilt every 16 cycles) stays within its own bar."""
+    d, _ = tiny_fit_config()
+    orc = oracle.Problem.from_data(d)
+    ref = orc.fit(prior="normal", variance=1.0, fixed_cycles=1000)
+    with gpu_model(P, d) as m:
+        m.set_prior("normal", 1.0)
+        r = m.fit(tol=-1.0, max_cycles=1000)
+        r32 = m.fit(tol=-1.0, max_cycles=1000, precision="fp32")
+    assert r["cycles"] == 1000
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-10, rtol=0)
+    assert rel(r["logpost"], ref["logpost"]) <= 1e-12
+    assert np.abs(r32["beta"] - ref["beta"]).max() <= 2e-4
