@@ -335,12 +335,49 @@ def run_ours(args, rank, world, local):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
-        print(json.dumps(line), flush=True)
     model.close()
+    if rank == 0 and world == 1 and not args.no_legs and args.scale == 1.0:
+        line.update(run_legs(args, local))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _leg(full, keep):
+    return {k: full[k] for k in keep if k in full}
+
+
+def run_legs(args, local):
+    """The other workloads at their full shapes, run after the headline fit in the same process
+    (one GPU): the paper-scale FP32 + polish fit with its per-coefficient error against the oracle
+    (which runs in a separate process meanwhile), the 256-fit batched launch against one fit at a
+    time, and the served fits per arrival rate against one fit at a time.  Each carries its own
+    clock record and roofline."""
+    import copy
+    legs = {}
+    a = copy.copy(args)
+    a.steps, a.warmup = 2, 3
+    t0 = time.perf_counter()
+    paper, pending = run_paper(a, 0, 1, local, emit=False, oracle_check=True)
+    paper["wall_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batched = run_batched(a, 0, 1, local, emit=False)
+    batched["wall_s"] = time.perf_counter() - t0
+    a2 = copy.copy(a)
+    a2.rates, a2.requests = "2,10,50,200", -1
+    t0 = time.perf_counter()
+    serving = run_serving(a2, 0, 1, local, emit=False)
+    serving["wall_s"] = time.perf_counter() - t0
+    paper["error_vs_oracle"] = paper_oracle_error(pending)
+    keep = ("metric", "value", "unit", "ms_per_step", "higher_is_better", "dtype", "config", "roofline", "clocks",
+            "wall_s")
+    legs["paper_scale"] = _leg(paper, keep + ("fit", "fp64_throughout", "error_vs_fp64", "error_vs_oracle"))
+    legs["batched"] = _leg(batched, keep + ("batch", "one_at_a_time", "e2e", "cpu_baseline"))
+    legs["serving"] = _leg(serving, keep + ("sweep", "one_at_a_time", "p50_ms", "p99_ms"))
+    return legs
 
 
 def cpu_baseline(d, fit):
@@ -385,7 +422,7 @@ def _est_nnz_batched(plan, f):
     return float(plan["sizes"][f]) * 8.0 * float(np.sum(plan["dens"]))
 
 
-def run_batched(args, rank, world, local):
+def run_batched(args, rank, world, local, emit=True):
     """One step = one batched launch of all the batch's fits from beta = 0 to convergence."""
     import ctypes
     from synth import batched_fit_plan, batched_fit_one
@@ -523,9 +560,12 @@ def run_batched(args, rank, world, local):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
     for m in batch_m + plain_m:
         m.close()
+    if not emit:
+        return line if rank == 0 else None
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -541,7 +581,12 @@ def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, 
     nf = 0 if folds_of is None else int(max(f.max() for f in folds_of)) + 1
     rows = []
     for ri, rate in enumerate(rates):
-        n_req = n_per_rate if n_per_rate > 0 else int(min(192, max(32, 3.0 * rate)))
+        if n_per_rate > 0:
+            n_req = n_per_rate
+        elif n_per_rate < 0:          # a short sweep: about 3 s of arrivals, 12 to 64 requests
+            n_req = int(max(12, min(64, 3.0 * rate)))
+        else:
+            n_req = int(min(192, max(32, 3.0 * rate)))
         reqs = serving_requests(n_req, rate, len(Js), seed=seed0 + ri, folds=nf)
         masks = [fold_weights(folds_of[o], k - 1) if k > 0 else (None, None) for (_t, o, _p, _v, k) in reqs]
         with sccs.FitServer(device=device, max_inflight=max_inflight, hbm_budget_bytes=budget) as srv:
@@ -576,7 +621,7 @@ def _serve_sweep(sccs, device, handles_of, Js, rates, n_per_rate, max_inflight, 
     return rows
 
 
-def run_serving(args, rank, world, local):
+def run_serving(args, rank, world, local, emit=True):
     """Poisson-arrival fit requests over a pool of resident outcomes, served with continuous
     batching, beside the same arrivals served one fit at a time."""
     import ctypes
@@ -613,10 +658,11 @@ def run_serving(args, rank, world, local):
     Js = [m.J for m in served]
     rates = [float(x) for x in args.rates.split(",")]
     budget = int(args.hbm_budget_gb * (1 << 30))
-    # warm-up: one request per outcome through each arm
+    # warm-up: three rounds of requests through each arm
     for arm in (served, plain):
-        _serve_sweep(sccs, local, [m.handle for m in arm], Js, [1000.0], min(args.outcomes, 8), 64, budget, 999,
-                     folds_of)
+        for w in range(3):
+            _serve_sweep(sccs, local, [m.handle for m in arm], Js, [1000.0], min(args.outcomes, 8), 64, budget,
+                         999 + w, folds_of)
     with ClockSampler(local) as clk:
         ours = _serve_sweep(sccs, local, [m.handle for m in served], Js, rates, args.requests, 64, budget, 2000,
                             folds_of, alts_of=[m.handle for m in plain])
@@ -627,7 +673,7 @@ def run_serving(args, rank, world, local):
         line = {
             "metric": "served SCCS MAP fits/s and p50/p99 latency (FP64, Poisson arrivals, continuous batching)",
             "value": top["fits_per_s"], "unit": "fits/s", "n_gpus": world, "steps": len(rates),
-            "warmup": 1, "ms_per_step": 1e3 / top["fits_per_s"], "higher_is_better": True, "scaling": "weak",
+            "warmup": 3, "ms_per_step": 1e3 / top["fits_per_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)", "workload": "serving",
             "config": {"workload": f"serving: {args.outcomes} resident outcomes, eras log-uniform 20k-"
                                    f"{args.max_eras / 1e6:g}M, 1000-5000 drugs, Zipf(1.2) columns up to eras/5; "
@@ -636,7 +682,8 @@ def run_serving(args, rank, world, local):
                                    "of the 10th returned), FP64 to rel |dP| < 1e-12; each outcome resident with "
                                    "an autotuned team and a full-device team, the server choosing per request; "
                                    + (f"{args.requests} Poisson arrivals per rate" if args.requests > 0 else
-                                      "3 s of Poisson arrivals per rate (32 to 192 requests)"),
+                                      ("about 3 s of Poisson arrivals per rate (12 to 64 requests)" if args.requests < 0
+                                       else "3 s of Poisson arrivals per rate (32 to 192 requests)")),
                        "outcomes": args.outcomes, "eras": int(sum(i["rows_kept"] for i in infos)),
                        "nnz": int(sum(i["nnz_kept"] for i in infos)), "rates_per_s": rates,
                        "teams": {"min": int(min(teams)), "max": int(max(teams))},
@@ -650,9 +697,12 @@ def run_serving(args, rank, world, local):
                     "what": "submit -> poll through the C ABI, datasets resident; the value itself is end to end"},
             "clocks": clocks,
         }
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
     for m in served + plain:
         m.close()
+    if not emit:
+        return line if rank == 0 else None
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -668,9 +718,44 @@ def algorithmic_bytes32(d, cycles, nonzero_frac=1.0):
     return cycles * per_cycle + 4 * K + 28 * N
 
 
-def run_paper(args, rank, world, local):
+def _oracle_paper_fit(scale, cycles):
+    """Pool worker: the serial FP64 oracle's Algorithm 1 on the paper-scale data (drawn again
+    from its seed), for a fixed number of cycles."""
+    import oracle
+    from synth import paper_scale_config
+    t0 = time.perf_counter()
+    d, fit = paper_scale_config(scale=scale)
+    prob = oracle.Problem.from_data(d)
+    t1 = time.perf_counter()
+    r = prob.fit(prior=fit["prior"], variance=fit["variance"], fixed_cycles=cycles)
+    return r["beta"], r["logpost"], time.perf_counter() - t1, t1 - t0
+
+
+def paper_oracle_error(pending, timeout_s=1500.0):
+    """Per-coefficient error of the GPU's FP32 + polish fit against the oracle's FP64 fit after the
+    same number of cycles (the oracle ran in a separate process meanwhile)."""
+    pool, fut, beta, logpost, cycles = pending
+    try:
+        ob, olp, fit_s, setup_s = fut.result(timeout=timeout_s)
+        db = np.abs(beta - ob)
+        out = {"max_abs_dbeta": float(db.max()), "mean_abs_dbeta": float(db.mean()),
+               "rel_logpost": abs(logpost - olp) / abs(olp),
+               "zero_pattern_identical": bool(np.array_equal(beta == 0, ob == 0)),
+               "nonzero_coefficients": int(np.count_nonzero(ob)), "cycles": int(cycles),
+               "oracle_fit_s": fit_s, "oracle_setup_s": setup_s,
+               "reference": "serial FP64 C oracle, Algorithm 1 for the same number of cycles as the GPU fit "
+                            "(FP32 phase + FP64 polish) on the same data"}
+    except Exception as e:  # a timeout or a failed worker is reported, not hidden
+        out = {"unavailable": f"oracle comparison did not finish: {type(e).__name__}: {e}"[:200]}
+    pool.shutdown(wait=False, cancel_futures=True)
+    return out
+
+
+def run_paper(args, rank, world, local, emit=True, oracle_check=False):
     """The paper-scale fit (4M subjects, ~40M eras, 5,000 drugs, Laplace): FP32 with compensated
-    per-subject sums then an FP64 polish, beside the same fit in FP64 throughout."""
+    per-subject sums then an FP64 polish, beside the same fit in FP64 throughout.  With
+    oracle_check the oracle's fit for the same number of cycles starts in a separate process;
+    returns (line, pending) for paper_oracle_error."""
     import ctypes
     import torch
     import paper_1208_0945_gb300 as sccs
@@ -716,6 +801,12 @@ def run_paper(args, rank, world, local):
     fp32_c = r32["fp32_cycles"]
     bytes32 = algorithmic_bytes32(info, fp32_c, nz32) + algorithmic_bytes(info, r32["cycles"] - fp32_c, nz32)
     flops_polish = fp64_flops(info, r32["cycles"] - fp32_c, nz32)
+    pending = None
+    if oracle_check and rank == 0:
+        pool = _spawn_pool(1)
+        pending = (pool, pool.submit(_oracle_paper_fit, args.scale, int(r32["cycles"])), r32["beta"].copy(),
+                   r32["logpost"], r32["cycles"])
+    line = None
     if rank == 0:
         line = {
             "metric": "coord-updates/s (paper-scale SCCS MAP fit, FP32 compensated + FP64 polish)",
@@ -747,8 +838,13 @@ def run_paper(args, rank, world, local):
             "gpu_launches": 6 * args.steps,
             "clocks": clocks,
         }
-        print(json.dumps(line), flush=True)
     model.close()
+    if not emit:
+        return line, pending
+    if rank == 0:
+        if pending is not None:
+            line["error_vs_oracle"] = paper_oracle_error(pending)
+        print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -831,6 +927,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's subjects")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="fit workload: only the headline fit (no paper-scale, batched and serving results)")
+    ap.add_argument("--oracle-check", action="store_true",
+                    help="paper workload: also run the oracle for the same cycles and report the per-beta error")
     ap.add_argument("--workload", default="fit", choices=["fit", "batched", "serving", "paper", "large-columns"],
                     help="fit: one full MAP fit per step (default); batched: all fits of a batch in one "
                          "launch per step; serving: Poisson-arrival requests over resident outcomes")
@@ -857,7 +957,7 @@ def main():
     if args.workload == "serving":
         return run_serving(args, rank, world, local)
     if args.workload == "paper":
-        return run_paper(args, rank, world, local)
+        return run_paper(args, rank, world, local, oracle_check=args.oracle_check)
     if args.workload == "large-columns":
         return run_large_columns(args, rank, world, local)
     return run_ours(args, rank, world, local)

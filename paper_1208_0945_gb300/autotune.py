@@ -1,4 +1,12 @@
-"""Team-size autotuner for batched fits.
+"""Autotuners: launch parameters of one fit, and team sizes for batched fits.
+
+`tune_launch` picks the launch parameters of a dataset's handle by timed probe fits through the
+library on the caller's own data: the thread-block cluster that takes the small and mid-size
+columns (its size, and the column size up to which a column runs there: the column tile of the
+cluster path), or without a cluster the narrow-column size and group limits, and the threads
+(warps) per CTA.  A coordinate search: each knob in turn, keeping the fastest setting so far.
+
+Team sizes for batched fits:
 
 A fit run by a team of S CTAs costs, per CCD cycle, about
 
@@ -136,3 +144,54 @@ def assign(fits, model: CostModel, capacity: int | None = None, max_rounds: int 
         if not improved:
             frozen.add(f)
     return S
+
+
+# ------------------------------------------------------------------ launch parameters of one fit
+
+@dataclasses.dataclass
+class LaunchChoice:
+    options: dict         # sccs_create keyword options of the fastest probe
+    kernel_ms: float      # its device time for the probe cycles
+    trials: list          # every probe: (options, kernel_ms), in the order taken
+
+
+def _knob_stages(best: dict) -> list:
+    """The settings tried for each knob in turn, given the choices made so far."""
+    on = best.get("cluster_ctas", 16) > 0
+    return [
+        [dict(cluster_ctas=16), dict(cluster_ctas=8), dict(cluster_ctas=-1)],
+        ([dict(cluster_max_nnz=v) for v in (16384, 65536, 262144)] if on
+         else [dict(narrow_max_nnz=v) for v in (512, 1024, 2048)]),
+        [] if on else [dict(narrow_group_max=g) for g in (1, 4, 8)],
+        [dict(threads_per_block=t) for t in (512, 384, 256)],
+    ]
+
+
+def _probe_launch(data, options, device, prior, variance, cycles) -> float:
+    with _s.SCCSModel(data, device=device, **options) as m:
+        m.set_prior(prior, variance)
+        m.fit(tol=-1.0, max_cycles=1)                       # warm-up
+        return min(m.fit(tol=-1.0, max_cycles=cycles)["kernel_ms"] for _ in range(2))
+
+
+def tune_launch(data, device: int = 0, prior: str = "normal", variance: float = 1.0, cycles: int = 2,
+                timer=None) -> LaunchChoice:
+    """Timed probe fits (`cycles` fixed cycles from beta = 0, best of two) on `data` for each knob
+    in turn; returns the fastest options.  `timer(data, options)` replaces the probe (tests)."""
+    probe = timer or (lambda d, o: _probe_launch(d, o, device, prior, variance, cycles))
+    best, best_ms, trials, seen = {}, float("inf"), [], {}
+    for stage in range(4):
+        cands = _knob_stages(best)[stage]
+        if not cands:
+            continue
+        stage_best = None
+        for c in cands:
+            opts = {**best, **c}
+            key = tuple(sorted(opts.items()))
+            if key not in seen:
+                seen[key] = probe(data, opts)
+                trials.append((opts, seen[key]))
+            if stage_best is None or seen[key] < stage_best[1]:
+                stage_best = (opts, seen[key])
+        best, best_ms = stage_best
+    return LaunchChoice(options=best, kernel_ms=best_ms, trials=trials)

@@ -47,3 +47,40 @@ def test_assign_is_monotone_in_load(model):
     small = assign([(200, 100_000, 10_000)] * 4, model)
     big = assign([(200, 100_000, 10_000)] * 400, model)
     assert sum(small) / 4 >= sum(big) / 400
+
+
+def test_tune_launch_takes_the_fastest_setting_of_each_knob():
+    """The coordinate search over the launch knobs with a made-up cost: every knob is set to its
+    fastest value given the earlier ones, each setting is probed once, and the result is the
+    fastest probe."""
+    from paper_1208_0945_gb300.autotune import tune_launch
+
+    def cost(opts):
+        t = 10.0
+        t += {16: 0.0, 8: 1.0, -1: 3.0}[opts.get("cluster_ctas", 16)]
+        t += {16384: 0.5, 65536: 0.0, 262144: 2.0}.get(opts.get("cluster_max_nnz", 65536), 0.0)
+        t += {512: 0.0, 384: 0.7, 256: 1.5}[opts.get("threads_per_block", 512)]
+        return t
+
+    calls = []
+    ch = tune_launch(None, timer=lambda d, o: calls.append(dict(o)) or cost(o))
+    assert ch.options == {"cluster_ctas": 16, "cluster_max_nnz": 65536, "threads_per_block": 512}
+    assert ch.kernel_ms == min(t for _, t in ch.trials) == cost(ch.options)
+    keys = [tuple(sorted(o.items())) for o in calls]
+    assert len(keys) == len(set(keys))                      # no setting probed twice
+    assert len(calls) == 3 + 3 + 3                           # one probe per setting of each knob
+
+
+def test_tune_launch_without_clusters_tunes_the_narrow_knobs():
+    from paper_1208_0945_gb300.autotune import tune_launch
+
+    def cost(opts):
+        t = {16: 5.0, 8: 6.0, -1: 1.0}[opts["cluster_ctas"]]
+        t += {512: 0.2, 1024: 0.0, 2048: 0.3}.get(opts.get("narrow_max_nnz", 1024), 0.0)
+        t += {1: 0.4, 4: 0.1, 8: 0.0}.get(opts.get("narrow_group_max", 8), 0.0)
+        t += {512: 0.0, 384: 0.1, 256: 0.2}[opts.get("threads_per_block", 512)]
+        return t
+
+    ch = tune_launch(None, timer=lambda d, o: cost(o))
+    assert ch.options == {"cluster_ctas": -1, "narrow_max_nnz": 1024, "narrow_group_max": 8, "threads_per_block": 512}
+    assert not any("cluster_max_nnz" in o for o, _ in ch.trials)

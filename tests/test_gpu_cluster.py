@@ -112,3 +112,18 @@ def test_cluster_and_grid_columns_without_narrow_columns(P):
         r = m.fit(tol=-1.0, max_cycles=3)
     np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11, rtol=0)
     assert rel(r["logpost"], ref["logpost"]) <= 1e-12
+
+
+def test_tuned_launch_fits_match_the_oracle(P):
+    """The launch autotuner's timed probe fits on a dataset, then a fit with the options it chose:
+    three cycles against the oracle (every option the tuner can pick gives the oracle's
+    trajectory)."""
+    from paper_1208_0945_gb300.autotune import tune_launch
+    d, fit = mid_fit_config(scale=0.02)
+    ch = tune_launch(d, device=0, prior="normal", variance=fit["variance"], cycles=2)
+    assert ch.kernel_ms > 0 and len(ch.trials) >= 6
+    ref = oracle.Problem.from_data(d).fit(prior="normal", variance=fit["variance"], fixed_cycles=3)
+    with P.SCCSModel(d, device=0, **ch.options) as m:
+        m.set_prior("normal", fit["variance"])
+        r = m.fit(tol=-1.0, max_cycles=3)
+    np.testing.assert_allclose(r["beta"], ref["beta"], atol=1e-11, rtol=0)
