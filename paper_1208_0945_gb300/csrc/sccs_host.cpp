@@ -389,7 +389,7 @@ void build_slices(int32_t J, int32_t S, const std::vector<int64_t> &shard_row, c
 
 constexpr int32_t kNarrowDefault = 1024;
 constexpr int32_t kClusterDefault = 16;
-constexpr int64_t kClusterMaxNnzDefault = 65536;
+constexpr int64_t kClusterMaxNnzDefault = 16384;
 using sccs::kNarrowGroupMax;
 constexpr int32_t kNarrowMinShards = 4;
 
