@@ -861,50 +861,59 @@ int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const d
         // reads what the other writes, so their steps can be taken side by side with exactly the
         // sequential result.
         hl.cgroup.assign(static_cast<size_t>(J), 0);
-        std::vector<uint8_t> seen(static_cast<size_t>(std::max<int64_t>(Nk, 1)), 0);
-        std::vector<int32_t> touched;
-        std::vector<int64_t> rows_c(static_cast<size_t>(C)), segs_c(static_cast<size_t>(C));
         auto slice_n = [&](const std::vector<int64_t> &a, int32_t c, int32_t j) {
             const int64_t idx = static_cast<int64_t>(c) * (J + 1) + j;
             return a[idx + 1] - a[idx];
         };
+        // ext[j]: the group the greedy rule forms when it starts at cluster column j, found for
+        // every j in parallel (each thread stamps subjects with the start column it is trying);
+        // the greedy walk below then only follows ext from the first column of each run
+        std::vector<int32_t> ext(static_cast<size_t>(J), 1);
+        const int64_t parts = std::max<int64_t>(1, std::min<int64_t>(host_threads(), J));
+        parallel_chunks(J, parts, [&](int64_t, int64_t lo, int64_t hi) {
+            std::vector<int32_t> stamp(static_cast<size_t>(std::max<int64_t>(Nk, 1)), -1);
+            std::vector<int64_t> rows_c(static_cast<size_t>(C)), segs_c(static_cast<size_t>(C));
+            for (int64_t jj = lo; jj < hi; ++jj) {
+                const int32_t j = static_cast<int32_t>(jj);
+                if (!hl.ccls[j] || j + 1 >= J || !hl.ccls[j + 1]) continue;
+                for (int32_t c = 0; c < C; ++c) {
+                    rows_c[c] = slice_n(hl.cslice_row, c, j);
+                    segs_c[c] = slice_n(hl.cslice_seg, c, j);
+                }
+                bool marked = false;
+                int32_t m = 1;
+                while (j + m < J && hl.ccls[j + m] && m < group_max) {
+                    const int32_t jn = j + m;
+                    bool fits = true;
+                    for (int32_t c = 0; c < C && fits; ++c)
+                        fits = rows_c[c] + slice_n(hl.cslice_row, c, jn) <= sccs::kRowCap &&
+                               segs_c[c] + slice_n(hl.cslice_seg, c, jn) <= sccs::kSegCap;
+                    if (!fits) break;
+                    if (!marked) {              // the start column's subjects, once a candidate fits
+                        for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) stamp[csub[e]] = j;
+                        marked = true;
+                    }
+                    for (int64_t e = cptr[jn]; e < cptr[jn + 1] && fits; ++e)
+                        if (stamp[csub[e]] == j) fits = false;
+                    if (!fits) break;
+                    for (int32_t c = 0; c < C; ++c) {
+                        rows_c[c] += slice_n(hl.cslice_row, c, jn);
+                        segs_c[c] += slice_n(hl.cslice_seg, c, jn);
+                    }
+                    for (int64_t e = cptr[jn]; e < cptr[jn + 1]; ++e) stamp[csub[e]] = j;
+                    ++m;
+                }
+                ext[j] = m;
+            }
+        });
+        // Groups: consecutive cluster columns with pairwise disjoint subjects, up to group_max, whose
+        // slices on every cluster shard fit one staging buffer together, formed greedily.
         for (int32_t j = 0; j < J;) {
             if (!hl.ccls[j]) {
                 ++j;
                 continue;
             }
-            for (int32_t c = 0; c < C; ++c) {
-                rows_c[c] = slice_n(hl.cslice_row, c, j);
-                segs_c[c] = slice_n(hl.cslice_seg, c, j);
-            }
-            for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e)
-                if (!seen[csub[e]]) {
-                    seen[csub[e]] = 1;
-                    touched.push_back(csub[e]);
-                }
-            int32_t m = 1;
-            while (j + m < J && hl.ccls[j + m] && m < group_max) {
-                const int32_t jn = j + m;
-                bool fits = true;
-                for (int32_t c = 0; c < C && fits; ++c)
-                    fits = rows_c[c] + slice_n(hl.cslice_row, c, jn) <= sccs::kRowCap &&
-                           segs_c[c] + slice_n(hl.cslice_seg, c, jn) <= sccs::kSegCap;
-                for (int64_t e = cptr[jn]; e < cptr[jn + 1] && fits; ++e)
-                    if (seen[csub[e]]) fits = false;
-                if (!fits) break;
-                for (int32_t c = 0; c < C; ++c) {
-                    rows_c[c] += slice_n(hl.cslice_row, c, jn);
-                    segs_c[c] += slice_n(hl.cslice_seg, c, jn);
-                }
-                for (int64_t e = cptr[jn]; e < cptr[jn + 1]; ++e)
-                    if (!seen[csub[e]]) {
-                        seen[csub[e]] = 1;
-                        touched.push_back(csub[e]);
-                    }
-                ++m;
-            }
-            for (int32_t i : touched) seen[i] = 0;
-            touched.clear();
+            const int32_t m = ext[j];
             hl.cgroup[j] = m;
             hl.cluster_groups++;
             j += m;
@@ -1373,7 +1382,10 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     // every column of a group keeps at least two warps of the CTA
     const int32_t group_cap = std::max(1, std::min(kNarrowGroupMax, threads / 64));
     const int32_t group_max = o.narrow_group_max <= 0 ? group_cap : std::min(o.narrow_group_max, group_cap);
-    int rc = build_layout(K, patient_id, y, offset_L, J, col_ptr, row_idx, S, narrow_max, group_max, hl, C,
+    // when every column small enough for the narrow path is a cluster column as well, the cluster
+    // takes them all and no narrow layout is built
+    const int32_t narrow_eff = (C > 0 && cluster_max >= narrow_max) ? -1 : narrow_max;
+    int rc = build_layout(K, patient_id, y, offset_L, J, col_ptr, row_idx, S, narrow_eff, group_max, hl, C,
                           cluster_max);
     if (rc != SCCS_OK) return rc;
 
