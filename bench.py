@@ -253,7 +253,8 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(dev)
     d, fit = mid_fit_config(scale=args.scale)
     stream = torch.cuda.current_stream(dev)
-    model = sccs.SCCSModel(d, device=local, stream=__import__("ctypes").c_void_p(stream.cuda_stream))
+    model = sccs.SCCSModel(d, device=local, stream=__import__("ctypes").c_void_p(stream.cuda_stream),
+                           cluster_ctas=args.cluster_ctas)
     model.set_prior(fit["prior"], fit["variance"])
     info = model.info
     fkw = dict(tol_mode=fit["tol_mode"], tol=fit["tol"], max_cycles=fit["max_cycles"])
@@ -299,7 +300,8 @@ def run_ours(args, rank, world, local):
     for _ in range(e2e_steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        m2 = sccs.SCCSModel(d, device=local, stream=__import__("ctypes").c_void_p(stream.cuda_stream))
+        m2 = sccs.SCCSModel(d, device=local, stream=__import__("ctypes").c_void_p(stream.cuda_stream),
+                            cluster_ctas=args.cluster_ctas)
         m2.set_prior(fit["prior"], fit["variance"])
         r2 = m2.fit(**fkw)
         h2d = m2.info["upload_bytes"]
@@ -934,6 +936,9 @@ def main():
     ap.add_argument("--workload", default="fit", choices=["fit", "batched", "serving", "paper", "large-columns"],
                     help="fit: one full MAP fit per step (default); batched: all fits of a batch in one "
                          "launch per step; serving: Poisson-arrival requests over resident outcomes")
+    ap.add_argument("--cluster-ctas", type=int, default=0,
+                    help="fit workload: CTAs per thread-block cluster of the cluster columns (0: the library's "
+                         "default, -1: none; ncu drops the cluster shape of a launch, so captures use -1)")
     ap.add_argument("--fits", type=int, default=256, help="batched: fits per batch")
     ap.add_argument("--max-subjects", type=int, default=500_000, help="batched: largest fit's subjects")
     ap.add_argument("--outcomes", type=int, default=32, help="serving: resident outcomes")

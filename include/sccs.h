@@ -357,6 +357,59 @@ int sccs_selftest_exp(int32_t device, const double *x, int64_t n, double *ours, 
 int sccs_selftest_div(int32_t device, const double *a, const double *b, int64_t n, double *ours, double *ref);
 
 /*
+ * sccs_debug_layout -- diagnostic for tests: a copy of one array of the handle's data layout
+ * (the representation of M and X_j that Section 2.4 puts in device memory, in this library's
+ * sharded jagged-diagonal form), so that a test can check it against its definition.
+ * which: one of SCCS_DBG_*; dst: host buffer of capacity bytes, or NULL to ask only for the size;
+ * *bytes (not NULL): the array's size in bytes.  Element types: int64 for the *_PTR, SLICE_*,
+ * SHARD_*, GRP_BASE, KEPT_FROM and SCALARS arrays; int32 for NEV, ROWS, YSUB, YCNT, NEXT_*,
+ * NAR_ROW, NAR_GROUP, CGROUP, CROWS, ROW_COL; {int32 subject, int32 length} pairs for SEGS and
+ * CSEGS; {subject, rows, first row, mark} int32 quadruples for NAR_SEG; uint8 for NARROW and CCLS;
+ * double for L and YTX.  SCALARS: {kept nonzeros, input subjects, narrow columns, cluster columns,
+ * first grid column, stash stride, E-stash stride, first wide column}.  An array the layout does not
+ * have (no narrow or cluster columns) has size 0.  Synchronous.  Errors: SCCS_E_INVAL (null
+ * handle or bytes, unknown which, capacity too small), SCCS_E_CUDA.
+ */
+#define SCCS_DBG_PAT_PTR 1
+#define SCCS_DBG_NEV 2
+#define SCCS_DBG_L 3
+#define SCCS_DBG_YTX 4
+#define SCCS_DBG_ROWS 5
+#define SCCS_DBG_SEGS 6
+#define SCCS_DBG_GRP_BASE 7
+#define SCCS_DBG_SLICE_ROW 8
+#define SCCS_DBG_SLICE_SEG 9
+#define SCCS_DBG_SLICE_GRP 10
+#define SCCS_DBG_SHARD_ROW 11
+#define SCCS_DBG_SHARD_PAT 12
+#define SCCS_DBG_YCOL_PTR 13
+#define SCCS_DBG_YSUB 14
+#define SCCS_DBG_YCNT 15
+#define SCCS_DBG_NARROW 16
+#define SCCS_DBG_NEXT_WIDE 17
+#define SCCS_DBG_NAR_PTR 18
+#define SCCS_DBG_NAR_SEG 19
+#define SCCS_DBG_NAR_ROW 20
+#define SCCS_DBG_NAR_GROUP 21
+#define SCCS_DBG_CCLS 22
+#define SCCS_DBG_NEXT_GRID 23
+#define SCCS_DBG_CGROUP 24
+#define SCCS_DBG_CROWS 25
+#define SCCS_DBG_CSEGS 26
+#define SCCS_DBG_CGRP_BASE 27
+#define SCCS_DBG_CSLICE_ROW 28
+#define SCCS_DBG_CSLICE_SEG 29
+#define SCCS_DBG_CSLICE_GRP 30
+#define SCCS_DBG_CSHARD_ROW 31
+#define SCCS_DBG_CSHARD_PAT 32
+#define SCCS_DBG_KEPT_FROM 33
+#define SCCS_DBG_ROW_PTR 34
+#define SCCS_DBG_ROW_COL 35
+#define SCCS_DBG_SCALARS 36
+#define SCCS_DBG_COUNT 37
+int sccs_debug_layout(const sccs_handle *h, int32_t which, void *dst, int64_t capacity, int64_t *bytes);
+
+/*
  * sccs_check_wait_timeout -- self-test of the bounded device-side waits (failure detection).
  * Launches the gradient kernel on one CTA fewer than the all-reduce counts, so the last
  * partial is never written and every launched CTA's wait must run out after timeout_ms

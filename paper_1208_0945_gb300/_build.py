@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libsccs.so")
-SOURCES = ["sccs_kernels.cu", "sccs_host.cpp", "sccs_server.cpp"]
+SOURCES = ["sccs_kernels.cu", "sccs_layout.cu", "sccs_host.cpp", "sccs_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

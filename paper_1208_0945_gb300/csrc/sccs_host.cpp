@@ -23,6 +23,7 @@
 
 #include "sccs.h"
 #include "sccs_internal.h"
+#include "sccs_layout.h"
 
 namespace {
 
@@ -76,25 +77,6 @@ int64_t host_threads() {
     const unsigned hw = std::thread::hardware_concurrency();
     return hw ? static_cast<int64_t>(hw) : 4;
 }
-
-// A host array left uninitialised (every element is written before it is read).
-template <class T>
-struct HostBuf {
-    std::unique_ptr<T[]> p;
-    size_t n = 0;
-    HostBuf() = default;
-    explicit HostBuf(size_t m) { alloc(m); }
-    void alloc(size_t m) {
-        p.reset(new T[m > 0 ? m : 1]);
-        n = m;
-    }
-    T &operator[](size_t i) { return p[i]; }
-    const T &operator[](size_t i) const { return p[i]; }
-    T *data() { return p.get(); }
-    const T *data() const { return p.get(); }
-    T *begin() { return p.get(); }
-    size_t size() const { return n; }
-};
 
 struct DeviceArena {
     sccs_alloc_fn alloc = nullptr;
@@ -163,6 +145,14 @@ struct sccs_handle {
     double *ytx_w = nullptr;           // J: weighted Y'X_j
     int32_t *w_host = nullptr;         // N, pinned
     bool e_stale = false;              // the FP64 E no longer matches beta (after an FP32-only fit)
+    // the layout's arrays by SCCS_DBG_* id, for the layout diagnostic: address and size
+    struct DbgArr {
+        const void *p = nullptr;
+        int64_t bytes = 0;
+        bool host = false;
+    };
+    DbgArr dbg[SCCS_DBG_COUNT];
+    std::vector<int64_t> cshard_row_h, cshard_pat_h, scalars_h;
 };
 
 namespace {
@@ -200,6 +190,31 @@ int alloc_zero(sccs_handle *h, T **dst, size_t count) {
     return SCCS_OK;
 }
 
+// A new device array of `count` elements that a layout kernel fills; `pad` zeroed bytes follow
+// (arrays read by bulk copies rounded out to 16-byte boundaries).
+template <class T>
+int alloc_padded(sccs_handle *h, T **dst, size_t count, size_t pad = 0) {
+    *dst = static_cast<T *>(h->arena.get(count * sizeof(T) + pad));
+    if (!*dst) return fail(SCCS_E_NOMEM, "device allocation failed");
+    if (pad) {
+        cudaError_t e = cudaMemsetAsync(reinterpret_cast<char *>(*dst) + count * sizeof(T), 0, pad, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    return SCCS_OK;
+}
+
+// A new device array holding a copy of `count` elements of device memory.
+template <class T>
+int copy_in(sccs_handle *h, T **dst, const T *src, size_t count) {
+    int rc = alloc_padded(h, dst, count);
+    if (rc) return rc;
+    if (count) {
+        cudaError_t e = cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2D");
+    }
+    return SCCS_OK;
+}
+
 void destroy_handle(sccs_handle *h) {
     if (!h) return;
     cudaSetDevice(h->device);
@@ -214,177 +229,6 @@ void destroy_handle(sccs_handle *h) {
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
-}
-
-// Host-built canonical layout.
-struct HostLayout {
-    int64_t K = 0, N = 0, nnz = 0;
-    int32_t J = 0, S = 0;
-    std::vector<int64_t> pat_ptr;   // N+1
-    std::vector<int32_t> nev;       // N
-    HostBuf<double> L;              // K (every element written)
-    std::vector<double> ytx;        // J
-    std::vector<int64_t> shard_row, shard_pat;
-    HostBuf<int32_t> rows;          // JDS rows (every element written)
-    HostBuf<int2> segs;
-    HostBuf<int64_t> grp_base;
-    std::vector<int64_t> slice_row, slice_seg, slice_grp;  // S*(J+1)
-    int64_t stash_stride = 1;
-    int64_t estash_stride = 1;
-    int64_t segments = 0;
-    int64_t max_col = 0;
-    int64_t subjects_in = 0;
-    std::vector<int64_t> kept_from;   // N: input subject of each kept subject
-    std::vector<int64_t> ycol_ptr;    // J+1: per column, (subject, sum of y) pairs with events
-    HostBuf<int32_t> ysub, ycnt;      // every element written
-    // narrow columns (whole column on one CTA)
-    int32_t narrow_count = 0, first_wide = -1;
-    std::vector<uint8_t> narrow;      // J
-    std::vector<int32_t> next_wide;   // J
-    std::vector<int64_t> nar_ptr;     // J+1
-    std::vector<int4> nar_seg;        // {subject, rows, first row in nar_row, the step it waits on}
-    std::vector<int32_t> nar_row;
-    std::vector<int32_t> nar_group;   // J: at a group's first column, its number of columns; else 0
-    int32_t narrow_groups = 0;
-    // cluster columns: run on the C CTAs of one thread-block cluster, over C subject shards of
-    // their own (their slices below; every other column has empty slices there)
-    int32_t C = 0, cluster_count = 0, first_grid = -1;
-    std::vector<uint8_t> ccls;        // J: 1 for a cluster column
-    std::vector<int32_t> cgroup;      // J: at a cluster group's first column its size, else 0
-    int32_t cluster_groups = 0;
-    std::vector<int32_t> next_grid;   // J: the next column run by the whole team, cyclically
-    std::vector<int64_t> cshard_row, cshard_pat;              // C+1
-    HostBuf<int32_t> crows;
-    HostBuf<int2> csegs;
-    HostBuf<int64_t> cgrp_base;
-    std::vector<int64_t> cslice_row, cslice_seg, cslice_grp;  // C*(J+1)
-};
-
-// Shards at subject boundaries, balanced by rows: shard s holds subjects [shard_pat[s],
-// shard_pat[s+1]) and rows [shard_row[s], shard_row[s+1]).
-void subject_shards(const std::vector<int64_t> &pat_ptr, int64_t Nk, int64_t Kk, int32_t S,
-                    std::vector<int64_t> &shard_pat, std::vector<int64_t> &shard_row) {
-    shard_pat.assign(static_cast<size_t>(S) + 1, 0);
-    shard_row.assign(static_cast<size_t>(S) + 1, 0);
-    for (int32_t s = 1; s < S; ++s) {
-        const int64_t target = (Kk * s) / S;
-        const int64_t p = std::lower_bound(pat_ptr.begin(), pat_ptr.end(), target) - pat_ptr.begin();
-        shard_pat[s] = std::max<int64_t>(shard_pat[s - 1], std::min<int64_t>(p, Nk));
-    }
-    shard_pat[S] = Nk;
-    for (int32_t s = 0; s <= S; ++s) shard_row[s] = pat_ptr[shard_pat[s]];
-}
-
-// Per (shard, column) slices of the columns with in_set(j) (the others get empty slices): a
-// slice's subject segments, longest first with ties in subject order, packed 32 to a group whose
-// rows are stored diagonal by diagonal.  crow / csub: each column's kept rows ascending and their
-// subjects.  Returns the largest slice's segments and rows.
-template <class InSet>
-void build_slices(int32_t J, int32_t S, const std::vector<int64_t> &shard_row, const std::vector<int64_t> &cptr,
-                  const int32_t *crow, const int32_t *csub, InSet in_set, HostBuf<int32_t> &rows_out,
-                  HostBuf<int2> &segs_out, HostBuf<int64_t> &grp_out, std::vector<int64_t> &slice_row,
-                  std::vector<int64_t> &slice_seg, std::vector<int64_t> &slice_grp, int64_t &max_seg,
-                  int64_t &max_rows, int64_t &segments) {
-    // ---- pass 1: per (shard, column) slice: nonzeros and segments
-    const int64_t SJ = static_cast<int64_t>(S) * (J + 1);
-    std::vector<int64_t> s_nnz(static_cast<size_t>(SJ), 0), s_seg(static_cast<size_t>(SJ), 0);
-    std::vector<int64_t> s_lo(static_cast<size_t>(SJ), 0);
-    // one merge of each column's (ascending) rows with the shard boundaries
-    parallel_for(J, [&](int64_t j) {
-        if (!in_set(static_cast<int32_t>(j))) return;
-        int64_t e = cptr[j];
-        const int64_t e1 = cptr[j + 1];
-        for (int32_t s = 0; s < S; ++s) {
-            const int32_t r1 = static_cast<int32_t>(shard_row[s + 1]);
-            const int64_t lo = e;
-            int64_t ns = 0;
-            int32_t prev = -1;
-            for (; e < e1 && crow[e] < r1; ++e)
-                if (csub[e] != prev) {
-                    ns++;
-                    prev = csub[e];
-                }
-            const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
-            s_lo[idx] = lo;
-            s_nnz[idx] = e - lo;
-            s_seg[idx] = ns;
-        }
-    });
-    slice_row.assign(static_cast<size_t>(SJ), 0);
-    slice_seg.assign(static_cast<size_t>(SJ), 0);
-    slice_grp.assign(static_cast<size_t>(SJ), 0);
-    int64_t tr = 0, ts = 0, tg = 0;
-    max_seg = 1;
-    max_rows = 1;
-    for (int32_t s = 0; s < S; ++s) {
-        for (int32_t j = 0; j <= J; ++j) {
-            const int64_t idx = static_cast<int64_t>(s) * (J + 1) + j;
-            slice_row[idx] = tr;
-            slice_seg[idx] = ts;
-            slice_grp[idx] = tg;
-            if (j < J) {
-                tr += s_nnz[idx];
-                ts += s_seg[idx];
-                tg += (s_seg[idx] + 31) / 32;
-                max_seg = std::max<int64_t>(max_seg, s_seg[idx]);
-                max_rows = std::max<int64_t>(max_rows, s_nnz[idx]);
-            }
-        }
-    }
-    segments = ts;
-    rows_out.alloc(static_cast<size_t>(tr));
-    segs_out.alloc(static_cast<size_t>(ts));
-    grp_out.alloc(static_cast<size_t>(tg));
-
-    // ---- pass 2: fill segments (longest first) and rows (diagonal-major per group)
-    parallel_for(S, [&](int64_t s) {
-        std::vector<int64_t> seg_start;
-        std::vector<int32_t> seg_len, seg_pid, order, len_pos;
-        for (int32_t j = 0; j < J; ++j) {
-            const int64_t idx = s * (J + 1) + j;
-            const int64_t lo = s_lo[idx], n = s_nnz[idx];
-            seg_start.clear();
-            seg_len.clear();
-            seg_pid.clear();
-            int32_t prev = -1;
-            for (int64_t q = lo; q < lo + n; ++q) {
-                const int32_t p = csub[q];
-                if (p != prev) {
-                    seg_start.push_back(q);
-                    seg_len.push_back(0);
-                    seg_pid.push_back(p);
-                    prev = p;
-                }
-                seg_len.back()++;
-            }
-            const int32_t ns = static_cast<int32_t>(seg_len.size());
-            // longest first, ties in subject order: a stable counting sort by length
-            int32_t lmax = 0;
-            for (int32_t i = 0; i < ns; ++i) lmax = std::max(lmax, seg_len[i]);
-            len_pos.assign(static_cast<size_t>(lmax) + 2, 0);
-            for (int32_t i = 0; i < ns; ++i) len_pos[seg_len[i]]++;
-            for (int32_t l = lmax, run = 0; l >= 1; --l) {
-                const int32_t c = len_pos[l];
-                len_pos[l] = run;
-                run += c;
-            }
-            order.resize(ns);
-            for (int32_t i = 0; i < ns; ++i) order[len_pos[seg_len[i]]++] = i;
-            int64_t rpos = slice_row[idx];
-            const int64_t spos = slice_seg[idx], gpos = slice_grp[idx];
-            for (int32_t i = 0; i < ns; ++i) segs_out[spos + i] = int2{seg_pid[order[i]], seg_len[order[i]]};
-            for (int32_t g = 0; g * 32 < ns; ++g) {
-                grp_out[gpos + g] = rpos;
-                const int32_t a = g * 32, b = std::min(ns, a + 32);
-                const int32_t maxlen = seg_len[order[a]];
-                for (int32_t t = 0; t < maxlen; ++t)
-                    for (int32_t l = a; l < b; ++l) {
-                        const int32_t o = order[l];
-                        if (seg_len[o] > t) rows_out[rpos++] = crow[seg_start[o] + t];
-                    }
-            }
-        }
-    });
 }
 
 constexpr int32_t kNarrowDefault = 1024;
@@ -438,499 +282,6 @@ int validate_inputs(int64_t K, const int64_t *patient_id, const int32_t *y, cons
     // every n_i = 0: no subject contributes to Eq. 2, so there is nothing to fit
     if (first_bad(K, [&](int64_t i) { return y[i] > 0; }) < 0)
         return fail(SCCS_E_INVAL, "no events: every subject has n_i = 0");
-    return SCCS_OK;
-}
-
-int build_layout(int64_t K, const int64_t *patient_id, const int32_t *y, const double *Lin, int32_t J,
-                 const int64_t *col_ptr, const int32_t *row_idx, int32_t S, int32_t narrow_max, int32_t group_max,
-                 HostLayout &hl, int32_t C = 0, int64_t cluster_max = 0) {
-    // ---- subjects, n_i, dropping n_i = 0 (chunked parallel scans: the subjects' first rows,
-    //      their event counts, then the kept subjects' new positions by prefix sums)
-    const int64_t PK = std::max<int64_t>(1, std::min<int64_t>(8 * host_threads(), K / 65536 + 1));
-    std::vector<int64_t> c_first(static_cast<size_t>(PK), 0);
-    parallel_chunks(K, PK, [&](int64_t c, int64_t lo, int64_t hi) {
-        int64_t n = 0;
-        for (int64_t k = lo; k < hi; ++k) n += (k == 0 || patient_id[k] != patient_id[k - 1]) ? 1 : 0;
-        c_first[c] = n;
-    });
-    std::vector<int64_t> c_off(static_cast<size_t>(PK) + 1, 0);
-    for (int64_t c = 0; c < PK; ++c) c_off[c + 1] = c_off[c] + c_first[c];
-    const int64_t nsub = c_off[PK];
-    std::vector<int64_t> sub_start(static_cast<size_t>(nsub) + 1);
-    parallel_chunks(K, PK, [&](int64_t c, int64_t lo, int64_t hi) {
-        int64_t w = c_off[c];
-        for (int64_t k = lo; k < hi; ++k)
-            if (k == 0 || patient_id[k] != patient_id[k - 1]) sub_start[w++] = k;
-    });
-    sub_start[nsub] = K;
-    hl.subjects_in = nsub;
-    const int64_t PS = std::max<int64_t>(1, std::min<int64_t>(8 * host_threads(), nsub / 16384 + 1));
-    std::vector<int64_t> sub_n(static_cast<size_t>(std::max<int64_t>(nsub, 1)));
-    std::vector<int64_t> ck(static_cast<size_t>(PS), 0), cr(static_cast<size_t>(PS), 0);
-    std::vector<char> c_big(static_cast<size_t>(PS), 0);
-    parallel_chunks(nsub, PS, [&](int64_t c, int64_t lo, int64_t hi) {
-        for (int64_t i = lo; i < hi; ++i) {
-            int64_t n = 0;
-            for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) n += y[k];
-            sub_n[i] = n;
-            if (n > 0) {
-                ck[c]++;
-                cr[c] += sub_start[i + 1] - sub_start[i];
-            }
-            if (n >= (int64_t(1) << 31)) c_big[c] = 1;
-        }
-    });
-    std::vector<int64_t> ck_off(static_cast<size_t>(PS) + 1, 0), cr_off(static_cast<size_t>(PS) + 1, 0);
-    for (int64_t c = 0; c < PS; ++c) {
-        ck_off[c + 1] = ck_off[c] + ck[c];
-        cr_off[c + 1] = cr_off[c] + cr[c];
-    }
-    const int64_t Nk = ck_off[PS], Kk = cr_off[PS];
-    if (Kk >= (int64_t(1) << 31)) return fail(SCCS_E_INVAL, "more than 2^31-1 kept rows");
-    for (int64_t c = 0; c < PS; ++c)
-        if (c_big[c]) return fail(SCCS_E_INVAL, "n_i exceeds 2^31-1");
-    hl.K = Kk;
-    hl.N = Nk;
-    hl.J = J;
-    hl.pat_ptr.assign(static_cast<size_t>(Nk) + 1, 0);
-    hl.nev.assign(static_cast<size_t>(Nk), 0);
-    hl.kept_from.assign(static_cast<size_t>(Nk), 0);
-    hl.L.alloc(static_cast<size_t>(Kk));
-    HostBuf<int32_t> newrow;                         // input row -> kept row, when subjects are dropped
-    const bool map_rows = Kk < K;
-    if (map_rows) newrow.alloc(static_cast<size_t>(K));
-    // per kept row, its subject (high word) and its event count (low word): one lookup for both
-    HostBuf<uint64_t> rowinfo(static_cast<size_t>(Kk));
-    parallel_chunks(nsub, PS, [&](int64_t c, int64_t lo, int64_t hi) {
-        int64_t i2 = ck_off[c], k2 = cr_off[c];
-        for (int64_t i = lo; i < hi; ++i) {
-            if (sub_n[i] == 0) {
-                if (map_rows)
-                    for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) newrow[k] = -1;
-                continue;
-            }
-            hl.pat_ptr[i2] = k2;
-            hl.nev[i2] = static_cast<int32_t>(sub_n[i]);
-            hl.kept_from[i2] = i;
-            for (int64_t k = sub_start[i]; k < sub_start[i + 1]; ++k) {
-                if (map_rows) newrow[k] = static_cast<int32_t>(k2);
-                rowinfo[k2] = (static_cast<uint64_t>(i2) << 32) | static_cast<uint32_t>(y[k]);
-                hl.L[k2] = Lin[k];
-                k2++;
-            }
-            i2++;
-        }
-    });
-    hl.pat_ptr[Nk] = Kk;
-
-    // ---- columns: map, drop, sort, reject duplicates; Y'X_j.  Per-column work is cut into
-    //      tasks of at most kTask nonzeros so that the largest columns do not serialise it.
-    const int64_t nnz_in = col_ptr[J];
-    std::vector<int64_t> cptr(static_cast<size_t>(J) + 1, 0);
-    const bool all_kept = Kk == K;                  // then row k stays row k
-    if (all_kept) {
-        for (int32_t j = 0; j <= J; ++j) cptr[j] = col_ptr[j];
-    } else {
-        std::vector<int64_t> cnt(static_cast<size_t>(J), 0);
-        parallel_for(J, [&](int64_t j) {
-            int64_t c = 0;
-            for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) c += newrow[row_idx[e]] >= 0;
-            cnt[j] = c;
-        });
-        for (int32_t j = 0; j < J; ++j) cptr[j + 1] = cptr[j] + cnt[j];
-    }
-    hl.nnz = cptr[J];
-    // the kept rows of each column, ascending: the input itself when nothing is dropped and every
-    // column is ascending already (the usual case), else a mapped and sorted copy
-    HostBuf<int32_t> crow_own;
-    const int32_t *crow = row_idx;
-    {
-        std::vector<char> unsorted(static_cast<size_t>(J), 0);
-        if (all_kept)
-            parallel_for(J, [&](int64_t j) {
-                unsorted[j] = std::is_sorted(row_idx + cptr[j], row_idx + cptr[j + 1]) ? 0 : 1;
-            });
-        const bool any_unsorted = std::find(unsorted.begin(), unsorted.end(), 1) != unsorted.end();
-        if (!all_kept || any_unsorted) {
-            crow_own.alloc(static_cast<size_t>(hl.nnz));
-            if (all_kept) {
-                parallel_chunks(nnz_in, std::max<int64_t>(1, std::min<int64_t>(8 * host_threads(), nnz_in / 65536 + 1)),
-                                [&](int64_t, int64_t lo, int64_t hi) {
-                                    std::memcpy(crow_own.data() + lo, row_idx + lo,
-                                                sizeof(int32_t) * static_cast<size_t>(hi - lo));
-                                });
-            } else {
-                parallel_for(J, [&](int64_t j) {
-                    int64_t w = cptr[j];
-                    for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) {
-                        int32_t r = newrow[row_idx[e]];
-                        if (r >= 0) crow_own[w++] = r;
-                    }
-                });
-            }
-            parallel_for(J, [&](int64_t j) {
-                int32_t *b = crow_own.data() + cptr[j], *e = crow_own.data() + cptr[j + 1];
-                if (!all_kept || unsorted[j]) {
-                    if (!std::is_sorted(b, e)) std::sort(b, e);
-                }
-            });
-            crow = crow_own.data();
-        }
-    }
-    // tasks: (column, first nonzero, end); a column's tasks are adjacent and in order
-    constexpr int64_t kTask = 65536;
-    std::vector<int32_t> t_col;
-    std::vector<int64_t> t_lo, t_hi;
-    for (int32_t j = 0; j < J; ++j)
-        for (int64_t lo = cptr[j]; lo < cptr[j + 1]; lo += kTask) {
-            t_col.push_back(j);
-            t_lo.push_back(lo);
-            t_hi.push_back(std::min(lo + kTask, cptr[j + 1]));
-        }
-    const int64_t NT = static_cast<int64_t>(t_col.size());
-    std::vector<int64_t> t_sum(static_cast<size_t>(NT), 0);
-    std::vector<char> t_dup(static_cast<size_t>(NT), 0);
-    // per nonzero, its subject and its row's event count: the one pass of random lookups
-    // (the later passes read these in order)
-    HostBuf<int32_t> csub(static_cast<size_t>(hl.nnz));
-    HostBuf<int32_t> cy(static_cast<size_t>(hl.nnz));
-    parallel_for(NT, [&](int64_t t) {
-        const int64_t c0 = cptr[t_col[t]];
-        int64_t sum = 0;
-        for (int64_t e = t_lo[t]; e < t_hi[t]; ++e) {
-            const int32_t r = crow[e];
-            if (e > c0 && r == crow[e - 1]) t_dup[t] = 1;
-            const uint64_t ri = rowinfo[r];
-            const int32_t yv = static_cast<int32_t>(ri & 0xffffffffu);
-            csub[e] = static_cast<int32_t>(ri >> 32);
-            cy[e] = yv;
-            sum += yv;
-        }
-        t_sum[t] = sum;
-    });
-    hl.ytx.assign(static_cast<size_t>(J), 0.0);
-    {
-        std::vector<int64_t> ytx_i(static_cast<size_t>(J), 0);
-        for (int64_t t = 0; t < NT; ++t) {
-            if (t_dup[t]) return fail(SCCS_E_DUPLICATE, "a row appears twice in column " + std::to_string(t_col[t]));
-            ytx_i[t_col[t]] += t_sum[t];
-        }
-        for (int32_t j = 0; j < J; ++j) hl.ytx[j] = static_cast<double>(ytx_i[j]);   // exact below 2^53
-    }
-    for (int32_t j = 0; j < J; ++j) hl.max_col = std::max<int64_t>(hl.max_col, cptr[j + 1] - cptr[j]);
-
-    // ---- per column, the subjects with events on its rows and their event sums (what a
-    //      weighted Y'X_j needs, Section 2.5); rows are ascending, so a subject's rows are adjacent.
-    //      The same tasks, each start moved forward to a subject boundary so that no subject's
-    //      rows are split between two tasks.
-    {
-        std::vector<int64_t> s_lo2(static_cast<size_t>(NT)), s_hi2(static_cast<size_t>(NT));
-        for (int64_t t = 0; t < NT; ++t) {
-            const int64_t c0 = cptr[t_col[t]], c1 = cptr[t_col[t] + 1];
-            int64_t lo = t_lo[t];
-            while (lo > c0 && lo < c1 && csub[lo] == csub[lo - 1]) ++lo;
-            if (t > 0 && t_col[t - 1] == t_col[t]) lo = std::max(lo, s_lo2[t - 1]);   // monotone
-            s_lo2[t] = lo;
-        }
-        for (int64_t t = 0; t < NT; ++t)
-            s_hi2[t] = (t + 1 < NT && t_col[t + 1] == t_col[t]) ? s_lo2[t + 1] : cptr[t_col[t] + 1];
-        std::vector<int64_t> npairs(static_cast<size_t>(NT), 0);
-        parallel_for(NT, [&](int64_t t) {
-            int64_t c = 0;
-            int32_t cur = -1;
-            for (int64_t e = s_lo2[t]; e < s_hi2[t]; ++e) {
-                if (cy[e] > 0 && csub[e] != cur) {
-                    cur = csub[e];
-                    ++c;
-                }
-            }
-            npairs[t] = c;
-        });
-        std::vector<int64_t> t_off(static_cast<size_t>(NT) + 1, 0);
-        for (int64_t t = 0; t < NT; ++t) t_off[t + 1] = t_off[t] + npairs[t];
-        hl.ycol_ptr.assign(static_cast<size_t>(J) + 1, 0);
-        {
-            int64_t t = 0;
-            for (int32_t j = 0; j < J; ++j) {
-                hl.ycol_ptr[j] = t_off[t];
-                while (t < NT && t_col[t] == j) ++t;
-            }
-            hl.ycol_ptr[J] = t_off[NT];
-        }
-        hl.ysub.alloc(static_cast<size_t>(t_off[NT]));
-        hl.ycnt.alloc(static_cast<size_t>(t_off[NT]));
-        parallel_for(NT, [&](int64_t t) {
-            int64_t q = t_off[t] - 1;
-            int32_t cur = -1, acc = 0;                  // a pair's sum <= n_i < 2^31
-            for (int64_t e = s_lo2[t]; e < s_hi2[t]; ++e) {
-                if (cy[e] <= 0) continue;
-                if (csub[e] != cur) {
-                    if (q >= t_off[t]) hl.ycnt[q] = acc;
-                    cur = csub[e];
-                    ++q;
-                    hl.ysub[q] = cur;
-                    acc = 0;
-                }
-                acc += cy[e];
-            }
-            if (q >= t_off[t]) hl.ycnt[q] = acc;
-        });
-    }
-
-    // ---- narrow columns: few rows and subjects, run whole on one CTA (rows ascending, so a
-    //      subject's rows are adjacent and its segment is a run)
-    hl.narrow.assign(static_cast<size_t>(J), 0);
-    hl.next_wide.assign(static_cast<size_t>(J), 0);
-    hl.nar_ptr.assign(static_cast<size_t>(J) + 1, 0);
-    if (narrow_max > 0 && S >= kNarrowMinShards) {
-        std::vector<int64_t> nseg(static_cast<size_t>(J), 0);
-        parallel_for(J, [&](int64_t j) {
-            int64_t c = 0;
-            int32_t cur = -1;
-            for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e)
-                if (csub[e] != cur) {
-                    cur = csub[e];
-                    ++c;
-                }
-            nseg[j] = c;
-        });
-        int64_t rows_total = 0;
-        for (int32_t j = 0; j < J; ++j) {
-            const int64_t n = cptr[j + 1] - cptr[j];
-            // half the shared buffers each: the next column is gathered while this one steps
-            const bool fits = n <= narrow_max && n <= sccs::kRowCap / 2 && nseg[j] <= sccs::kSegCap / 2 &&
-                              rows_total + n < (int64_t(1) << 31);
-            hl.narrow[j] = fits ? 1 : 0;
-            hl.nar_ptr[j + 1] = hl.nar_ptr[j] + (fits ? nseg[j] : 0);
-            if (fits) {
-                rows_total += n;
-                hl.narrow_count++;
-            }
-        }
-        hl.nar_seg.resize(static_cast<size_t>(hl.nar_ptr[J]));
-        hl.nar_row.reserve(static_cast<size_t>(rows_total));
-        for (int32_t j = 0; j < J; ++j) {
-            if (!hl.narrow[j]) continue;
-            int64_t q = hl.nar_ptr[j] - 1;
-            int32_t cur = -1;
-            for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) {
-                const int32_t r = crow[e];
-                if (csub[e] != cur) {
-                    cur = csub[e];
-                    ++q;
-                    hl.nar_seg[q] = make_int4(cur, 0, static_cast<int>(hl.nar_row.size()), 0);
-                }
-                hl.nar_seg[q].y++;
-                hl.nar_row.push_back(r);
-            }
-        }
-        // Groups: consecutive narrow columns with pairwise disjoint subjects.  Neither column of a
-        // pair reads what the other writes (their subjects' E and D), so their coordinate steps can
-        // be taken side by side and give exactly the sequential result.  A group fits half the
-        // shared buffers (rows, segments), like one narrow column.
-        hl.nar_group.assign(static_cast<size_t>(J), 0);
-        std::vector<uint8_t> mark(static_cast<size_t>(std::max<int64_t>(hl.N, 1)), 0);
-        std::vector<int32_t> marked;
-        auto subjects_of = [&](int32_t j, bool set, bool &clash) {
-            for (int64_t q = hl.nar_ptr[j]; q < hl.nar_ptr[j + 1]; ++q) {
-                const int32_t i = hl.nar_seg[q].x;
-                if (mark[i]) clash = true;
-                if (set && !mark[i]) {
-                    mark[i] = 1;
-                    marked.push_back(i);
-                }
-            }
-        };
-        int32_t j = 0;
-        while (j < J) {
-            if (!hl.narrow[j]) {
-                ++j;
-                continue;
-            }
-            int32_t m = 1;
-            int64_t segs = hl.nar_ptr[j + 1] - hl.nar_ptr[j];
-            int64_t rows = cptr[j + 1] - cptr[j];
-            bool clash = false;
-            subjects_of(j, true, clash);
-            while (j + m < J && hl.narrow[j + m] && m < group_max) {
-                const int32_t jn = j + m;
-                const int64_t sg = hl.nar_ptr[jn + 1] - hl.nar_ptr[jn], rw = cptr[jn + 1] - cptr[jn];
-                if (segs + sg > sccs::kSegCap / 2 || rows + rw > sccs::kRowCap / 2) break;
-                clash = false;
-                subjects_of(jn, false, clash);
-                if (clash) break;
-                subjects_of(jn, true, clash);
-                segs += sg;
-                rows += rw;
-                ++m;
-            }
-            for (int32_t i : marked) mark[i] = 0;
-            marked.clear();
-            hl.nar_group[j] = m;
-            hl.narrow_groups++;
-            j += m;
-        }
-        // A group's state is gathered before the step ahead of it has written E and D: the run's
-        // first group while the wide column before the run is still being applied on the other
-        // shards, a later group while the previous group steps.  Each segment records the one
-        // step that can change its subject: w = c + 1 if the subject is in column c of the
-        // previous group, kNarrowAfterWide if the run's preceding wide column touches it, else 0.
-        // The kernel gathers a segment again when that step was not zero.
-        // (the wide column's subjects by binary search: its rows are ascending, a subject's rows
-        // are [pat_ptr[i], pat_ptr[i+1]))
-        std::vector<int64_t> tag(static_cast<size_t>(std::max<int64_t>(hl.N, 1)), -1);
-        int64_t pass = 0;
-        for (int32_t g = 0; g < J;) {
-            if (!hl.narrow[g]) {
-                ++g;
-                continue;
-            }
-            const int32_t m = hl.nar_group[g];
-            const bool run_start = g == 0 || !hl.narrow[g - 1];
-            ++pass;
-            for (int64_t q = hl.nar_ptr[g]; q < hl.nar_ptr[g + m]; ++q) {
-                const int32_t i = hl.nar_seg[q].x;
-                int w = 0;
-                if (run_start) {
-                    if (g > 0) {
-                        const int32_t *b = crow + cptr[g - 1], *e = crow + cptr[g];
-                        const int32_t *f = std::lower_bound(b, e, static_cast<int32_t>(hl.pat_ptr[i]));
-                        if (f != e && *f < hl.pat_ptr[i + 1]) w = sccs::kNarrowAfterWide;
-                    }
-                } else if (tag[i] >= 0 && tag[i] / 16 == pass - 1) {
-                    w = static_cast<int>(tag[i] % 16) + 1;
-                }
-                hl.nar_seg[q].w = w;
-            }
-            for (int32_t c = 0; c < m; ++c)
-                for (int64_t q = hl.nar_ptr[g + c]; q < hl.nar_ptr[g + c + 1]; ++q) tag[hl.nar_seg[q].x] = pass * 16 + c;
-            g += m;
-        }
-    }
-    for (int32_t j = 0; j < J; ++j)
-        if (!hl.narrow[j]) {
-            hl.first_wide = j;
-            break;
-        }
-    {
-        int32_t nxt = hl.first_wide;
-        for (int32_t j = J - 1; j >= 0; --j) {
-            hl.next_wide[j] = nxt;
-            if (!hl.narrow[j]) nxt = j;
-        }
-    }
-
-    // ---- shards at subject boundaries, balanced by rows; every column's slices over them
-    hl.S = S;
-    subject_shards(hl.pat_ptr, Nk, Kk, S, hl.shard_pat, hl.shard_row);
-    build_slices(J, S, hl.shard_row, cptr, crow, csub.data(), [](int32_t) { return true; }, hl.rows, hl.segs,
-                 hl.grp_base, hl.slice_row, hl.slice_seg, hl.slice_grp, hl.stash_stride, hl.estash_stride,
-                 hl.segments);
-
-    // ---- cluster columns: at most cluster_max nonzeros, over C subject shards of their own, each
-    //      slice small enough to be staged whole (else the column stays with the whole team)
-    hl.ccls.assign(static_cast<size_t>(J), 0);
-    hl.next_grid.assign(static_cast<size_t>(J), 0);
-    if (C > 0) {
-        hl.C = C;
-        subject_shards(hl.pat_ptr, Nk, Kk, C, hl.cshard_pat, hl.cshard_row);
-        for (int32_t j = 0; j < J; ++j) hl.ccls[j] = (cptr[j + 1] - cptr[j]) <= cluster_max ? 1 : 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            int64_t ms = 0, mr = 0, segs = 0;
-            build_slices(J, C, hl.cshard_row, cptr, crow, csub.data(), [&](int32_t j) { return hl.ccls[j] != 0; },
-                         hl.crows, hl.csegs, hl.cgrp_base, hl.cslice_row, hl.cslice_seg, hl.cslice_grp, ms, mr,
-                         segs);
-            bool changed = false;
-            for (int32_t j = 0; j < J; ++j) {
-                if (!hl.ccls[j]) continue;
-                for (int32_t c = 0; c < C; ++c) {
-                    const int64_t idx = static_cast<int64_t>(c) * (J + 1) + j;
-                    if (hl.cslice_row[idx + 1] - hl.cslice_row[idx] > sccs::kRowCap ||
-                        hl.cslice_seg[idx + 1] - hl.cslice_seg[idx] > sccs::kSegCap) {
-                        hl.ccls[j] = 0;
-                        changed = true;
-                        break;
-                    }
-                }
-            }
-            if (!changed) break;
-        }
-        for (int32_t j = 0; j < J; ++j) hl.cluster_count += hl.ccls[j];
-        // Groups: consecutive cluster columns with pairwise disjoint subjects, up to group_max, whose
-        // slices on every cluster shard fit one staging buffer together.  Neither column of a pair
-        // reads what the other writes, so their steps can be taken side by side with exactly the
-        // sequential result.
-        hl.cgroup.assign(static_cast<size_t>(J), 0);
-        auto slice_n = [&](const std::vector<int64_t> &a, int32_t c, int32_t j) {
-            const int64_t idx = static_cast<int64_t>(c) * (J + 1) + j;
-            return a[idx + 1] - a[idx];
-        };
-        // ext[j]: the group the greedy rule forms when it starts at cluster column j, found for
-        // every j in parallel (each thread stamps subjects with the start column it is trying);
-        // the greedy walk below then only follows ext from the first column of each run
-        std::vector<int32_t> ext(static_cast<size_t>(J), 1);
-        const int64_t parts = std::max<int64_t>(1, std::min<int64_t>(host_threads(), J));
-        parallel_chunks(J, parts, [&](int64_t, int64_t lo, int64_t hi) {
-            std::vector<int32_t> stamp(static_cast<size_t>(std::max<int64_t>(Nk, 1)), -1);
-            std::vector<int64_t> rows_c(static_cast<size_t>(C)), segs_c(static_cast<size_t>(C));
-            for (int64_t jj = lo; jj < hi; ++jj) {
-                const int32_t j = static_cast<int32_t>(jj);
-                if (!hl.ccls[j] || j + 1 >= J || !hl.ccls[j + 1]) continue;
-                for (int32_t c = 0; c < C; ++c) {
-                    rows_c[c] = slice_n(hl.cslice_row, c, j);
-                    segs_c[c] = slice_n(hl.cslice_seg, c, j);
-                }
-                bool marked = false;
-                int32_t m = 1;
-                while (j + m < J && hl.ccls[j + m] && m < group_max) {
-                    const int32_t jn = j + m;
-                    bool fits = true;
-                    for (int32_t c = 0; c < C && fits; ++c)
-                        fits = rows_c[c] + slice_n(hl.cslice_row, c, jn) <= sccs::kRowCap &&
-                               segs_c[c] + slice_n(hl.cslice_seg, c, jn) <= sccs::kSegCap;
-                    if (!fits) break;
-                    if (!marked) {              // the start column's subjects, once a candidate fits
-                        for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) stamp[csub[e]] = j;
-                        marked = true;
-                    }
-                    for (int64_t e = cptr[jn]; e < cptr[jn + 1] && fits; ++e)
-                        if (stamp[csub[e]] == j) fits = false;
-                    if (!fits) break;
-                    for (int32_t c = 0; c < C; ++c) {
-                        rows_c[c] += slice_n(hl.cslice_row, c, jn);
-                        segs_c[c] += slice_n(hl.cslice_seg, c, jn);
-                    }
-                    for (int64_t e = cptr[jn]; e < cptr[jn + 1]; ++e) stamp[csub[e]] = j;
-                    ++m;
-                }
-                ext[j] = m;
-            }
-        });
-        // Groups: consecutive cluster columns with pairwise disjoint subjects, up to group_max, whose
-        // slices on every cluster shard fit one staging buffer together, formed greedily.
-        for (int32_t j = 0; j < J;) {
-            if (!hl.ccls[j]) {
-                ++j;
-                continue;
-            }
-            const int32_t m = ext[j];
-            hl.cgroup[j] = m;
-            hl.cluster_groups++;
-            j += m;
-        }
-    }
-    for (int32_t j = 0; j < J; ++j)
-        if (!hl.ccls[j]) {
-            hl.first_grid = j;
-            break;
-        }
-    {
-        int32_t nxt = hl.first_grid;
-        for (int32_t j = J - 1; j >= 0; --j) {
-            hl.next_grid[j] = nxt;
-            if (!hl.ccls[j]) nxt = j;
-        }
-    }
     return SCCS_OK;
 }
 
@@ -1377,7 +728,6 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     }
     const int64_t cluster_max = o.cluster_max_nnz > 0 ? o.cluster_max_nnz : kClusterMaxNnzDefault;
 
-    HostLayout hl;
     const int32_t narrow_max = o.narrow_max_nnz == 0 ? kNarrowDefault : o.narrow_max_nnz;
     // every column of a group keeps at least two warps of the CTA
     const int32_t group_cap = std::max(1, std::min(kNarrowGroupMax, threads / 64));
@@ -1385,9 +735,6 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     // when every column small enough for the narrow path is a cluster column as well, the cluster
     // takes them all and no narrow layout is built
     const int32_t narrow_eff = (C > 0 && cluster_max >= narrow_max) ? -1 : narrow_max;
-    int rc = build_layout(K, patient_id, y, offset_L, J, col_ptr, row_idx, S, narrow_eff, group_max, hl, C,
-                          cluster_max);
-    if (rc != SCCS_OK) return rc;
 
     sccs_handle *h = new sccs_handle();
     h->device = o.device;
@@ -1405,45 +752,124 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
         }
         h->own_stream = true;
     }
+    // the layout's scratch (device) and the pinned words its stages read back
+    sccs::lay::Scratch scr(h->stream);
+    unsigned long long *pinned = nullptr;
     auto bail = [&](int code) {
         std::string msg = g_last_error;
+        scr.release();
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        if (pinned) cudaFreeHost(pinned);
         destroy_handle(h);
         g_last_error = msg;
         return code;
     };
+    int rc = SCCS_OK;
+    auto lay_fail = [&](int e, const char *what) { return bail(cuda_fail(static_cast<cudaError_t>(e), what)); };
     if ((ce = cudaEventCreate(&h->ev0)) != cudaSuccess || (ce = cudaEventCreate(&h->ev1)) != cudaSuccess)
         return bail(cuda_fail(ce, "cudaEventCreate"));
     if ((ce = cudaMallocHost(&h->out_host, sizeof(sccs::FitOut))) != cudaSuccess)
         return bail(cuda_fail(ce, "cudaMallocHost"));
     if ((ce = cudaMallocHost(&h->beta_host, sizeof(double) * std::max<int32_t>(J, 1))) != cudaSuccess)
         return bail(cuda_fail(ce, "cudaMallocHost"));
+    if ((ce = cudaMallocHost(&pinned, sizeof(unsigned long long) * (sccs::lay::kFCount + 2))) != cudaSuccess)
+        return bail(cuda_fail(ce, "cudaMallocHost"));
+
+    // ---- the layout, on the device (sccs_layout.cu); the host decides over columns
+    namespace lay = sccs::lay;
+    lay::Ctx c;
+    c.st = h->stream;
+    c.scr = &scr;
+    c.K = K;
+    c.nnz_in = col_ptr[J];
+    c.J = J;
+    c.flags_h = pinned;
+    c.total_h = reinterpret_cast<long long *>(pinned + lay::kFCount);
+    int le = lay::upload_inputs(c, patient_id, y, offset_L, col_ptr, row_idx);
+    if (le) return lay_fail(le, "layout: input upload");
+    h->arena.uploaded += K * (8 + 4 + 8) + 8 * (static_cast<int64_t>(J) + 1) + 4 * c.nnz_in;
+    // subjects, n_i, dropping n_i = 0
+    if ((le = lay::subjects_count(c))) return lay_fail(le, "layout: subjects");
+    if (c.Kk >= (int64_t(1) << 31)) return bail(fail(SCCS_E_INVAL, "more than 2^31-1 kept rows"));
+    if (c.flags_h[lay::kFBigN]) return bail(fail(SCCS_E_INVAL, "n_i exceeds 2^31-1"));
+    const int64_t Nk = c.Nk, Kk = c.Kk;
+    int64_t *pat_s = scr.get_n<int64_t>(static_cast<size_t>(Nk) + 1);
+    int32_t *nev_s = scr.get_n<int32_t>(static_cast<size_t>(Nk));
+    int64_t *kf_s = scr.get_n<int64_t>(static_cast<size_t>(Nk));
+    double *L_s = scr.get_n<double>(static_cast<size_t>(Kk));
+    if (!pat_s || !nev_s || !kf_s || !L_s) return bail(fail(SCCS_E_NOMEM, "layout scratch"));
+    if ((le = lay::subjects_fill(c, pat_s, nev_s, kf_s, L_s))) return lay_fail(le, "layout: subjects");
+    // columns: kept rows ascending, duplicates, Y'X_j
+    std::vector<int64_t> cptr, ytx_i, cseg;
+    if ((le = lay::columns(c, cptr, ytx_i))) return lay_fail(le, "layout: columns");
+    if (c.flags_h[lay::kFDup] != lay::kNone)
+        return bail(fail(SCCS_E_DUPLICATE, "a row appears twice in column " + std::to_string(c.flags_h[lay::kFDup])));
+    if ((le = lay::segments(c, cseg))) return lay_fail(le, "layout: segments");
+    lay::ScanBuf pair_sb;
+    int64_t npairs = 0;
+    if ((le = lay::pairs_count(c, pair_sb, npairs))) return lay_fail(le, "layout: pairs");
+    // shards at subject boundaries, balanced by rows, and their slices
+    int64_t *shard_pat_s = scr.get_n<int64_t>(static_cast<size_t>(S) + 1);
+    int64_t *shard_row_s = scr.get_n<int64_t>(static_cast<size_t>(S) + 1);
+    if (!shard_pat_s || !shard_row_s) return bail(fail(SCCS_E_NOMEM, "layout scratch"));
+    if ((le = lay::shards(c, pat_s, S, shard_pat_s, shard_row_s))) return lay_fail(le, "layout: shards");
+    lay::SliceSet ss;
+    ss.Sp = S;
+    ss.shard_pat = shard_pat_s;
+    if ((le = lay::slices_count(c, ss, nullptr, nullptr))) return lay_fail(le, "layout: slices");
+    int64_t max_col = 0;
+    for (int32_t j = 0; j < J; ++j) max_col = std::max<int64_t>(max_col, cptr[j + 1] - cptr[j]);
 
     sccs::DevLayout &d = h->d;
     d.S = S;
     d.J = J;
-    d.K = hl.K;
-    d.N = hl.N;
+    d.K = Kk;
+    d.N = Nk;
+    const size_t SJ = static_cast<size_t>(S) * (static_cast<size_t>(J) + 1);
     int32_t *rows;
     int2 *segs;
     int64_t *grp_base, *slice_row, *slice_seg, *slice_grp, *shard_row, *shard_pat, *pat_ptr;
     int32_t *nev, *ysub, *ycnt;
     double *L, *ytx;
     int64_t *ycol_ptr;
-    if ((rc = upload(h, &rows, hl.rows.data(), hl.rows.size(), sccs::kCopyPad)) ||
-        (rc = upload(h, &segs, hl.segs.data(), hl.segs.size(), sccs::kCopyPad)) ||
-        (rc = upload(h, &grp_base, hl.grp_base.data(), hl.grp_base.size(), sccs::kCopyPad)) ||
-        (rc = upload(h, &slice_row, hl.slice_row.data(), hl.slice_row.size())) ||
-        (rc = upload(h, &slice_seg, hl.slice_seg.data(), hl.slice_seg.size())) ||
-        (rc = upload(h, &slice_grp, hl.slice_grp.data(), hl.slice_grp.size())) ||
-        (rc = upload(h, &shard_row, hl.shard_row.data(), hl.shard_row.size())) ||
-        (rc = upload(h, &shard_pat, hl.shard_pat.data(), hl.shard_pat.size())) ||
-        (rc = upload(h, &pat_ptr, hl.pat_ptr.data(), hl.pat_ptr.size())) ||
-        (rc = upload(h, &nev, hl.nev.data(), hl.nev.size())) ||
-        (rc = upload(h, &L, hl.L.data(), hl.L.size())) ||
-        (rc = upload(h, &ytx, hl.ytx.data(), hl.ytx.size())))
+    std::vector<double> ytx_h(static_cast<size_t>(J));
+    for (int32_t j = 0; j < J; ++j) ytx_h[j] = static_cast<double>(ytx_i[j]);   // exact below 2^53
+    // allocation order as measured fastest for the fit: static structure, then the state
+    if ((rc = alloc_padded(h, &rows, static_cast<size_t>(ss.tr), sccs::kCopyPad)) ||
+        (rc = alloc_padded(h, &segs, static_cast<size_t>(ss.ts), sccs::kCopyPad)) ||
+        (rc = alloc_padded(h, &grp_base, static_cast<size_t>(ss.tg), sccs::kCopyPad)) ||
+        (rc = alloc_padded(h, &slice_row, SJ)) || (rc = alloc_padded(h, &slice_seg, SJ)) ||
+        (rc = alloc_padded(h, &slice_grp, SJ)) ||
+        (rc = copy_in(h, &shard_row, shard_row_s, static_cast<size_t>(S) + 1)) ||
+        (rc = copy_in(h, &shard_pat, shard_pat_s, static_cast<size_t>(S) + 1)) ||
+        (rc = copy_in(h, &pat_ptr, pat_s, static_cast<size_t>(Nk) + 1)) ||
+        (rc = copy_in(h, &nev, nev_s, static_cast<size_t>(Nk))) || (rc = copy_in(h, &L, L_s, static_cast<size_t>(Kk))) ||
+        (rc = upload(h, &ytx, ytx_h.data(), ytx_h.size())))
         return bail(rc);
-    h->kept_from = std::move(hl.kept_from);
-    h->nev_host = hl.nev;
+    if ((le = lay::slices_fill(c, ss, slice_row, slice_seg, slice_grp, rows, segs, grp_base)))
+        return lay_fail(le, "layout: slices");
+    auto reg = [&](int id, const void *p, int64_t bytes, bool host = false) { h->dbg[id] = {p, bytes, host}; };
+    reg(SCCS_DBG_ROWS, rows, 4 * ss.tr);
+    reg(SCCS_DBG_SEGS, segs, 8 * ss.ts);
+    reg(SCCS_DBG_GRP_BASE, grp_base, 8 * ss.tg);
+    reg(SCCS_DBG_SLICE_ROW, slice_row, 8 * static_cast<int64_t>(SJ));
+    reg(SCCS_DBG_SLICE_SEG, slice_seg, 8 * static_cast<int64_t>(SJ));
+    reg(SCCS_DBG_SLICE_GRP, slice_grp, 8 * static_cast<int64_t>(SJ));
+    reg(SCCS_DBG_SHARD_ROW, shard_row, 8 * (static_cast<int64_t>(S) + 1));
+    reg(SCCS_DBG_SHARD_PAT, shard_pat, 8 * (static_cast<int64_t>(S) + 1));
+    reg(SCCS_DBG_PAT_PTR, pat_ptr, 8 * (Nk + 1));
+    reg(SCCS_DBG_NEV, nev, 4 * Nk);
+    reg(SCCS_DBG_L, L, 8 * Kk);
+    reg(SCCS_DBG_YTX, ytx, 8 * static_cast<int64_t>(J));
+    h->kept_from.resize(static_cast<size_t>(Nk));
+    h->nev_host.resize(static_cast<size_t>(Nk));
+    if (Nk > 0) {
+        if ((ce = cudaMemcpyAsync(h->kept_from.data(), kf_s, 8 * static_cast<size_t>(Nk), cudaMemcpyDeviceToHost,
+                                  h->stream)) != cudaSuccess ||
+            (ce = cudaMemcpyAsync(h->nev_host.data(), nev_s, 4 * static_cast<size_t>(Nk), cudaMemcpyDeviceToHost,
+                                  h->stream)) != cudaSuccess)
+            return bail(cuda_fail(ce, "cudaMemcpyAsync D2H"));
+    }
     for (int32_t v : h->nev_host) h->max_nev = std::max(h->max_nev, v);
     d.rows = rows;
     d.segs = segs;
@@ -1457,97 +883,320 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
     d.nev = nev;
     d.L = L;
     d.ytx = ytx;
-    d.stash_stride = hl.stash_stride;
-    if ((rc = alloc_zero(h, &d.E, static_cast<size_t>(hl.K))) ||
-        (rc = alloc_zero(h, &d.D, static_cast<size_t>(hl.N))) ||
-        (rc = alloc_zero(h, &d.E32, static_cast<size_t>(hl.K))) ||
-        (rc = alloc_zero(h, &d.D32, static_cast<size_t>(hl.N))) ||
+    d.stash_stride = ss.max_seg;
+    if ((rc = alloc_zero(h, &d.E, static_cast<size_t>(Kk))) ||
+        (rc = alloc_zero(h, &d.D, static_cast<size_t>(Nk))) ||
+        (rc = alloc_zero(h, &d.E32, static_cast<size_t>(Kk))) ||
+        (rc = alloc_zero(h, &d.D32, static_cast<size_t>(Nk))) ||
         (rc = alloc_zero(h, &d.beta_priv, static_cast<size_t>(S) * std::max<int32_t>(J, 1))) ||
         (rc = alloc_zero(h, &d.trust_priv, static_cast<size_t>(S) * std::max<int32_t>(J, 1))) ||
-        (rc = alloc_zero(h, &d.stash, static_cast<size_t>(S) * 2 * static_cast<size_t>(hl.stash_stride))) ||
+        (rc = alloc_zero(h, &d.stash, static_cast<size_t>(S) * 2 * static_cast<size_t>(ss.max_seg))) ||
         (rc = alloc_zero(h, &d.slots, static_cast<size_t>(S) * 4)) ||
         (rc = alloc_zero(h, &h->out_dev, 1)) ||
         (rc = alloc_zero(h, &h->beta_dev, static_cast<size_t>(std::max<int32_t>(J, 1)))))
         return bail(rc);
     d.abort_flag = &h->out_dev->abort_flag;
     // The weighted-count pairs go last: the fit's state arrays keep the placement measured
-    // fastest (uploading 2 x 16 MB of pairs before them cost the 1M-subject fit 4%).
-    if ((rc = upload(h, &ycol_ptr, hl.ycol_ptr.data(), hl.ycol_ptr.size())) ||
-        (rc = upload(h, &ysub, hl.ysub.data(), hl.ysub.size())) ||
-        (rc = upload(h, &ycnt, hl.ycnt.data(), hl.ycnt.size())))
+    // fastest (placing 2 x 16 MB of pairs before them cost the 1M-subject fit 4%).
+    std::vector<int64_t> ycol_h;
+    if ((rc = alloc_padded(h, &ycol_ptr, static_cast<size_t>(J) + 1)) ||
+        (rc = alloc_padded(h, &ysub, static_cast<size_t>(npairs))) ||
+        (rc = alloc_padded(h, &ycnt, static_cast<size_t>(npairs))))
         return bail(rc);
+    if ((le = lay::pairs_fill(c, pair_sb, npairs, ysub, ycnt, ycol_h))) return lay_fail(le, "layout: pairs");
+    if ((ce = cudaMemcpyAsync(ycol_ptr, ycol_h.data(), 8 * ycol_h.size(), cudaMemcpyHostToDevice, h->stream)) !=
+        cudaSuccess)
+        return bail(cuda_fail(ce, "cudaMemcpyAsync H2D"));
     d.ycol_ptr = ycol_ptr;
     d.ysub = ysub;
     d.ycnt = ycnt;
+    reg(SCCS_DBG_YCOL_PTR, ycol_ptr, 8 * (static_cast<int64_t>(J) + 1));
+    reg(SCCS_DBG_YSUB, ysub, 4 * npairs);
+    reg(SCCS_DBG_YCNT, ycnt, 4 * npairs);
     {
-        // row -> columns index, built on the device from the slices (scratch freed below)
+        // row -> columns index, built on the device from the slices (scratch freed with the rest)
         int64_t *row_ptr = nullptr;
         int32_t *row_col = nullptr;
-        if ((rc = alloc_zero(h, &row_ptr, static_cast<size_t>(hl.K) + 1)) ||
-            (rc = alloc_zero(h, &row_col, static_cast<size_t>(hl.nnz))))
+        if ((rc = alloc_zero(h, &row_ptr, static_cast<size_t>(Kk) + 1)) ||
+            (rc = alloc_zero(h, &row_col, static_cast<size_t>(c.nnz))))
             return bail(rc);
-        void *scratch = nullptr;
-        const size_t K1 = static_cast<size_t>(std::max<int64_t>(hl.K, 1));
-        const size_t sb = 4 * K1 + 8 * K1 + 8 * sccs::row_index_scan_blocks(hl.K) + 512;
-        if (cudaMalloc(&scratch, sb) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return bail(fail(SCCS_E_NOMEM, "row index scratch"));
-        }
-        char *sp = static_cast<char *>(scratch);
-        auto *cnt = reinterpret_cast<int32_t *>(sp);
-        auto *cursor = reinterpret_cast<int64_t *>(sp + (4 * K1 + 255) / 256 * 256);
-        auto *sums = reinterpret_cast<int64_t *>(sp + (4 * K1 + 255) / 256 * 256 + (8 * K1 + 255) / 256 * 256);
-        const int le = sccs::launch_build_row_index(d, row_ptr, row_col, cnt, cursor, sums, h->stream);
-        const cudaError_t se = cudaStreamSynchronize(h->stream);
-        cudaFree(scratch);
-        if (le != 0) return bail(cuda_fail(static_cast<cudaError_t>(le), "row index build"));
-        if (se != cudaSuccess) return bail(cuda_fail(se, "row index build"));
+        const size_t K1 = static_cast<size_t>(std::max<int64_t>(Kk, 1));
+        int32_t *cnt = scr.get_n<int32_t>(K1);
+        int64_t *cursor = scr.get_n<int64_t>(K1);
+        int64_t *sums = scr.get_n<int64_t>(sccs::row_index_scan_blocks(Kk));
+        if (!cnt || !cursor || !sums) return bail(fail(SCCS_E_NOMEM, "row index scratch"));
+        if ((le = sccs::launch_build_row_index(d, row_ptr, row_col, cnt, cursor, sums, h->stream)))
+            return lay_fail(le, "row index build");
         d.row_ptr = row_ptr;
         d.row_col = row_col;
+        reg(SCCS_DBG_ROW_PTR, row_ptr, 8 * (Kk + 1));
+        reg(SCCS_DBG_ROW_COL, row_col, 4 * c.nnz);
     }
-    if (hl.narrow_count > 0) {
-        uint8_t *nar;
-        int32_t *nxt, *nrow, *ngrp;
-        int64_t *nptr;
-        int4 *nseg;
-        unsigned long long *nsync;
-        if ((rc = upload(h, &nar, hl.narrow.data(), hl.narrow.size())) ||
-            (rc = upload(h, &nxt, hl.next_wide.data(), hl.next_wide.size())) ||
-            (rc = upload(h, &nptr, hl.nar_ptr.data(), hl.nar_ptr.size())) ||
-            (rc = upload(h, &nseg, hl.nar_seg.data(), hl.nar_seg.size())) ||
-            (rc = upload(h, &nrow, hl.nar_row.data(), hl.nar_row.size())) ||
-            (rc = upload(h, &ngrp, hl.nar_group.data(), hl.nar_group.size())) ||
-            (rc = alloc_zero(h, &nsync, static_cast<size_t>(32))))
-            return bail(rc);
-        d.narrow = nar;
-        d.next_wide = nxt;
-        d.first_wide = hl.first_wide;
-        d.nar_ptr = nptr;
-        d.nar_seg = nseg;
-        d.nar_row = nrow;
-        d.nar_group = ngrp;
-        d.nar_sync = nsync;
+    std::vector<int32_t> nseg_col(static_cast<size_t>(J));
+    for (int32_t j = 0; j < J; ++j) nseg_col[j] = static_cast<int32_t>(cseg[j + 1] - cseg[j]);
+    // ---- narrow columns: few rows and subjects, run whole on one CTA
+    int32_t narrow_count = 0, first_wide_col = -1;
+    if (narrow_eff > 0 && S >= kNarrowMinShards) {
+        std::vector<uint8_t> narrow(static_cast<size_t>(J), 0);
+        std::vector<int64_t> nar_ptr(static_cast<size_t>(J) + 1, 0), row_first(static_cast<size_t>(J), 0);
+        int64_t rows_total = 0;
+        std::vector<int32_t> ncols;
+        for (int32_t j = 0; j < J; ++j) {
+            const int64_t n = cptr[j + 1] - cptr[j];
+            // half the shared buffers each: the next column is gathered while this one steps
+            const bool fits = n <= narrow_eff && n <= sccs::kRowCap / 2 && nseg_col[j] <= sccs::kSegCap / 2 &&
+                              rows_total + n < (int64_t(1) << 31);
+            narrow[j] = fits ? 1 : 0;
+            nar_ptr[j + 1] = nar_ptr[j] + (fits ? nseg_col[j] : 0);
+            row_first[j] = rows_total;
+            if (fits) {
+                rows_total += n;
+                ncols.push_back(j);
+            }
+        }
+        narrow_count = static_cast<int32_t>(ncols.size());
+        if (narrow_count > 0) {
+            std::vector<int32_t> lp_n;
+            if ((le = lay::last_prev_columns(c, pat_ptr, d.row_ptr, d.row_col, ncols, lp_n)))
+                return lay_fail(le, "layout: narrow groups");
+            std::vector<int32_t> lp(static_cast<size_t>(J), -1);
+            for (size_t q = 0; q < ncols.size(); ++q) lp[ncols[q]] = lp_n[q];
+            // Groups: consecutive narrow columns with pairwise disjoint subjects (no column of the
+            // group before jn shares a subject with jn: lp[jn] < j).  Neither column of a pair
+            // reads what the other writes (their subjects' E and D), so their coordinate steps
+            // can be taken side by side and give exactly the sequential result.  A group fits
+            // half the shared buffers (rows, segments), like one narrow column.
+            std::vector<int32_t> nar_group(static_cast<size_t>(J), 0);
+            for (int32_t j = 0; j < J;) {
+                if (!narrow[j]) {
+                    ++j;
+                    continue;
+                }
+                int32_t m = 1;
+                int64_t sg = nseg_col[j], rw = cptr[j + 1] - cptr[j];
+                while (j + m < J && narrow[j + m] && m < group_max) {
+                    const int32_t jn = j + m;
+                    if (sg + nseg_col[jn] > sccs::kSegCap / 2 || rw + (cptr[jn + 1] - cptr[jn]) > sccs::kRowCap / 2)
+                        break;
+                    if (lp[jn] >= j) break;
+                    sg += nseg_col[jn];
+                    rw += cptr[jn + 1] - cptr[jn];
+                    ++m;
+                }
+                nar_group[j] = m;
+                j += m;
+            }
+            // A group's state is gathered before the step ahead of it has written E and D: the
+            // run's first group while the wide column before the run is still being applied on
+            // the other shards, a later group while the previous group steps.  Each segment
+            // records the one step that can change its subject: w = c + 1 if the subject is in
+            // column c of the previous group, kNarrowAfterWide if the run's preceding wide column
+            // touches it, else 0.  The kernel gathers a segment again when that step was not zero.
+            std::vector<lay::NarrowCol> meta;
+            meta.reserve(ncols.size());
+            int32_t prev0 = -1, prevm = 0;
+            for (int32_t g = 0; g < J;) {
+                if (!narrow[g]) {
+                    ++g;
+                    continue;
+                }
+                const int32_t m = nar_group[g];
+                const bool run_start = g == 0 || !narrow[g - 1];
+                for (int32_t q = g; q < g + m; ++q) {
+                    lay::NarrowCol nc{};
+                    nc.j = q;
+                    nc.run_wide = run_start && g > 0 ? g - 1 : -1;
+                    nc.prev0 = run_start ? -1 : prev0;
+                    nc.prevm = run_start ? 0 : prevm;
+                    nc.nar_first = nar_ptr[q];
+                    nc.row_first = row_first[q];
+                    meta.push_back(nc);
+                }
+                prev0 = g;
+                prevm = m;
+                g += m;
+            }
+            std::vector<int32_t> next_wide(static_cast<size_t>(J), 0);
+            int32_t first_wide = -1;
+            for (int32_t j = 0; j < J; ++j)
+                if (!narrow[j]) {
+                    first_wide = j;
+                    break;
+                }
+            {
+                int32_t nxt = first_wide;
+                for (int32_t j = J - 1; j >= 0; --j) {
+                    next_wide[j] = nxt;
+                    if (!narrow[j]) nxt = j;
+                }
+            }
+            uint8_t *nar;
+            int32_t *nxt, *nrow, *ngrp;
+            int64_t *nptr;
+            int4 *nseg;
+            unsigned long long *nsync;
+            if ((rc = upload(h, &nar, narrow.data(), narrow.size())) ||
+                (rc = upload(h, &nxt, next_wide.data(), next_wide.size())) ||
+                (rc = upload(h, &nptr, nar_ptr.data(), nar_ptr.size())) ||
+                (rc = alloc_padded(h, &nseg, static_cast<size_t>(nar_ptr[J]))) ||
+                (rc = alloc_padded(h, &nrow, static_cast<size_t>(rows_total))) ||
+                (rc = upload(h, &ngrp, nar_group.data(), nar_group.size())) ||
+                (rc = alloc_zero(h, &nsync, static_cast<size_t>(32))))
+                return bail(rc);
+            if ((le = lay::narrow_fill(c, pat_ptr, d.row_ptr, d.row_col, meta, nseg, nrow, sccs::kNarrowAfterWide)))
+                return lay_fail(le, "layout: narrow columns");
+            d.narrow = nar;
+            d.next_wide = nxt;
+            d.first_wide = first_wide;
+            first_wide_col = first_wide;
+            reg(SCCS_DBG_NARROW, nar, J);
+            reg(SCCS_DBG_NEXT_WIDE, nxt, 4 * static_cast<int64_t>(J));
+            reg(SCCS_DBG_NAR_PTR, nptr, 8 * (static_cast<int64_t>(J) + 1));
+            reg(SCCS_DBG_NAR_SEG, nseg, 16 * nar_ptr[J]);
+            reg(SCCS_DBG_NAR_ROW, nrow, 4 * rows_total);
+            reg(SCCS_DBG_NAR_GROUP, ngrp, 4 * static_cast<int64_t>(J));
+            d.nar_ptr = nptr;
+            d.nar_seg = nseg;
+            d.nar_row = nrow;
+            d.nar_group = ngrp;
+            d.nar_sync = nsync;
+        }
     }
-    if (hl.C > 0) {
-        uint8_t *ccls;
+    // ---- cluster columns: at most cluster_max nonzeros, over C subject shards of their own, each
+    //      slice small enough to be staged whole (else the column stays with the whole team)
+    int32_t cluster_count = 0, first_grid_col = -1;
+    if (C > 0) {
+        int64_t *csp = scr.get_n<int64_t>(static_cast<size_t>(C) + 1);
+        int64_t *csr_s = scr.get_n<int64_t>(static_cast<size_t>(C) + 1);
+        uint8_t *mask_d = scr.get_n<uint8_t>(static_cast<size_t>(std::max<int32_t>(J, 1)));
+        if (!csp || !csr_s || !mask_d) return bail(fail(SCCS_E_NOMEM, "layout scratch"));
+        if ((le = lay::shards(c, pat_ptr, C, csp, csr_s))) return lay_fail(le, "layout: cluster shards");
+        std::vector<uint8_t> ccls(static_cast<size_t>(J), 0);
+        for (int32_t j = 0; j < J; ++j) ccls[j] = (cptr[j + 1] - cptr[j]) <= cluster_max ? 1 : 0;
+        if (J > 0 && (ce = cudaMemcpyAsync(mask_d, ccls.data(), ccls.size(), cudaMemcpyHostToDevice, h->stream)) !=
+                         cudaSuccess)
+            return bail(cuda_fail(ce, "cudaMemcpyAsync H2D"));
+        std::vector<int64_t> cnz, cns;
+        lay::SliceSet cs;
+        cs.Sp = C;
+        cs.shard_pat = csp;
+        cs.mask = mask_d;
+        if ((le = lay::slices_count(c, cs, &cnz, &cns))) return lay_fail(le, "layout: cluster slices");
+        auto at = [&](int32_t q, int32_t j) { return static_cast<size_t>(q) * (static_cast<size_t>(J) + 1) + j; };
+        bool changed = false;
+        for (int32_t j = 0; j < J; ++j) {
+            if (!ccls[j]) continue;
+            for (int32_t q = 0; q < C; ++q)
+                if (cnz[at(q, j)] > sccs::kRowCap || cns[at(q, j)] > sccs::kSegCap) {
+                    ccls[j] = 0;
+                    changed = true;
+                    break;
+                }
+        }
+        if (changed) {
+            if ((ce = cudaMemcpyAsync(mask_d, ccls.data(), ccls.size(), cudaMemcpyHostToDevice, h->stream)) !=
+                cudaSuccess)
+                return bail(cuda_fail(ce, "cudaMemcpyAsync H2D"));
+            lay::SliceSet cs2;
+            cs2.Sp = C;
+            cs2.shard_pat = csp;
+            cs2.mask = mask_d;
+            cs = cs2;
+            if ((le = lay::slices_count(c, cs, nullptr, nullptr))) return lay_fail(le, "layout: cluster slices");
+        }
+        std::vector<int32_t> ccols;
+        for (int32_t j = 0; j < J; ++j)
+            if (ccls[j]) ccols.push_back(j);
+        cluster_count = static_cast<int32_t>(ccols.size());
+        std::vector<int32_t> lp_c;
+        if ((le = lay::last_prev_columns(c, pat_ptr, d.row_ptr, d.row_col, ccols, lp_c)))
+            return lay_fail(le, "layout: cluster groups");
+        std::vector<int32_t> lp(static_cast<size_t>(J), -1);
+        for (size_t q = 0; q < ccols.size(); ++q) lp[ccols[q]] = lp_c[q];
+        // Groups: consecutive cluster columns with pairwise disjoint subjects, up to group_max,
+        // whose slices on every cluster shard fit one staging buffer together, formed greedily.
+        // Neither column of a pair reads what the other writes, so their steps can be taken side
+        // by side with exactly the sequential result.
+        std::vector<int32_t> cgroup(static_cast<size_t>(J), 0);
+        std::vector<int64_t> rows_c(static_cast<size_t>(C)), segs_c(static_cast<size_t>(C));
+        for (int32_t j = 0; j < J;) {
+            if (!ccls[j]) {
+                ++j;
+                continue;
+            }
+            for (int32_t q = 0; q < C; ++q) {
+                rows_c[q] = cnz[at(q, j)];
+                segs_c[q] = cns[at(q, j)];
+            }
+            int32_t m = 1;
+            while (j + m < J && ccls[j + m] && m < group_max) {
+                const int32_t jn = j + m;
+                bool fits = lp[jn] < j;
+                for (int32_t q = 0; q < C && fits; ++q)
+                    fits = rows_c[q] + cnz[at(q, jn)] <= sccs::kRowCap && segs_c[q] + cns[at(q, jn)] <= sccs::kSegCap;
+                if (!fits) break;
+                for (int32_t q = 0; q < C; ++q) {
+                    rows_c[q] += cnz[at(q, jn)];
+                    segs_c[q] += cns[at(q, jn)];
+                }
+                ++m;
+            }
+            cgroup[j] = m;
+            j += m;
+        }
+        int32_t first_grid = -1;
+        for (int32_t j = 0; j < J; ++j)
+            if (!ccls[j]) {
+                first_grid = j;
+                break;
+            }
+        std::vector<int32_t> next_grid(static_cast<size_t>(J), 0);
+        {
+            int32_t nxt = first_grid;
+            for (int32_t j = J - 1; j >= 0; --j) {
+                next_grid[j] = nxt;
+                if (!ccls[j]) nxt = j;
+            }
+        }
+        const size_t CJ = static_cast<size_t>(C) * (static_cast<size_t>(J) + 1);
+        uint8_t *ccls_d;
         int32_t *ngrid, *crows, *cgrp_n;
         int2 *csegs;
         int64_t *cgrp, *csr, *css, *csg;
         unsigned long long *csync;
-        if ((rc = upload(h, &ccls, hl.ccls.data(), hl.ccls.size())) ||
-            (rc = upload(h, &ngrid, hl.next_grid.data(), hl.next_grid.size())) ||
-            (rc = upload(h, &cgrp_n, hl.cgroup.data(), hl.cgroup.size())) ||
-            (rc = upload(h, &crows, hl.crows.data(), hl.crows.size(), sccs::kCopyPad)) ||
-            (rc = upload(h, &csegs, hl.csegs.data(), hl.csegs.size(), sccs::kCopyPad)) ||
-            (rc = upload(h, &cgrp, hl.cgrp_base.data(), hl.cgrp_base.size(), sccs::kCopyPad)) ||
-            (rc = upload(h, &csr, hl.cslice_row.data(), hl.cslice_row.size())) ||
-            (rc = upload(h, &css, hl.cslice_seg.data(), hl.cslice_seg.size())) ||
-            (rc = upload(h, &csg, hl.cslice_grp.data(), hl.cslice_grp.size())) ||
+        if ((rc = upload(h, &ccls_d, ccls.data(), ccls.size())) ||
+            (rc = upload(h, &ngrid, next_grid.data(), next_grid.size())) ||
+            (rc = upload(h, &cgrp_n, cgroup.data(), cgroup.size())) ||
+            (rc = alloc_padded(h, &crows, static_cast<size_t>(cs.tr), sccs::kCopyPad)) ||
+            (rc = alloc_padded(h, &csegs, static_cast<size_t>(cs.ts), sccs::kCopyPad)) ||
+            (rc = alloc_padded(h, &cgrp, static_cast<size_t>(cs.tg), sccs::kCopyPad)) ||
+            (rc = alloc_padded(h, &csr, CJ)) || (rc = alloc_padded(h, &css, CJ)) || (rc = alloc_padded(h, &csg, CJ)) ||
             (rc = alloc_zero(h, &csync, static_cast<size_t>(32))))
             return bail(rc);
-        d.C = hl.C;
-        d.first_grid = hl.first_grid;
-        d.ccls = ccls;
+        if ((le = lay::slices_fill(c, cs, csr, css, csg, crows, csegs, cgrp)))
+            return lay_fail(le, "layout: cluster slices");
+        d.C = C;
+        d.first_grid = first_grid;
+        first_grid_col = first_grid;
+        h->cshard_row_h.assign(static_cast<size_t>(C) + 1, 0);
+        h->cshard_pat_h.assign(static_cast<size_t>(C) + 1, 0);
+        if ((ce = cudaMemcpyAsync(h->cshard_row_h.data(), csr_s, 8 * (static_cast<size_t>(C) + 1),
+                                  cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+            (ce = cudaMemcpyAsync(h->cshard_pat_h.data(), csp, 8 * (static_cast<size_t>(C) + 1),
+                                  cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+            return bail(cuda_fail(ce, "cudaMemcpyAsync D2H"));
+        reg(SCCS_DBG_CCLS, ccls_d, J);
+        reg(SCCS_DBG_NEXT_GRID, ngrid, 4 * static_cast<int64_t>(J));
+        reg(SCCS_DBG_CGROUP, cgrp_n, 4 * static_cast<int64_t>(J));
+        reg(SCCS_DBG_CROWS, crows, 4 * cs.tr);
+        reg(SCCS_DBG_CSEGS, csegs, 8 * cs.ts);
+        reg(SCCS_DBG_CGRP_BASE, cgrp, 8 * cs.tg);
+        reg(SCCS_DBG_CSLICE_ROW, csr, 8 * static_cast<int64_t>(CJ));
+        reg(SCCS_DBG_CSLICE_SEG, css, 8 * static_cast<int64_t>(CJ));
+        reg(SCCS_DBG_CSLICE_GRP, csg, 8 * static_cast<int64_t>(CJ));
+        reg(SCCS_DBG_CSHARD_ROW, h->cshard_row_h.data(), 8 * (static_cast<int64_t>(C) + 1), true);
+        reg(SCCS_DBG_CSHARD_PAT, h->cshard_pat_h.data(), 8 * (static_cast<int64_t>(C) + 1), true);
+        d.ccls = ccls_d;
         d.next_grid = ngrid;
         d.cgroup = cgrp_n;
         d.crows = crows;
@@ -1562,32 +1211,58 @@ int sccs_create(sccs_handle **out, int64_t K, const int64_t *patient_id, const i
         // E per row of an unstaged slice between its phases A and C (allocated last: the arrays
         // above keep their measured placement)
         double *estash = nullptr;
-        if ((rc = alloc_zero(h, &estash, static_cast<size_t>(S) * static_cast<size_t>(hl.estash_stride))))
+        if ((rc = alloc_zero(h, &estash, static_cast<size_t>(S) * static_cast<size_t>(ss.max_rows))))
             return bail(rc);
         d.estash = estash;
-        d.estash_stride = hl.estash_stride;
+        d.estash_stride = ss.max_rows;
     }
     if ((rc = run_init_state(h, nullptr))) return bail(rc);
+    scr.release();
     ce = cudaStreamSynchronize(h->stream);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamSynchronize"));
+    cudaFreeHost(pinned);
+    pinned = nullptr;
 
+    h->scalars_h = {c.nnz, c.nsub, narrow_count, cluster_count, first_grid_col, ss.max_seg, ss.max_rows,
+                    first_wide_col};
+    h->dbg[SCCS_DBG_SCALARS] = {h->scalars_h.data(), 8 * static_cast<int64_t>(h->scalars_h.size()), true};
+    h->dbg[SCCS_DBG_KEPT_FROM] = {h->kept_from.data(), 8 * static_cast<int64_t>(h->kept_from.size()), true};
     sccs_data_info &info = h->info;
     info.rows_in = K;
-    info.rows_kept = hl.K;
-    info.subjects_in = hl.subjects_in;
-    info.subjects_kept = hl.N;
-    info.nnz_kept = hl.nnz;
-    info.segments = hl.segments;
-    info.max_column_nnz = hl.max_col;
+    info.rows_kept = Kk;
+    info.subjects_in = c.nsub;
+    info.subjects_kept = Nk;
+    info.nnz_kept = c.nnz;
+    info.segments = ss.ts;
+    info.max_column_nnz = max_col;
     info.device_bytes = h->arena.total;
     info.upload_bytes = h->arena.uploaded;
     info.columns = J;
     info.num_shards = S;
     info.threads_per_block = threads;
-    info.narrow_columns = hl.narrow_count;
-    info.cluster_ctas = hl.C;
-    info.cluster_columns = hl.cluster_count;
+    info.narrow_columns = narrow_count;
+    info.cluster_ctas = C;
+    info.cluster_columns = cluster_count;
     *out = h;
+    return SCCS_OK;
+}
+
+int sccs_debug_layout(const sccs_handle *h, int32_t which, void *dst, int64_t capacity, int64_t *bytes) {
+    if (!h || !bytes) return fail(SCCS_E_INVAL, "null argument");
+    if (which < 1 || which >= SCCS_DBG_COUNT) return fail(SCCS_E_INVAL, "unknown layout array");
+    const sccs_handle::DbgArr &a = h->dbg[which];
+    *bytes = a.p ? a.bytes : 0;
+    if (!dst || *bytes == 0) return SCCS_OK;
+    if (capacity < *bytes) return fail(SCCS_E_INVAL, "buffer too small for the layout array");
+    if (a.host) {
+        std::memcpy(dst, a.p, static_cast<size_t>(a.bytes));
+        return SCCS_OK;
+    }
+    int rc = set_device(h);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(dst, a.p, static_cast<size_t>(a.bytes), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "layout copy");
     return SCCS_OK;
 }
 

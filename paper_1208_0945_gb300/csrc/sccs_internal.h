@@ -118,7 +118,8 @@ struct FitParams {
     const int32_t *ho_nev;     // device [N] or null: held-out counts w_i n_i (FP64 fits only); the
     const double *ho_ytx;      // [J] fit then ends with Eq. 2 under them in out->heldout_loglik
     int32_t cluster;           // 1: launched in clusters of DevLayout::C CTAs (cluster columns on)
-    int32_t pad_c;
+    int32_t regather_e;        // 1: phase C of slices too big to stage gathers E again (from L2)
+                               //    instead of reading the E stash phase A wrote
 };
 
 struct FitOut {

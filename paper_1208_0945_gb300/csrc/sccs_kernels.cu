@@ -87,7 +87,14 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p) {
 // 4-byte asynchronous global -> shared copies (no registers held while in flight).
 __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
     const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+#if SCCS_L2HINT >= 1
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem_src), "l"(pol)
+                 : "memory");
+#else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem_src) : "memory");
+#endif
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -133,13 +140,64 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+#ifndef SCCS_L2HINT
+#define SCCS_L2HINT 0
+#endif
+#ifndef SCCS_REGATHER_E
+#define SCCS_REGATHER_E 0
+#endif
+// L2 eviction priorities: the static structure is read once per cycle and streamed past the
+// state (E, D), which is read and written at every step
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+template <class T>
+__device__ __forceinline__ T ld_static(const T *p) {
+#if SCCS_L2HINT >= 1
+    return __ldcs(p);
+#else
+    return *p;
+#endif
+}
+__device__ __forceinline__ double ld_state(const double *p) {
+#if SCCS_L2HINT >= 2
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(l2_evict_last()));
+    return v;
+#else
+    return *p;
+#endif
+}
+__device__ __forceinline__ void st_state(double *p, double v) {
+#if SCCS_L2HINT >= 2
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(l2_evict_last()) : "memory");
+#else
+    *p = v;
+#endif
+}
+
 // Global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+#if SCCS_L2HINT >= 1
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(l2_evict_first())
+        : "memory");
+#else
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+#endif
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
@@ -699,7 +757,7 @@ __device__ void phase_a_staged(const DevLayout &d, const ColDesc &cd, const Stag
         const int si = sbase + 32 * (g - gbase) + lane;
         const bool valid = si < send;
         const int2 sg = valid ? sseg[si] : make_int2(0, 0);
-        const double Dv = valid ? d.D[sg.x] : 1.0;
+        const double Dv = valid ? ld_state(d.D + sg.x) : 1.0;
         const int nv = valid ? d.nev[sg.x] : 0;
         int base = static_cast<int>(sgrp[g] - cd.row0);
         const int maxlen = __shfl_sync(kFull, sg.y, 0);  // segments are sorted longest first
@@ -718,7 +776,7 @@ __device__ void phase_a_staged(const DevLayout &d, const ColDesc &cd, const Stag
             }
             double e[kBatch];
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? d.E[k[u]] : 0.0;
+            for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? ld_state(d.E + k[u]) : 0.0;
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 if (t0 + u < maxlen) {       // warp-uniform: skip the FP64 add on empty diagonals
@@ -755,7 +813,8 @@ __device__ void phase_a_staged(const DevLayout &d, const ColDesc &cd, const Stag
 // E gathers start from rows already on chip instead of behind a dependent load.  Without a ring
 // (kRing false: a kernel with no room for it) the rows are read from global memory in place.
 template <bool kPipe>
-__device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, double &G, double &H, bool &bad) {
+__device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, double &G, double &H, bool &bad,
+                               bool stash_e = true) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
@@ -775,8 +834,8 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, 
         base = 0;
         if (g < ngrp) {
             const long long si = seg0 + 32 * static_cast<long long>(g) + lane;
-            if (si < seg1) sg = d.segs[si];
-            base = d.grp_base[grp0 + g];
+            if (si < seg1) sg = ld_static(d.segs + si);
+            base = ld_static(d.grp_base + grp0 + g);
         }
     };
     // the rows of a group's first kBatch diagonals are contiguous from its base (segments are
@@ -807,7 +866,7 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, 
         desc(g + 2 * nwarps, sg_n2, base_n2);
         const bool has_next = g + nwarps < ngrp;     // warp-uniform
         if (has_next) stage_rows(sg_n1, base_n1, half ^ 1);
-        const double Dv = valid ? d.D[sg.x] : 1.0;
+        const double Dv = valid ? ld_state(d.D + sg.x) : 1.0;
         const int nv = valid ? d.nev[sg.x] : 0;
         // this group's rows have landed (every copy group but the newest), for every lane
         if (kPipe) {
@@ -826,12 +885,12 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, 
             for (int u = 0; u < kBatch; ++u) {
                 const bool act = sg.y > t0 + u;
                 const unsigned m = __ballot_sync(kFull, act);
-                k[u] = act ? (staged ? rr[static_cast<int>(base - gbase) + lane] : d.rows[base + lane]) : -1;
+                k[u] = act ? (staged ? rr[static_cast<int>(base - gbase) + lane] : ld_static(d.rows + base + lane)) : -1;
                 base += __popc(m);
             }
             double e[kBatch];
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? d.E[k[u]] : 0.0;
+            for (int u = 0; u < kBatch; ++u) e[u] = k[u] >= 0 ? ld_state(d.E + k[u]) : 0.0;
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 if (t0 + u < maxlen) {                // warp-uniform
@@ -839,7 +898,7 @@ __device__ void phase_a_global(const DevLayout &d, int s, int j, int *ring_all, 
                     if (k[u] >= 0) {
                         if (init && u == 0) num = e[u];
                         else num += e[u];
-                        if (kPipe) __stcs(estash + (pb - row0 + lane), e[u]);   // streaming: E stays in L2
+                        if (kPipe && stash_e) __stcs(estash + (pb - row0 + lane), e[u]);   // streaming: E stays in L2
                     }
                     pb += __popc(m);
                 }
@@ -875,22 +934,44 @@ __device__ void phase_c_staged(const DevLayout &d, const ColDesc &cd, const Stag
                                double r, double em1) {
     const int2 *sseg = sb.segs + cd.seg_off;
     const int32_t *srow = sb.rows + cd.row_off;
-    for (int p = threadIdx.x; p < cd.nnz; p += blockDim.x) d.E[srow[p]] = sm.wide.est[p] * r;
+    for (int p = threadIdx.x; p < cd.nnz; p += blockDim.x) st_state(d.E + srow[p], sm.wide.est[p] * r);
     for (int si = threadIdx.x; si < cd.nseg; si += blockDim.x) {
         const double2 st = sm.wide.seg_stash[si];
-        d.D[sseg[si].x] = fma(em1, st.x, st.y);
+        st_state(d.D + sseg[si].x, fma(em1, st.x, st.y));
     }
 }
 
 // Phase C over a global slice.
-__device__ void phase_c_global(const DevLayout &d, int s, int j, double r, double em1) {
+__device__ void phase_c_global(const DevLayout &d, int s, int j, double r, double em1, bool regather = false) {
     const long long so = static_cast<long long>(s) * (d.J + 1) + j;
     const long long row0 = d.slice_row[so], row1 = d.slice_row[so + 1];
     const long long seg0 = d.slice_seg[so], seg1 = d.slice_seg[so + 1];
     const double *stash = d.stash + 2 * static_cast<long long>(s) * d.stash_stride;
+    const long long T = blockDim.x;
+    if (regather) {                               // E at the slice's rows again, mostly from L2
+        long long p = row0 + threadIdx.x;
+        for (; p + 3 * T < row1; p += 4 * T) {
+            int32_t k[4];
+            double e[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k[u] = ld_static(d.rows + p + u * T);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = ld_state(d.E + k[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) st_state(d.E + k[u], e[u] * r);
+        }
+        for (; p < row1; p += T) {
+            const int32_t k = ld_static(d.rows + p);
+            st_state(d.E + k, ld_state(d.E + k) * r);
+        }
+        for (long long si = seg0 + threadIdx.x; si < seg1; si += T) {
+            const double num = stash[2 * (si - seg0)], Dv = stash[2 * (si - seg0) + 1];
+            st_state(d.D + ld_static(d.segs + si).x, fma(em1, num, Dv));
+        }
+        return;
+    }
     // E as phase A gathered it, at each row's position in the slice (coalesced, no gather)
     const double *estash = d.estash + static_cast<long long>(s) * d.estash_stride - row0;
-    const long long T = blockDim.x;
     long long p = row0 + threadIdx.x;
     for (; p + 3 * T < row1; p += 4 * T) {
         int32_t k[4];
@@ -2080,7 +2161,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     double G = 0.0, H = 0.0;
                     if (cd.staged)
                         phase_a_staged(d, cd, sm.stage[buf], sm, warp, cd.ngrp, nwarps, 0, 0, cd.nseg, G, H, bad);
-                    else phase_a_global<true>(d, s, j, reinterpret_cast<int *>(&sm.wide), G, H, bad);
+                    else phase_a_global<true>(d, s, j, reinterpret_cast<int *>(&sm.wide), G, H, bad, !p.regather_e);
                     ga = fx_from_double(G, bad);
                     ha = fx_from_double(H, bad);
                 }
@@ -2176,7 +2257,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                         else phase_c_global32(d, s, j, r32, em32);
                     } else {
                         if (cd.staged) phase_c_staged(d, cd, sm.stage[buf], sm, sh.r, sh.em1);
-                        else phase_c_global(d, s, j, sh.r, sh.em1);
+                        else phase_c_global(d, s, j, sh.r, sh.em1, p.regather_e != 0);
                     }
                 }
                 if (threadIdx.x == tb) {
@@ -2287,20 +2368,31 @@ __global__ void __launch_bounds__(512, 1) fit_kernel(DevLayout d, FitParams p, F
     __shared__ SharedState sh;
     const bool clustered = p.cluster != 0;
     if (clustered) {
+        // The cluster columns take CTA c of the first cluster as cluster shard c and address their
+        // peers by cluster rank, so the launch must be in clusters of exactly C consecutive CTAs.
+        // A CTA that finds otherwise (a launch that dropped the cluster shape) takes no step: it
+        // sets the abort flag, every other CTA's waits give up, and the host reports the fit failed.
+        unsigned cid, crank, csize;
+        asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
+        const bool shape_ok = csize == static_cast<unsigned>(d.C) && cid * csize + crank == blockIdx.x;
         // the cluster all-reduce's mbarriers (one arrival and C x 16 bytes a round) are initialised
         // in every CTA before any CTA of the cluster can send bytes to them
         if (threadIdx.x == 0) {
             mbar_init(&sh.cbar[0], 1);
             mbar_init(&sh.cbar[1], 1);
             mbar_init_fence();
-            // the cluster columns take CTA c of the first cluster as cluster shard c: a launch whose
-            // clusters are not runs of consecutive CTAs is refused (every wait then gives up)
-            unsigned cid, crank;
-            asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
-            asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
-            if (cid * static_cast<unsigned>(d.C) + crank != blockIdx.x) atomicExch(d.abort_flag, 1);
+            if (!shape_ok) {
+                atomicExch(d.abort_flag, 1);
+                out->err_where = 4;
+            }
         }
         cluster_barrier_all();
+        if (!shape_ok) {
+            cluster_barrier_all();
+            return;
+        }
     }
     run_fit<F32>(d, p, out, hist, blockIdx.x, *reinterpret_cast<SmemLayout *>(smem_raw), sh);
     if (clustered) cluster_barrier_all();   // no CTA exits while another may still write its shared memory
@@ -2752,6 +2844,7 @@ int launch_fit(const DevLayout &d, const FitParams &p, FitOut *out_dev, double *
     FitParams pp = p;
     // FP64 fits of a layout with cluster columns launch in clusters of d.C CTAs
     pp.cluster = (!fp32 && d.C > 0 && d.S % d.C == 0) ? 1 : 0;
+    pp.regather_e = (!fp32 && SCCS_REGATHER_E) ? 1 : 0;
     void *args[] = {&dd, &pp, &out_dev, &hist_dev};
     void *fn = fp32 ? reinterpret_cast<void *>(fit_kernel<true>) : reinterpret_cast<void *>(fit_kernel<false>);
     if (!pp.cluster)

@@ -107,6 +107,7 @@ _SIGS = {
     "sccs_selftest_exp": (ctypes.c_int, [ctypes.c_int32, _dp, ctypes.c_int64, _dp, _dp]),
     "sccs_selftest_div": (ctypes.c_int, [ctypes.c_int32, _dp, _dp, ctypes.c_int64, _dp, _dp]),
     "sccs_check_wait_timeout": (ctypes.c_int, [_P, ctypes.c_double]),
+    "sccs_debug_layout": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "sccs_grad_hess_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int64, _P, _P]),
     "sccs_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(sccs_server_opts)]),
     "sccs_submit": (ctypes.c_int, [_P, ctypes.POINTER(sccs_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -295,6 +296,34 @@ def sccs_get_beta(handle, J: int) -> np.ndarray:
 def sccs_check_wait_timeout(handle, timeout_ms: float) -> int:
     """Returns the raw status; E_TIMEOUT (-6) is the expected result."""
     return _lib.sccs_check_wait_timeout(handle, float(timeout_ms))
+
+
+DBG = {name: i + 1 for i, name in enumerate(
+    "PAT_PTR NEV L YTX ROWS SEGS GRP_BASE SLICE_ROW SLICE_SEG SLICE_GRP SHARD_ROW SHARD_PAT YCOL_PTR YSUB YCNT "
+    "NARROW NEXT_WIDE NAR_PTR NAR_SEG NAR_ROW NAR_GROUP CCLS NEXT_GRID CGROUP CROWS CSEGS CGRP_BASE CSLICE_ROW "
+    "CSLICE_SEG CSLICE_GRP CSHARD_ROW CSHARD_PAT KEPT_FROM ROW_PTR ROW_COL SCALARS".split())}
+_DBG_TYPES = {"NEV": np.int32, "ROWS": np.int32, "YSUB": np.int32, "YCNT": np.int32, "NEXT_WIDE": np.int32,
+              "NAR_ROW": np.int32, "NAR_GROUP": np.int32, "NEXT_GRID": np.int32, "CGROUP": np.int32,
+              "CROWS": np.int32, "ROW_COL": np.int32, "SEGS": np.int32, "CSEGS": np.int32, "NAR_SEG": np.int32,
+              "NARROW": np.uint8, "CCLS": np.uint8, "L": np.float64, "YTX": np.float64}
+
+
+def sccs_debug_layout(handle, name: str) -> np.ndarray:
+    """One array of the handle's layout (a test diagnostic); SEGS / CSEGS come back as (n, 2) and
+    NAR_SEG as (n, 4) int32."""
+    which = DBG[name]
+    nbytes = ctypes.c_int64()
+    _check(_lib.sccs_debug_layout(handle, which, None, 0, ctypes.byref(nbytes)), "sccs_debug_layout")
+    dt = _DBG_TYPES.get(name, np.int64)
+    out = np.empty(nbytes.value // np.dtype(dt).itemsize, dt)
+    if out.size:
+        _check(_lib.sccs_debug_layout(handle, which, out.ctypes.data, nbytes.value, ctypes.byref(nbytes)),
+               "sccs_debug_layout")
+    if name in ("SEGS", "CSEGS"):
+        return out.reshape(-1, 2)
+    if name == "NAR_SEG":
+        return out.reshape(-1, 4)
+    return out
 
 
 NOALLOC_MAX_SEGMENTS = 1048576

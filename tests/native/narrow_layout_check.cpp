@@ -1,14 +1,19 @@
-// Host-side check of the narrow-column layout built by the library's own host code
-// (sccs_host.cpp, compiled into this program): every group's columns touch pairwise disjoint
+// Check of the narrow-column layout the library builds at sccs_create (fetched through the
+// layout diagnostic): every group's columns touch pairwise disjoint
 // subjects and fit half the shared buffers, and every segment's mark names exactly the one
 // earlier step that can change its subject -- the wide column before the run (for a run's
 // first group) or the column of the previous group holding the same subject -- checked by
-// brute force over the columns.  Exit status 0 when all hold.  Test infrastructure only.
-#include "../../paper_1208_0945_gb300/csrc/sccs_host.cpp"
+// brute force over the columns.  Exit status 0 when all hold (2: the handle could not be made).
+// Needs a GPU.  Test infrastructure only.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <random>
 #include <set>
+
+#include "../../paper_1208_0945_gb300/csrc/sccs_internal.h"
+#include "layout_fetch.h"
 
 int main(int argc, char **argv) {
     const int nsub = argc > 1 ? atoi(argv[1]) : 20000;
@@ -40,11 +45,19 @@ int main(int argc, char **argv) {
         for (int32_t r : rows) ri.push_back(r);
         cp[j + 1] = static_cast<int64_t>(ri.size());
     }
-    HostLayout hl;
-    if (build_layout(K, pid.data(), y.data(), L.data(), J, cp.data(), ri.data(), S, 1024, group_max, hl)) {
-        printf("build_layout failed\n");
+    sccs_create_opts o{};
+    o.struct_size = sizeof(o);
+    o.num_shards = S;
+    o.cluster_ctas = -1;
+    o.narrow_max_nnz = 1024;
+    o.narrow_group_max = group_max;
+    sccs_handle *h = nullptr;
+    if (sccs_create(&h, K, pid.data(), y.data(), L.data(), J, cp.data(), ri.data(), nullptr, &o) != SCCS_OK) {
+        printf("sccs_create failed: %s\n", sccs_last_error(nullptr));
         return 2;
     }
+    const Layout hl = load_layout(h);
+    sccs_destroy(h);
     if (hl.N != nsub || hl.K != K) {
         printf("unexpected subject drop\n");
         return 2;

@@ -1,17 +1,21 @@
-// Host-side check of the whole layout the library's host code builds (sccs_host.cpp, compiled
-// into this program), against a brute-force construction from the definitions: the kept
+// Check of the whole layout the library builds on the device at sccs_create (fetched through
+// the layout diagnostic), against a brute-force construction from the definitions: the kept
 // subjects (n_i > 0, input order) and their rows, each column's kept rows and Y'X_j, the
 // per-column (subject, event sum) pairs, and every (shard, column) slice -- its rows, its subject
 // segments longest first (ties in subject order), the rows of each 32-segment group diagonal by
 // diagonal, the group bases -- and the stash strides.  The data has subjects without events and
-// columns in shuffled order, or neither, so both paths of the host code run.  Exit status 0
-// when all hold.  Test infrastructure only.
-#include "../../paper_1208_0945_gb300/csrc/sccs_host.cpp"
+// columns in shuffled order, or neither, so every path of the layout stages runs.  Exit status 0
+// when all hold (2: the handle could not be made).  Needs a GPU.  Test infrastructure only.
 #include <algorithm>
+#include <cstdlib>
 #include <cstdio>
 #include <map>
 #include <iterator>
 #include <random>
+#include <string>
+
+#include "../../paper_1208_0945_gb300/csrc/sccs_internal.h"
+#include "layout_fetch.h"
 
 static long long g_bad = 0;
 #define CHECK(cond, ...)                      \
@@ -63,11 +67,17 @@ int main(int argc, char **argv) {
         for (int32_t r : col) ri.push_back(r);
         cp[j + 1] = static_cast<int64_t>(ri.size());
     }
-    HostLayout hl;
-    if (build_layout(K, pid.data(), y.data(), L.data(), J, cp.data(), ri.data(), S, 1024, 8, hl, C, cmax)) {
-        printf("build_layout failed: %s\n", g_last_error.c_str());
+    sccs_create_opts o{};
+    o.struct_size = sizeof(o);
+    o.num_shards = S;
+    o.cluster_ctas = C > 0 ? C : -1;
+    o.cluster_max_nnz = static_cast<int32_t>(std::min<int64_t>(cmax, 2000000000));
+    sccs_handle *h = nullptr;
+    if (sccs_create(&h, K, pid.data(), y.data(), L.data(), J, cp.data(), ri.data(), nullptr, &o) != SCCS_OK) {
+        printf("sccs_create failed: %s\n", sccs_last_error(nullptr));
         return 2;
     }
+    const Layout hl = load_layout(h);
 
     // ---- subjects and rows, from the definitions
     std::vector<int64_t> first;                      // input subjects' first rows
@@ -127,8 +137,9 @@ int main(int argc, char **argv) {
     // ---- slices of one partition (S shards, or the C cluster shards) of the columns in_set
     auto check_slices = [&](const char *tag, int S_, const std::vector<int64_t> &shard_row, const std::vector<int64_t> &shard_pat,
                             const std::vector<int64_t> &slice_row, const std::vector<int64_t> &slice_seg,
-                            const std::vector<int64_t> &slice_grp, const HostBuf<int32_t> &hrows, const HostBuf<int2> &hsegs,
-                            const HostBuf<int64_t> &hgrp, auto in_set, int64_t &max_seg, int64_t &max_rows) {
+                            const std::vector<int64_t> &slice_grp, const std::vector<int32_t> &hrows,
+                            const std::vector<int2> &hsegs, const std::vector<int64_t> &hgrp, auto in_set,
+                            int64_t &max_seg, int64_t &max_rows) {
         max_seg = 1;
         max_rows = 1;
         CHECK(shard_row[0] == 0 && shard_row[S_] == Kk && shard_pat[S_] == Nk, "%s shard ends\n", tag);
@@ -261,17 +272,20 @@ int main(int argc, char **argv) {
             j += m;
         }
     }
-    int32_t first_grid = -1;
-    for (int j = 0; j < J && first_grid < 0; ++j)
-        if (!hl.ccls[j]) first_grid = j;
-    CHECK(hl.first_grid == first_grid, "first grid column\n");
-    for (int j = 0; j < J; ++j) {
-        int32_t nx = -1;
-        for (int t = 1; t <= J && nx < 0; ++t)
-            if (!hl.ccls[(j + t) % J]) nx = (j + t) % J;
-        CHECK(hl.next_grid[j] == nx, "next grid column after %d\n", j);
+    if (C > 0) {
+        int32_t first_grid = -1;
+        for (int j = 0; j < J && first_grid < 0; ++j)
+            if (!hl.ccls[j]) first_grid = j;
+        CHECK(hl.first_grid == first_grid, "first grid column\n");
+        for (int j = 0; j < J; ++j) {
+            int32_t nx = -1;
+            for (int t = 1; t <= J && nx < 0; ++t)
+                if (!hl.ccls[(j + t) % J]) nx = (j + t) % J;
+            CHECK(hl.next_grid[j] == nx, "next grid column after %d\n", j);
+        }
     }
     CHECK(hl.stash_stride == max_seg && hl.estash_stride == max_rows, "stash strides\n");
+    sccs_destroy(h);
     printf("subjects %lld kept %lld rows %lld nnz %lld shards %d columns %d cluster_columns %lld mismatches %lld\n",
            (long long)nin, (long long)Nk, (long long)Kk, (long long)nnz, S, J, (long long)ccount, g_bad);
     return g_bad ? 1 : 0;

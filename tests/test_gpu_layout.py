@@ -1,13 +1,18 @@
-"""Host logic of the device layout (no GPU).  Narrow columns: groups of consecutive narrow columns touch
-pairwise disjoint subjects and fit half the shared buffers, and each segment's mark names the
-one earlier step that can change its subject (the GPU re-gathers a segment exactly when that
-step was not zero).  The check compiles the library's host source into a small C++ program and
-compares every mark with a brute-force search over the columns."""
+"""The data layout sccs_create builds on the device, against its definitions.  Two small C++
+programs link the library, make a handle, copy its layout back through the layout diagnostic
+(sccs_debug_layout) and compare it with a brute-force construction: the whole layout (kept
+subjects and rows, each column's kept rows, Y'X_j and event pairs, every slice's segments,
+diagonal-major rows and group bases, the cluster columns and their groups), and the narrow
+columns (groups of consecutive narrow columns touch pairwise disjoint subjects and fit half the
+shared buffers; each segment's mark names the one earlier step that can change its subject, so
+the GPU re-gathers a segment exactly when that step was not zero)."""
 import os
 import shutil
 import subprocess
 
 import pytest
+
+pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "tests", "native", "narrow_layout_check.cpp")
@@ -22,8 +27,6 @@ def checker(tmp_path_factory):
     import __graft_entry__
     lib = __graft_entry__._build_module().build()
     exe = str(tmp_path_factory.mktemp("narrow") / "narrow_layout_check")
-    # the host source is compiled in; the kernels' launchers it names come from the built
-    # library and are never called, so the program needs no GPU
     cmd = [nvcc, "-std=c++17", "-O2", "-I" + os.path.join(ROOT, "include"), SRC, lib,
            "-Xlinker", "-rpath=" + os.path.dirname(lib), "-o", exe, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -71,7 +74,7 @@ def slice_checker(tmp_path_factory):
                                                          (20000, 90, 11, 24, 0, 8, 100000),
                                                          (6000, 50, 12, 8, 1, 4, 5000), (3000, 30, 13, 8, 1, 8, 10**9)])
 def test_slice_layout_against_brute_force(slice_checker, nsub, J, seed, S, messy, C, cmax):
-    """The whole host layout -- kept subjects and rows, per-column kept rows, Y'X_j and event
+    """The whole layout -- kept subjects and rows, per-column kept rows, Y'X_j and event
     pairs, every (shard, column) slice's segments, diagonal-major rows and group bases -- against
     a brute-force construction, with dropped subjects and shuffled columns (messy) or without; with
     C > 0 also the cluster columns (at most cmax nonzeros and every slice over the C cluster shards
