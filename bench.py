@@ -43,7 +43,7 @@ def workload_config(d, fit):
 
 def recorded_traffic():
     """DRAM bytes per fit-kernel launch from the committed ncu record, if it was taken on the
-    kernel source that is built now (else None: the counters are stale)."""
+    kernel source that is built now (else None: the counters are stale), and how it was taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "fit_kernel_traffic_mid_1M_subjects.json")) as f:
@@ -51,10 +51,10 @@ def recorded_traffic():
         with open(os.path.join(ROOT, rec["kernel_source"]), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
         if sha != rec["kernel_source_sha256"]:
-            return None
-        return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+            return None, None
+        return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"], rec.get("config_note")
     except Exception:
-        return None
+        return None, None
 
 
 def load_peaks():
@@ -292,6 +292,7 @@ def run_ours(args, rank, world, local):
     flops_launch = fp64_flops(info, statistics.mean(cycles), nz_frac)
     clocks = clk.summary()
 
+    traffic, traffic_note = recorded_traffic() if args.scale == 1.0 else (None, None)
     # end to end through the C ABI from host arrays: create (validate, lay out, upload),
     # fit, read beta back, destroy
     e2e_ms = []
@@ -328,13 +329,15 @@ def run_ours(args, rank, world, local):
                     "shards": info["num_shards"], "threads_per_block": info["threads_per_block"],
                     "wall_s": wall},
             "roofline": roofline(bytes_launch, flops_launch, kern_ms, "fit_kernel (one persistent launch per fit)",
-                                 recorded_traffic() if args.scale == 1.0 else None),
+                                 traffic),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms_max,
                     "what": "sccs_create from host arrays (validate, lay out, upload) + sccs_fit + beta D2H + destroy"},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
         }
+        if traffic_note:
+            line["roofline"]["traffic_note"] = traffic_note
         if cpu is not None:
             line["cpu_baseline"] = cpu
     model.close()
@@ -869,7 +872,7 @@ def run_large_columns(args, rank, world, local):
     torch.cuda.set_device(dev)
     d, fit = large_columns_config(scale=args.scale)
     stream = torch.cuda.current_stream(dev)
-    model = sccs.SCCSModel(d, device=local, stream=ctypes.c_void_p(stream.cuda_stream))
+    model = sccs.SCCSModel(d, device=local, stream=ctypes.c_void_p(stream.cuda_stream), cluster_ctas=args.cluster_ctas)
     model.set_prior(fit["prior"], fit["variance"])
     info = model.info
     cycles = fit["cycles"]
