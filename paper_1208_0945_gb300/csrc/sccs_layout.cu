@@ -379,19 +379,18 @@ struct PairG {
 // ------------------------------------------------------------------ shards and slices
 
 // Shards at subject boundaries, balanced by rows (one thread: Sp binary searches)
+// Shard s starts at the first subject whose rows begin at or after K s / Sp (one thread per shard:
+// the targets rise with s, so the starts do too).
 __global__ void shards_kernel(const long long *pat_ptr, long long Nk, long long Kk, int Sp, long long *shard_pat,
                               long long *shard_row) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    shard_pat[0] = 0;
-    long long prev = 0;
-    for (int s = 1; s < Sp; ++s) {
-        const long long target = (Kk * s) / Sp;
-        const long long p = lower_bound_dev(pat_ptr, 0, Nk + 1, target);
-        prev = max(prev, min(p, Nk));
-        shard_pat[s] = prev;
+    for (int s = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x); s <= Sp;
+         s += static_cast<int>(gridDim.x * blockDim.x)) {
+        long long p = 0;
+        if (s == Sp) p = Nk;
+        else if (s > 0) p = min(lower_bound_dev(pat_ptr, 0, Nk + 1, (Kk * s) / Sp), Nk);
+        shard_pat[s] = p;
+        shard_row[s] = pat_ptr[p];
     }
-    shard_pat[Sp] = Nk;
-    for (int s = 0; s <= Sp; ++s) shard_row[s] = pat_ptr[shard_pat[s]];
 }
 
 __global__ void slice_count_kernel(int Sp, int J, const long long *shard_pat, const uint8_t *mask,
@@ -898,7 +897,7 @@ int pairs_fill(Ctx &c, ScanBuf &sb, int64_t npairs, int32_t *ysub, int32_t *ycnt
 }
 
 int shards(Ctx &c, const int64_t *pat_ptr, int32_t Sp, int64_t *shard_pat, int64_t *shard_row) {
-    shards_kernel<<<1, 32, 0, c.st>>>(reinterpret_cast<const long long *>(pat_ptr), c.Nk, c.Kk, Sp,
+    shards_kernel<<<(Sp + 1 + 127) / 128, 128, 0, c.st>>>(reinterpret_cast<const long long *>(pat_ptr), c.Nk, c.Kk, Sp,
                                       reinterpret_cast<long long *>(shard_pat), reinterpret_cast<long long *>(shard_row));
     return static_cast<int>(cudaGetLastError());
 }
