@@ -22,11 +22,12 @@
 //     shared memory by bulk asynchronous copies (cp.async.bulk + mbarrier) one column ahead,
 //     so only the gathers of the state E and D remain on the critical path.
 //   * FP64 issues at one warp-instruction per 64 cycles per SM sub-partition, whatever the
-//     number of active lanes, so every reduction (lane -> warp -> CTA -> grid) is done in
-//     exact 192-bit fixed point with integer instructions.  Exact sums are independent of
-//     order: all CTAs obtain bit-identical totals, and results do not depend on the launch
-//     shape.  FP64 is kept for the per-subject arithmetic and the scalar step, which one
-//     lane computes once per coordinate.
+//     number of active lanes, so the reduction inside a CTA (lane -> warp -> CTA) is done in
+//     exact 192-bit fixed point with integer instructions: it does not depend on which thread
+//     took which subject.  Each CTA's total, rounded once, then meets the other CTAs' totals in
+//     a fixed FP64 order (by shard, not by arrival), so all CTAs obtain bit-identical totals
+//     and every run is repeatable bit for bit.  FP64 is kept for the per-subject arithmetic and
+//     the scalar step, which one lane computes once per coordinate.
 //
 // Every wait is bounded by a deadline on %globaltimer; a CTA that gives up raises the abort
 // flag, waits (bounded) for its own bulk copies in flight and returns; the others see the
@@ -353,6 +354,14 @@ __device__ __forceinline__ Fx fx_warp_sum(Fx v) {
     return v;
 }
 
+// Warp sum by a fixed FP64 tree (xor butterfly): lane 0's order of additions is always the same,
+// so its result is a deterministic function of the 32 inputs; only lane 0's result is used.
+__device__ __forceinline__ double warp_tree_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
 // ------------------------------------------------------------------ shared state
 
 struct StageBuf {
@@ -377,6 +386,7 @@ struct SharedState {
     Fx wa[kMaxWarps];
     Fx wb[kMaxWarps];
     int wbad[kMaxWarps];
+    double wda[kMaxWarps], wdb[kMaxWarps];   // per warp: its FP64 sums (the coordinate path)
     double db, r, em1;
     // a group of narrow (or cluster) columns: per column step results, and the group's flags
     double gdb[kNarrowGroupMax], gr[kNarrowGroupMax], gem1[kNarrowGroupMax], gnbj[kNarrowGroupMax],
@@ -441,8 +451,9 @@ static_assert(sizeof(SmemLayout) - sizeof(NarrowBuf) >= offsetof(SmemLayout, nar
 // phase ((seq >> 1) & 1) ^ 1, which differs from what the buffer held two rounds earlier,
 // so a reader can tell a fresh value from a stale one without a separate flag.  A CTA can
 // not run two rounds ahead of a reader, because the round after next needs the reader's
-// own contribution.  The totals are exact fixed-point sums rounded once, so every CTA
-// holds the same bits.  With `sync` the round is also a release/acquire: each CTA's writes
+// own contribution.  The totals are FP64 sums in one fixed order over the slots (each lane its
+// slots in ascending order, then a fixed tree over the lanes, whose lane-0 result every CTA
+// takes), so every CTA holds the same bits, whatever the order the partials arrived in.  With `sync` the round is also a release/acquire: each CTA's writes
 // before its contribution (ordered by a CTA barrier before the call) are visible to every
 // CTA after the call (and, after a CTA barrier, to all its threads).
 __device__ bool grid_allreduce2(const DevLayout &d, int me, unsigned long long seq, double a, double b, double &A,
@@ -459,8 +470,7 @@ __device__ bool grid_allreduce2(const DevLayout &d, int me, unsigned long long s
         st_relaxed_v2(buf + 2 * me, ea, eb);
     }
     const long long deadline = now_ns() + timeout_ns;
-    Fx sa = fx_zero(), sb = fx_zero();
-    bool bad = false;
+    double sa = 0.0, sb = 0.0;
     for (int it = 0;; ++it) {
         bool ready = true;
         unsigned long long va[5], vb[5];
@@ -479,18 +489,20 @@ __device__ bool grid_allreduce2(const DevLayout &d, int me, unsigned long long s
         for (int q = 0; q < 5; ++q)
             if (lane + 32 * q < d.S) ready &= ((va[q] >> 63) == phase) && ((vb[q] >> 63) == phase);
         if (__all_sync(kFull, ready)) {
+            // each lane adds its slots in ascending order, then a fixed tree over the lanes: lane
+            // 0's order of additions is the same in every CTA (NaN, a bad partial, carries through)
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
                 if (lane + 32 * q < d.S) {
-                    sa = fx_add(sa, fx_from_double(__longlong_as_double(static_cast<long long>(va[q] & 0x7fffffffffffffffull)), bad));
-                    sb = fx_add(sb, fx_from_double(__longlong_as_double(static_cast<long long>(vb[q] & 0x7fffffffffffffffull)), bad));
+                    sa += __longlong_as_double(static_cast<long long>(va[q] & 0x7fffffffffffffffull));
+                    sb += __longlong_as_double(static_cast<long long>(vb[q] & 0x7fffffffffffffffull));
                 }
             }
             for (int s = lane + 160; s < d.S; s += 32) {
                 unsigned long long x, y;
                 ld_relaxed_v2(buf + 2 * s, x, y);
-                sa = fx_add(sa, fx_from_double(__longlong_as_double(static_cast<long long>(x & 0x7fffffffffffffffull)), bad));
-                sb = fx_add(sb, fx_from_double(__longlong_as_double(static_cast<long long>(y & 0x7fffffffffffffffull)), bad));
+                sa += __longlong_as_double(static_cast<long long>(x & 0x7fffffffffffffffull));
+                sb += __longlong_as_double(static_cast<long long>(y & 0x7fffffffffffffffull));
             }
             break;
         }
@@ -503,13 +515,13 @@ __device__ bool grid_allreduce2(const DevLayout &d, int me, unsigned long long s
         }
     }
     if (sync) __threadfence();                        // acquire: after reading every slot
-    sa = fx_warp_sum(sa);
-    sb = fx_warp_sum(sb);
-    const bool any_bad = __any_sync(kFull, bad);
-    double ta = fx_to_double(sa), tb = fx_to_double(sb);
-    if (any_bad) ta = tb = __longlong_as_double(0x7ff8000000000000ll);
-    A = __shfl_sync(kFull, ta, 0);
-    B = __shfl_sync(kFull, tb, 0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(kFull, sa, o);
+        sb += __shfl_xor_sync(kFull, sb, o);
+    }
+    A = __shfl_sync(kFull, sa, 0);
+    B = __shfl_sync(kFull, sb, 0);
     return true;
 }
 
@@ -1741,7 +1753,7 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
 // (gather L x exp(Xb), the segment numerators, the W terms of Eqs. 7-9), the CTA's exact sums,
 // then warp t sends its column's pair to slot [t][c] of every CTA of the cluster by asynchronous
 // stores counted on the receiver's mbarrier of this round (r & 1; armed by warp 0 for the C x m
-// pairs it receives), waits (bounded) for that phase, adds the C pairs exactly -- every CTA holds
+// pairs it receives), waits (bounded) for that phase, adds the C pairs in a fixed order -- every CTA holds
 // the same totals -- and lane 0 takes the step of Eq. 4 (prior, trust region) for column j + t.
 // Then phase C for every column with db != 0.  A CTA is at most one round ahead of another (the
 // round after needs the slower CTA's own pairs), so bytes of round r + 1 only meet the other
@@ -1767,12 +1779,12 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
         phase_a_staged(d, cd, sb, sm, go.goff[t] + wi, go.goff[t + 1], wpc, go.goff[t], go.soff[t], go.soff[t + 1], G, H,
                        bad);
     {
-        const Fx fa = fx_warp_sum(fx_from_double(G, bad));
-        const Fx fb = fx_warp_sum(fx_from_double(H, bad));
+        const double fa = warp_tree_sum(G);
+        const double fb = warp_tree_sum(H);
         const int wbad = __any_sync(kFull, bad);
         if (lane == 0) {
-            sh.wa[warp] = fa;
-            sh.wb[warp] = fb;
+            sh.wda[warp] = fa;
+            sh.wdb[warp] = fb;
             sh.wbad[warp] = wbad;
         }
     }
@@ -1781,13 +1793,10 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
         const int C = d.C;
         const int buf = static_cast<int>(round & 1u);
         const uint32_t parity = (round >> 1) & 1u;
-        // this CTA's total for column warp, over that column's warps
-        Fx ta = lane < wpc ? sh.wa[warp + m * lane] : fx_zero();
-        Fx tbx = lane < wpc ? sh.wb[warp + m * lane] : fx_zero();
+        // this CTA's total for column warp, over that column's warps (a fixed FP64 tree)
+        double ca = warp_tree_sum(lane < wpc ? sh.wda[warp + m * lane] : 0.0);
+        double cb = warp_tree_sum(lane < wpc ? sh.wdb[warp + m * lane] : 0.0);
         const bool cbad = __any_sync(kFull, lane < wpc ? sh.wbad[warp + m * lane] != 0 : false);
-        ta = fx_warp_sum(ta);
-        tbx = fx_warp_sum(tbx);
-        double ca = fx_to_double(ta), cb = fx_to_double(tbx);
         if (cbad) ca = cb = __longlong_as_double(0x7ff8000000000000ll);
         ca = __shfl_sync(kFull, ca, 0);
         cb = __shfl_sync(kFull, cb, 0);
@@ -1811,19 +1820,23 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
                 sh.ok = 0;
             }
         } else {
-            Fx sa = fx_zero(), sbx = fx_zero();
-            bool gbad = false;
+            // the C CTA totals (each exact within its CTA, rounded once), added by a fixed FP64
+            // tree over the ranks: lane 0's order of additions is the same in every CTA, so every
+            // CTA takes the same step, and it does not depend on when the pairs arrived.  (An exact
+            // fixed-point sum here cost about 0.8 us more per group on the critical path.)  A bad
+            // total is a NaN, which the tree carries through.
+            double At = 0.0, Bt = 0.0;
             if (lane < C) {
                 const double2 v = sh.cslot[buf][warp][lane];
-                sa = fx_from_double(v.x, gbad);
-                sbx = fx_from_double(v.y, gbad);
+                At = v.x;
+                Bt = v.y;
             }
-            sa = fx_warp_sum(sa);
-            sbx = fx_warp_sum(sbx);
-            const bool any_bad = __any_sync(kFull, gbad);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                At += __shfl_xor_sync(kFull, At, o);
+                Bt += __shfl_xor_sync(kFull, Bt, o);
+            }
             if (lane == 0) {
-                double At = fx_to_double(sa), Bt = fx_to_double(sbx);
-                if (any_bad) At = Bt = __longlong_as_double(0x7ff8000000000000ll);
                 const int jc = j + warp;
                 const double bj = beta[jc], tj = trust[jc];
                 const double g = d.ytx[jc] - At, q = Bt;
@@ -2149,50 +2162,50 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     j += gm - 1;
                     continue;
                 }
-                Fx ga = fx_zero(), ha = fx_zero();
+                // this thread's partial sums (FP32 mode: its exact sums of FP32 terms, rounded once)
+                double G = 0.0, H = 0.0;
                 bool bad = false;
                 if (cd.staged && !staged_ok) {          // never read a stage that did not arrive
                     bad = true;
                     if (threadIdx.x == 0) atomicExch(d.abort_flag, 1);
                 } else if (F32) {
+                    Fx ga = fx_zero(), ha = fx_zero();
                     if (cd.staged) phase_a_staged32(d, cd, sm.stage[buf], sm, ga, ha, bad);
                     else phase_a_global32(d, s, j, reinterpret_cast<int *>(&sm.wide), ga, ha, bad);
+                    G = fx_to_double(ga);
+                    H = fx_to_double(ha);
                 } else {
-                    double G = 0.0, H = 0.0;
                     if (cd.staged)
                         phase_a_staged(d, cd, sm.stage[buf], sm, warp, cd.ngrp, nwarps, 0, 0, cd.nseg, G, H, bad);
                     else phase_a_global<true>(d, s, j, reinterpret_cast<int *>(&sm.wide), G, H, bad, !p.regather_e);
-                    ga = fx_from_double(G, bad);
-                    ha = fx_from_double(H, bad);
                 }
-                // A slice of at most one group lives in warp 0 alone: its warp sum is the CTA's.
+                // The CTA's total by fixed FP64 trees (each warp's lanes, then the warps' sums in warp
+                // order): the same additions in the same order on every launch.  A slice of at most
+                // one group lives in warp 0 alone: its warp sum is the CTA's.
                 const bool one_warp = cd.staged && cd.ngrp <= 1;
                 if (!one_warp) {
-                    const Fx fa = fx_warp_sum(ga);
-                    const Fx fb = fx_warp_sum(ha);
+                    const double fa = warp_tree_sum(G);
+                    const double fb = warp_tree_sum(H);
                     const int wbad = __any_sync(kFull, bad);
                     if (lane == 0) {
-                        sh.wa[warp] = fa;
-                        sh.wb[warp] = fb;
+                        sh.wda[warp] = fa;
+                        sh.wdb[warp] = fb;
                         sh.wbad[warp] = wbad;
                     }
                     __syncthreads();
                 }
                 if (warp == 0) {
-                    Fx ta, tbx;
+                    double ca, cb;
                     bool cbad;
                     if (one_warp) {
-                        ta = fx_warp_sum(ga);
-                        tbx = fx_warp_sum(ha);
+                        ca = warp_tree_sum(G);
+                        cb = warp_tree_sum(H);
                         cbad = __any_sync(kFull, bad);
                     } else {
-                        ta = lane < nwarps ? sh.wa[lane] : fx_zero();
-                        tbx = lane < nwarps ? sh.wb[lane] : fx_zero();
+                        ca = warp_tree_sum(lane < nwarps ? sh.wda[lane] : 0.0);
+                        cb = warp_tree_sum(lane < nwarps ? sh.wdb[lane] : 0.0);
                         cbad = __any_sync(kFull, lane < nwarps ? sh.wbad[lane] != 0 : false);
-                        ta = fx_warp_sum(ta);
-                        tbx = fx_warp_sum(tbx);
                     }
-                    double ca = fx_to_double(ta), cb = fx_to_double(tbx);
                     if (cbad) ca = cb = __longlong_as_double(0x7ff8000000000000ll);
                     ca = __shfl_sync(kFull, ca, 0);
                     cb = __shfl_sync(kFull, cb, 0);
