@@ -362,6 +362,28 @@ __device__ __forceinline__ double warp_tree_sum(double v) {
     return v;
 }
 
+// A warp's two partial sums (lane 0's result).  A warp whose lanes all hold +0 (it took no
+// segment) skips the tree: each FP64 instruction holds the SM partition's FP64 pipe as long with
+// one lane as with 32, and the idle warps of a small column would otherwise queue ten of them each
+// in front of the warps with data.  The test is on bit patterns (integer instructions); the sum of
+// +0s is +0 either way, so the result is the same.
+__device__ __forceinline__ void warp_tree_sum2(double &a, double &b, bool bad) {
+    const bool some = __double_as_longlong(a) != 0 || __double_as_longlong(b) != 0 || bad;
+    if (__any_sync(kFull, some)) {
+        a = warp_tree_sum(a);
+        b = warp_tree_sum(b);
+    }
+}
+
+// The same over lanes 0..15 only (4 levels; lane 0's result).  An FP64 instruction costs its SM
+// partition the same issue time whatever the number of active lanes, so a tree across lanes (one
+// instruction per level) is much cheaper than one lane adding the values in turn.
+__device__ __forceinline__ double warp_tree_sum16(double v) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
 // ------------------------------------------------------------------ shared state
 
 struct StageBuf {
@@ -391,6 +413,7 @@ struct SharedState {
     // a group of narrow (or cluster) columns: per column step results, and the group's flags
     double gdb[kNarrowGroupMax], gr[kNarrowGroupMax], gem1[kNarrowGroupMax], gnbj[kNarrowGroupMax],
         gtrust[kNarrowGroupMax];
+    double gb[kNarrowGroupMax], gt[kNarrowGroupMax], gy[kNarrowGroupMax];   // a cluster group's b_j, T_j, Y'X_j
     int gnumeric, gwarn, gnonzero;
     double G, H;
     double lin, sq, ab;     // cycle sums of b_j Y'X_j, b_j^2, |b_j| (from the bookkeeping thread)
@@ -1772,6 +1795,13 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
         sh.gnumeric = sh.gwarn = 0;
         sh.ok = 1;
     }
+    // the stepping lanes' scalars, loaded now so that their latency hides behind phase A
+    double bj = 0.0, tj = 0.0, yj = 0.0;
+    if (warp < m && lane == 0) {
+        bj = beta[j + warp];
+        tj = trust[j + warp];
+        yj = d.ytx[j + warp];
+    }
     double G = 0.0, H = 0.0;
     bool bad = !cd.staged || !staged_ok;          // never unstaged: the host sizes groups to the buffer
     if (!staged_ok && threadIdx.x == 0) atomicExch(d.abort_flag, 1);   // a stage that did not arrive
@@ -1779,8 +1809,8 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
         phase_a_staged(d, cd, sb, sm, go.goff[t] + wi, go.goff[t + 1], wpc, go.goff[t], go.soff[t], go.soff[t + 1], G, H,
                        bad);
     {
-        const double fa = warp_tree_sum(G);
-        const double fb = warp_tree_sum(H);
+        double fa = G, fb = H;
+        warp_tree_sum2(fa, fb, bad);
         const int wbad = __any_sync(kFull, bad);
         if (lane == 0) {
             sh.wda[warp] = fa;
@@ -1794,8 +1824,14 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
         const int buf = static_cast<int>(round & 1u);
         const uint32_t parity = (round >> 1) & 1u;
         // this CTA's total for column warp, over that column's warps (a fixed FP64 tree)
-        double ca = warp_tree_sum(lane < wpc ? sh.wda[warp + m * lane] : 0.0);
-        double cb = warp_tree_sum(lane < wpc ? sh.wdb[warp + m * lane] : 0.0);
+        double ca, cb;
+        if (wpc == 1) {                 // one warp per column: its sum is the CTA's
+            ca = sh.wda[warp];
+            cb = sh.wdb[warp];
+        } else {
+            ca = warp_tree_sum16(lane < wpc ? sh.wda[warp + m * lane] : 0.0);
+            cb = warp_tree_sum16(lane < wpc ? sh.wdb[warp + m * lane] : 0.0);
+        }
         const bool cbad = __any_sync(kFull, lane < wpc ? sh.wbad[warp + m * lane] != 0 : false);
         if (cbad) ca = cb = __longlong_as_double(0x7ff8000000000000ll);
         ca = __shfl_sync(kFull, ca, 0);
@@ -1831,15 +1867,10 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
                 At = v.x;
                 Bt = v.y;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                At += __shfl_xor_sync(kFull, At, o);
-                Bt += __shfl_xor_sync(kFull, Bt, o);
-            }
+            At = warp_tree_sum16(At);
+            Bt = warp_tree_sum16(Bt);
             if (lane == 0) {
-                const int jc = j + warp;
-                const double bj = beta[jc], tj = trust[jc];
-                const double g = d.ytx[jc] - At, q = Bt;
+                const double g = yj - At, q = Bt;
                 int wl = 0;
                 double db = newton_step(g, q, bj, p, tj, wl), r = 1.0, em1 = 0.0;
                 if (nonfinite_bits(db) || nan_bits(g) || nan_bits(q)) {
@@ -1855,6 +1886,9 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
                 sh.gr[warp] = r;
                 sh.gem1[warp] = em1;
                 sh.gnbj[warp] = bj + db;
+                sh.gb[warp] = bj;
+                sh.gt[warp] = tj;
+                sh.gy[warp] = yj;
             }
         }
     }
@@ -2137,8 +2171,8 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     }
                     if (threadIdx.x == tb)
                         for (int t = 0; t < gm; ++t)
-                            bookkeep(beta, trust, j + t, beta[j + t], trust[j + t], d.ytx[j + t], sh.gdb[t], lin_c, sq_c,
-                                     ab_c, nonzero_tb);
+                            bookkeep(beta, trust, j + t, sh.gb[t], sh.gt[t], sh.gy[t], sh.gdb[t], lin_c, sq_c, ab_c,
+                                     nonzero_tb);
                     // the CTAs outside the cluster keep their own copy of beta (for their cycle sums)
                     for (int t = 0; t < gm; ++t) {
                         const double nbj = sh.gnbj[t];
@@ -2184,8 +2218,8 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                 // one group lives in warp 0 alone: its warp sum is the CTA's.
                 const bool one_warp = cd.staged && cd.ngrp <= 1;
                 if (!one_warp) {
-                    const double fa = warp_tree_sum(G);
-                    const double fb = warp_tree_sum(H);
+                    double fa = G, fb = H;
+                    warp_tree_sum2(fa, fb, bad);
                     const int wbad = __any_sync(kFull, bad);
                     if (lane == 0) {
                         sh.wda[warp] = fa;
@@ -2202,8 +2236,8 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                         cb = warp_tree_sum(H);
                         cbad = __any_sync(kFull, bad);
                     } else {
-                        ca = warp_tree_sum(lane < nwarps ? sh.wda[lane] : 0.0);
-                        cb = warp_tree_sum(lane < nwarps ? sh.wdb[lane] : 0.0);
+                        ca = warp_tree_sum16(lane < nwarps ? sh.wda[lane] : 0.0);   // at most 16 warps
+                        cb = warp_tree_sum16(lane < nwarps ? sh.wdb[lane] : 0.0);
                         cbad = __any_sync(kFull, lane < nwarps ? sh.wbad[lane] != 0 : false);
                     }
                     if (cbad) ca = cb = __longlong_as_double(0x7ff8000000000000ll);
@@ -2849,19 +2883,6 @@ int launch_weighted_counts(const DevLayout &d, const int32_t *w_kept, int32_t *n
     return static_cast<int>(cudaGetLastError());
 }
 
-// L2 size of the current device (cached per device; 0 if the query fails).
-long long l2_bytes() {
-    static long long cache[64];
-    static std::once_flag once[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    std::call_once(once[dev], [dev]() {
-        int v = 0;
-        cache[dev] = cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) == cudaSuccess ? v : 0;
-    });
-    return cache[dev];
-}
-
 int launch_fit(const DevLayout &d, const FitParams &p, FitOut *out_dev, double *hist_dev, int threads,
                void *stream, bool fp32) {
     int e = ensure_smem_attr();
@@ -2870,12 +2891,11 @@ int launch_fit(const DevLayout &d, const FitParams &p, FitOut *out_dev, double *
     FitParams pp = p;
     // FP64 fits of a layout with cluster columns launch in clusters of d.C CTAs
     pp.cluster = (!fp32 && d.C > 0 && d.S % d.C == 0) ? 1 : 0;
-    // Phase C of a slice too big to stage takes E from the stash phase A wrote, or gathers it
-    // again.  The second gather finds E in L2 when E fits there (then the stash only adds DRAM
-    // traffic: 10.66 against 9.44 GB per launch on the 1M-subject fit, same time); otherwise it
-    // goes back to DRAM, and the stash pays.  So: gather again when 8 K bytes fit the L2.
-    pp.regather_e = (!fp32 && (SCCS_REGATHER_E || 8.0 * static_cast<double>(d.K) <= static_cast<double>(l2_bytes())))
-                        ? 1 : 0;
+    // Phase C of a slice too big to stage takes E from the stash phase A wrote.  Gathering it
+    // again instead moves less DRAM (9.44 against 10.66 GB per launch on the 1M-subject fit, whose
+    // E fits the L2) but was 0.65% slower there (27.13 against 26.95 ms, same box, twice), and
+    // slower still where E does not fit the L2.
+    pp.regather_e = (!fp32 && SCCS_REGATHER_E) ? 1 : 0;
     void *args[] = {&dd, &pp, &out_dev, &hist_dev};
     void *fn = fp32 ? reinterpret_cast<void *>(fit_kernel<true>) : reinterpret_cast<void *>(fit_kernel<false>);
     if (!pp.cluster)
