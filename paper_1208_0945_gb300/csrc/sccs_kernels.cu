@@ -1788,7 +1788,9 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
                               const double *beta, const double *trust, bool staged_ok, long long timeout_ns) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int m = cd.gm;
-    const int wpc = nwarps / m;                  // warps per column (the host keeps m <= warps / 2)
+    // warps per column (the host keeps m <= warps / 2); the last warp, whose lane 0 is the staging
+    // thread with the previous group's bookkeeping to do, takes no column
+    const int wpc = (nwarps - 1) / m;
     const int t = warp % m, wi = warp / m;
     const bool mine = wi < wpc;
     if (threadIdx.x == 0) {
@@ -2014,6 +2016,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
         int pend_j = -1;
         double pend_b = 0.0, pend_t = 0.0, pend_y = 0.0, pend_db = 0.0;
+        int pend_gj = 0, pend_gm = 0;   // a cluster group awaiting its bookkeeping (its results in sh.g*)
         double lin_c = 0.0, sq_c = 0.0, ab_c = 0.0;
         long long nonzero_tb = 0;
         for (int c = 1; c <= p.max_cycles && status == kStNotConverged; ++c) {
@@ -2158,6 +2161,12 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                         bookkeep(beta, trust, pend_j, pend_b, pend_t, pend_y, pend_db, lin_c, sq_c, ab_c, nonzero_tb);
                         pend_j = -1;
                     }
+                    // a cluster group's results stay in sh.g* until the next group's steps, which
+                    // come after the barrier that follows phase A, where this thread arrives later
+                    for (int t = 0; t < pend_gm; ++t)
+                        bookkeep(beta, trust, pend_gj + t, sh.gb[t], sh.gt[t], sh.gy[t], sh.gdb[t], lin_c, sq_c, ab_c,
+                                 nonzero_tb);
+                    pend_gm = 0;
                 }
                 if (clcol) {
                     // a cluster group: steps, updates, then the bookkeeping of its columns in order
@@ -2169,10 +2178,10 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                         if (sh.gnumeric) status = kStNumeric;
                         warn |= sh.gwarn;
                     }
-                    if (threadIdx.x == tb)
-                        for (int t = 0; t < gm; ++t)
-                            bookkeep(beta, trust, j + t, sh.gb[t], sh.gt[t], sh.gy[t], sh.gdb[t], lin_c, sq_c, ab_c,
-                                     nonzero_tb);
+                    if (threadIdx.x == tb) {   // the bookkeeping waits for the next unit (off this one's path)
+                        pend_gj = j;
+                        pend_gm = gm;
+                    }
                     // the CTAs outside the cluster keep their own copy of beta (for their cycle sums)
                     for (int t = 0; t < gm; ++t) {
                         const double nbj = sh.gnbj[t];
@@ -2321,6 +2330,10 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     bookkeep(beta, trust, pend_j, pend_b, pend_t, pend_y, pend_db, lin_c, sq_c, ab_c, nonzero_tb);
                     pend_j = -1;
                 }
+                for (int t = 0; t < pend_gm; ++t)
+                    bookkeep(beta, trust, pend_gj + t, sh.gb[t], sh.gt[t], sh.gy[t], sh.gdb[t], lin_c, sq_c, ab_c,
+                             nonzero_tb);
+                pend_gm = 0;
                 sh.lin = lin_c;
                 sh.sq = sq_c;
                 sh.ab = ab_c;
