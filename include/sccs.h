@@ -58,8 +58,9 @@ extern "C" {
 
 /* ---- arithmetic ----------------------------------------------------------------------- */
 #define SCCS_PREC_FP64 0         /* every step in FP64 */
-#define SCCS_PREC_FP32_POLISH 1  /* FP32 phase (FP32 E, compensated per-subject sums, exact
-                                    cross-subject sums, FP64 step) to a relative change of
+#define SCCS_PREC_FP32_POLISH 1  /* FP32 phase (FP32 E, compensated per-subject sums, each
+                                    thread's terms summed exactly, FP64 cross-thread and
+                                    cross-CTA sums in a fixed order, FP64 step) to a relative change of
                                     1e-6, then FP64 cycles from that point to the requested tol
                                     (tol < 0: exactly max_cycles FP64 cycles) */
 #define SCCS_PREC_FP32 2         /* the FP32 phase alone, to the requested tol (no polish) */
