@@ -548,6 +548,90 @@ __device__ bool grid_allreduce2(const DevLayout &d, int me, unsigned long long s
     return true;
 }
 
+// Grid all-reduce of a launch in thread-block clusters of C CTAs (warp 0 of every CTA; S = k C).
+// Two levels.  The C CTAs of a cluster first exchange their pairs through distributed shared
+// memory: every CTA sends its pair to slot [0][rank] of every CTA of its cluster by asynchronous
+// stores counted on that CTA's mbarrier of cluster round `round` (the cluster groups' protocol),
+// and adds the C pairs in rank order by a lane tree, so each holds its cluster's total.  Then every
+// CTA writes that total into its own global slot (phase-tagged as in grid_allreduce2, so every
+// slot of the buffer carries the round's phase and the flat all-reduce may use the same slots
+// next), and reads the k cluster totals from the slots of the clusters' first CTAs (one slot per
+// lane, k <= 32), added by a lane tree.  Every order is fixed, so all CTAs hold the same bits.
+// A CTA can not run two rounds ahead: the round after next needs every cluster's total of the
+// next round, which needs every CTA's pair of it, sent only after it read this round.
+__device__ bool cluster_grid_allreduce2(const DevLayout &d, SharedState &sh, int me, int rank, unsigned round,
+                                        unsigned long long seq, double a, double b, double &A, double &B,
+                                        long long timeout_ns) {
+    const int lane = threadIdx.x & 31;
+    const int C = d.C;
+    const int ncl = d.S / C;
+    // level 1: the cluster
+    const int cbuf = static_cast<int>(round & 1u);
+    const uint32_t parity = (round >> 1) & 1u;
+    if (lane == 0) mbar_arrive_expect_tx(&sh.cbar[cbuf], static_cast<uint32_t>(16 * C));
+    if (lane < C) st_async_f64x2(cluster_addr(&sh.cslot[cbuf][0][rank], lane), a, b, cluster_addr(&sh.cbar[cbuf], lane));
+    int ok = 1;
+    if (!mbar_try_wait(&sh.cbar[cbuf], parity)) {
+        const long long deadline = now_ns() + timeout_ns;
+        for (int it = 0;; ++it) {
+            if (mbar_try_wait(&sh.cbar[cbuf], parity)) break;
+            if ((it & 31) == 31 && (ld_relaxed_i32(d.abort_flag) != 0 || now_ns() > deadline)) {
+                ok = 0;
+                break;
+            }
+        }
+    }
+    if (!__all_sync(kFull, ok)) {
+        if (lane == 0) atomicExch(d.abort_flag, 1);
+        return false;
+    }
+    double ca = 0.0, cb = 0.0;
+    if (lane < C) {
+        const double2 v = sh.cslot[cbuf][0][lane];
+        ca = v.x;
+        cb = v.y;
+    }
+    ca = __shfl_sync(kFull, warp_tree_sum16(ca), 0);
+    cb = __shfl_sync(kFull, warp_tree_sum16(cb), 0);
+    // level 2: the clusters, through global memory
+    const unsigned long long phase = ((seq >> 1) & 1ull) ^ 1ull;
+    unsigned long long *buf = d.slots + (seq & 1ull) * 2ull * static_cast<unsigned long long>(d.S);
+    if (lane == 0) {
+        const unsigned long long ea = (static_cast<unsigned long long>(__double_as_longlong(ca)) &
+                                       0x7fffffffffffffffull) | (phase << 63);
+        const unsigned long long eb = (static_cast<unsigned long long>(__double_as_longlong(cb)) &
+                                       0x7fffffffffffffffull) | (phase << 63);
+        st_relaxed_v2(buf + 2 * me, ea, eb);
+    }
+    const long long deadline = now_ns() + timeout_ns;
+    double sa = 0.0, sb = 0.0;
+    for (int it = 0;; ++it) {
+        bool ready = true;
+        unsigned long long va = 0ull, vb = 0ull;
+        if (lane < ncl) {
+            ld_relaxed_v2(buf + 2 * static_cast<long long>(lane) * C, va, vb);
+            ready = ((va >> 63) == phase) && ((vb >> 63) == phase);
+        }
+        if (__all_sync(kFull, ready)) {
+            if (lane < ncl) {
+                sa = __longlong_as_double(static_cast<long long>(va & 0x7fffffffffffffffull));
+                sb = __longlong_as_double(static_cast<long long>(vb & 0x7fffffffffffffffull));
+            }
+            break;
+        }
+        int give_up = 0;
+        if (lane == 0 && (it & 15) == 15)
+            give_up = (ld_relaxed_i32(d.abort_flag) != 0) || (now_ns() > deadline);
+        if (__shfl_sync(kFull, give_up, 0)) {
+            if (lane == 0) atomicExch(d.abort_flag, 1);
+            return false;
+        }
+    }
+    A = __shfl_sync(kFull, warp_tree_sum(sa), 0);
+    B = __shfl_sync(kFull, warp_tree_sum(sb), 0);
+    return true;
+}
+
 // Block reduction of two per-thread partials (exact), then the grid all-reduce by warp 0.
 // On return (all threads) sh.G, sh.H hold the grid totals; returns false on abort.
 __device__ bool block_grid_reduce(const DevLayout &d, int me, unsigned long long seq, long long timeout_ns,
@@ -1942,6 +2026,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
     // the grid columns only and wait while the cluster runs the rest
     const bool use_cluster = !F32 && p.cluster != 0 && d.C > 0 && d.ccls != nullptr;
     const bool in_cluster = use_cluster && s < d.C;
+    const bool cl_launch = !F32 && p.cluster != 0 && d.C > 0 && d.S / d.C <= 32;   // launched in clusters of d.C CTAs
     const bool use_narrow = !F32 && !use_cluster && d.narrow != nullptr;
     unsigned cround = 0;             // cluster all-reduce rounds taken (one per cluster column)
     unsigned long long crun = 0;     // cluster runs in this launch
@@ -2257,7 +2342,11 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     // before a narrow run, a release/acquire round: CTA 0 then reads every
                     // shard's E and D as of this column's start (the run's first gather)
                     const bool before_run = use_narrow && d.next_wide[j] != (j + 1 < J ? j + 1 : 0);
-                    const bool ok = grid_allreduce2(d, s, seq, ca, cb, At, Bt, timeout, before_run);
+                    // in a launch in clusters the CTAs of each cluster first meet in distributed
+                    // shared memory, and only the clusters' totals go through global memory
+                    const bool ok = cl_launch
+                                        ? cluster_grid_allreduce2(d, sh, s, s % d.C, cround, seq, ca, cb, At, Bt, timeout)
+                                        : grid_allreduce2(d, s, seq, ca, cb, At, Bt, timeout, before_run);
                     if (lane == 0) {
                         double db = 0.0, r = 1.0, em1 = 0.0;
                         if (ok) {
@@ -2303,6 +2392,7 @@ __device__ void run_fit(const DevLayout &d, const FitParams &p, FitOut *out, dou
                     }
                 }
                 ++seq;
+                if (cl_launch) ++cround;
                 __syncthreads();
                 if (!sh.ok) goto aborted;
                 const double db = sh.db;
