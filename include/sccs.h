@@ -97,7 +97,7 @@ typedef struct sccs_create_opts {
                                   in whole clusters.  0 = the default (16 when num_shards is 0, else
                                   off); 2, 4, 8 or 16; < 0 = off.  The result is the same as without
                                   clusters up to rounding (the sums are split differently). */
-    int32_t cluster_max_nnz;   /* 0 = the default 16384 */
+    int32_t cluster_max_nnz;   /* 0 = the default 8192 */
 } sccs_create_opts;
 
 typedef struct sccs_data_info {

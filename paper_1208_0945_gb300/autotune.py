@@ -160,7 +160,7 @@ def _knob_stages(best: dict) -> list:
     on = best.get("cluster_ctas", 16) > 0
     return [
         [dict(cluster_ctas=16), dict(cluster_ctas=8), dict(cluster_ctas=-1)],
-        ([dict(cluster_max_nnz=v) for v in (16384, 65536, 262144)] if on
+        ([dict(cluster_max_nnz=v) for v in (8192, 16384, 65536)] if on
          else [dict(narrow_max_nnz=v) for v in (512, 1024, 2048)]),
         [] if on else [dict(narrow_group_max=g) for g in (1, 4, 8)],
         [dict(threads_per_block=t) for t in (512, 384, 256)],

@@ -233,7 +233,7 @@ void destroy_handle(sccs_handle *h) {
 
 constexpr int32_t kNarrowDefault = 1024;
 constexpr int32_t kClusterDefault = 16;
-constexpr int64_t kClusterMaxNnzDefault = 16384;
+constexpr int64_t kClusterMaxNnzDefault = 8192;
 using sccs::kNarrowGroupMax;
 constexpr int32_t kNarrowMinShards = 4;
 

@@ -58,13 +58,13 @@ def test_tune_launch_takes_the_fastest_setting_of_each_knob():
     def cost(opts):
         t = 10.0
         t += {16: 0.0, 8: 1.0, -1: 3.0}[opts.get("cluster_ctas", 16)]
-        t += {16384: 0.5, 65536: 0.0, 262144: 2.0}.get(opts.get("cluster_max_nnz", 65536), 0.0)
+        t += {8192: 0.5, 16384: 0.0, 65536: 2.0}.get(opts.get("cluster_max_nnz", 16384), 0.0)
         t += {512: 0.0, 384: 0.7, 256: 1.5}[opts.get("threads_per_block", 512)]
         return t
 
     calls = []
     ch = tune_launch(None, timer=lambda d, o: calls.append(dict(o)) or cost(o))
-    assert ch.options == {"cluster_ctas": 16, "cluster_max_nnz": 65536, "threads_per_block": 512}
+    assert ch.options == {"cluster_ctas": 16, "cluster_max_nnz": 16384, "threads_per_block": 512}
     assert ch.kernel_ms == min(t for _, t in ch.trials) == cost(ch.options)
     keys = [tuple(sorted(o.items())) for o in calls]
     assert len(keys) == len(set(keys))                      # no setting probed twice
