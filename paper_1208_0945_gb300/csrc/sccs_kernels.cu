@@ -21,13 +21,15 @@
 //   * The static part of a column's slice (segments, rows, group offsets) is staged into
 //     shared memory by bulk asynchronous copies (cp.async.bulk + mbarrier) one column ahead,
 //     so only the gathers of the state E and D remain on the critical path.
-//   * FP64 issues at one warp-instruction per 64 cycles per SM sub-partition, whatever the
-//     number of active lanes, so the reduction inside a CTA (lane -> warp -> CTA) is done in
-//     exact 192-bit fixed point with integer instructions: it does not depend on which thread
-//     took which subject.  Each CTA's total, rounded once, then meets the other CTAs' totals in
-//     a fixed FP64 order (by shard, not by arrival), so all CTAs obtain bit-identical totals
-//     and every run is repeatable bit for bit.  FP64 is kept for the per-subject arithmetic and
-//     the scalar step, which one lane computes once per coordinate.
+//   * An FP64 instruction holds its SM sub-partition's FP64 pipe about as long with one active
+//     lane as with 32.  The coordinate path's sums (lane -> warp -> CTA -> cluster or grid) are
+//     therefore lane trees in FP64, one instruction per level, in orders fixed by the launch
+//     shape (lane butterflies, warps in warp order, CTAs by cluster rank or shard), never by
+//     arrival: all CTAs obtain bit-identical totals and every run is repeatable bit for bit.
+//     Warps that took no segment skip their tree.  Exact 192-bit fixed point (integer
+//     instructions) remains for the cycle-end log-posterior, the narrow columns and the FP32
+//     mode's per-thread sums.  FP64 is kept for the per-subject arithmetic and the scalar step,
+//     which one lane computes once per coordinate.
 //
 // Every wait is bounded by a deadline on %globaltimer; a CTA that gives up raises the abort
 // flag, waits (bounded) for its own bulk copies in flight and returns; the others see the
@@ -1114,8 +1116,9 @@ __device__ void phase_c_global(const DevLayout &d, int s, int j, double r, doubl
 //
 // FP32 mode (the single-precision variant): E in FP32, each segment's numerator a Kahan
 // (compensated) FP32 sum, D_i an FP32 (hi, lo) pair updated with an error-free two-sum, W_i and
-// its two terms in FP32; the per-subject terms then enter the same exact fixed-point sums, so
-// the cross-subject reductions stay exact.  The scalar step stays in FP64.
+// its two terms in FP32; each thread's per-subject terms are summed exactly in fixed point and
+// rounded once to FP64, then enter the FP64 sums of the coordinate path.  The scalar step stays
+// in FP64.
 
 // Exact conversion of a finite non-negative float below 2^60 (see fx_from_double).
 __device__ __forceinline__ Fx fx_from_float(float v, bool &bad) {
@@ -1857,7 +1860,7 @@ __device__ void narrow_columns(const DevLayout &d, const FitParams &p, int j0, i
 // staged range).  Neither column reads the E or D another writes, so their steps are taken side by
 // side and the result is the sequential one.  Warps are interleaved over the columns (warp w works
 // for column w mod m, as in a narrow group).  Per column: phase A of Section 2.3 over its slice
-// (gather L x exp(Xb), the segment numerators, the W terms of Eqs. 7-9), the CTA's exact sums,
+// (gather L x exp(Xb), the segment numerators, the W terms of Eqs. 7-9), the CTA's sums,
 // then warp t sends its column's pair to slot [t][c] of every CTA of the cluster by asynchronous
 // stores counted on the receiver's mbarrier of this round (r & 1; armed by warp 0 for the C x m
 // pairs it receives), waits (bounded) for that phase, adds the C pairs in a fixed order -- every CTA holds
@@ -1942,8 +1945,8 @@ __device__ bool cluster_group(const DevLayout &d, const FitParams &p, const ColD
                 sh.ok = 0;
             }
         } else {
-            // the C CTA totals (each exact within its CTA, rounded once), added by a fixed FP64
-            // tree over the ranks: lane 0's order of additions is the same in every CTA, so every
+            // the C CTA totals, added by a fixed FP64 tree over the ranks: lane 0's order of
+            // additions is the same in every CTA, so every
             // CTA takes the same step, and it does not depend on when the pairs arrived.  (An exact
             // fixed-point sum here cost about 0.8 us more per group on the critical path.)  A bad
             // total is a NaN, which the tree carries through.
