@@ -369,11 +369,17 @@ __device__ __forceinline__ double warp_tree_sum(double v) {
 // one lane as with 32, and the idle warps of a small column would otherwise queue ten of them each
 // in front of the warps with data.  The test is on bit patterns (integer instructions); the sum of
 // +0s is +0 either way, so the result is the same.
+// The tree also stops at the highest lane that holds data: with data in lanes 0..n-1 only (a
+// small slice), log2 n levels give lane 0 the same sum as five (the other lanes add +0 exactly).
 __device__ __forceinline__ void warp_tree_sum2(double &a, double &b, bool bad) {
     const bool some = __double_as_longlong(a) != 0 || __double_as_longlong(b) != 0 || bad;
-    if (__any_sync(kFull, some)) {
-        a = warp_tree_sum(a);
-        b = warp_tree_sum(b);
+    const unsigned m = __ballot_sync(kFull, some);
+    if (m != 0u) {
+        const int top = 31 - __clz(static_cast<int>(m));     // highest lane with data
+        for (int o = top > 0 ? 1 << (31 - __clz(top)) : 0; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(kFull, a, o);
+            b += __shfl_xor_sync(kFull, b, o);
+        }
     }
 }
 
